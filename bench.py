@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the APM solve (Passy & Bryan, arXiv:1410.0010) on GB300.
+
+One step = one full APM solve over the workload's hierarchy: per level the
+drift + TSC deposit (+ baryons), the FFT convolution with the Green's table,
+the FD accelerations with the parent carry, then the TSC interpolation to all
+particles.  Default workload: periodic 512^3 root + 2 levels of 64 subgrids of
+128^3, 16,777,216 Zel'dovich particles (the largest single-GPU configuration).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+Run: python bench.py [--gpus N --steps K --warmup W] [--workload c5|c4|c3]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "APM level-solve Mcells/s + particles/s, FP32 vs FP64 GPU at stated err; HBM GB/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload(name):
+    import apm_inputs as W
+    return W.CONFIGS[name]()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 7:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = max(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes of each kernel (compulsory HBM traffic of its inputs/outputs)
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(solver, w, levels, csz, rsz):
+    """Bytes per step per kernel, summed over the solved levels.
+
+    csz / rsz: bytes of one complex / real value of the precision."""
+    out = {k: 0 for k in ("gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green",
+                          "fft_y_inv", "fft_x_inv", "accel_carry", "tsc_interp")}
+    n = w.n_particles
+    for lev in levels:
+        for gi in solver.level_grids[lev]:
+            inf = solver.info[gi]
+            G, M, Wd, F = inf["gmf"], inf["fft"], inf["phi_short"], inf["field"]
+            Hx = M[0] // 2 + 1
+            cg = G[0] * G[1] * G[2]
+            gas_b = 8 * int(np.prod(w.grids[gi].dims)) if (w.gas is not None and w.gas[gi] is not None) else 0
+            out["gas_init"] += 8 * cg + gas_b
+            out["tsc_deposit"] += 8 * cg                      # the accumulated field
+            out["fft_x_fwd"] += 8 * cg + csz * G[1] * G[2] * Hx
+            out["fft_y_fwd"] += csz * G[1] * G[2] * Hx + csz * G[2] * M[1] * Hx
+            out["fft_z_green"] += (csz * G[2] * M[1] * Hx + csz * Wd[2] * M[1] * Hx
+                                   + rsz * Hx * (M[1] // 2 + 1) * (M[2] // 2 + 1))
+            out["fft_y_inv"] += csz * Wd[2] * M[1] * Hx + csz * Wd[2] * Wd[1] * Hx
+            out["fft_x_inv"] += csz * Wd[2] * Wd[1] * Hx + rsz * Wd[0] * Wd[1] * Wd[2]
+            ec = F[0] * F[1] * F[2]
+            out["accel_carry"] += rsz * Wd[0] * Wd[1] * Wd[2] + 4 * rsz * ec
+            out["tsc_interp"] += 3 * rsz * ec
+        out["tsc_deposit"] += 56 * n      # x, y, z, vx, vy, vz, m per level
+        out["tsc_interp"] += 48 * n       # positions and velocities per level
+    out["tsc_interp"] += 3 * rsz * n      # accelerations written once
+    return out
+
+
+# ----------------------------------------------------------------------------
+# oracle sample (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(w, n_grids=2):
+    """The first n_grids refined grids of the workload solved by the FP64 CPU oracle:
+    TSC deposit of every particle touching each GMF, naive-DFT convolution on its
+    M grid, FD accelerations (the parent carry is omitted: zero parent fields).
+    Returns (interior cells, seconds, description)."""
+    import oracle
+    cfg = oracle.Config(periodic=w.periodic, mass_frac_bits=w.mass_frac_bits)
+    grids = [oracle.Grid(*g) for g in w.grids]
+    ids = [i for i, g in enumerate(w.grids) if g.level >= 1][:n_grids]
+    oracle.lib()
+    t0 = time.perf_counter()
+    for gi in ids:
+        gas = None if w.gas is None else w.gas[gi]
+        gmf, _ = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt, gas=gas)
+        phis = oracle.solve(cfg, grids, gi, gmf)
+        oracle.accel(cfg, grids, gi, phis)
+    dt = time.perf_counter() - t0
+    cells = int(sum(np.prod(w.grids[gi].dims) for gi in ids))
+    plans = [oracle.plan_grid(cfg, grids, gi).M for gi in ids]
+    desc = (f"oracle solve of {len(ids)} refined subgrids {[tuple(w.grids[gi].dims) for gi in ids]} "
+            f"(M={plans}): deposit of all {w.n_particles} particles, naive-DFT convolution, "
+            f"FD accelerations")
+    return cells, dt, desc
+
+
+def cpu_cores():
+    n = os.environ.get("APM_ORACLE_THREADS")
+    return int(n) if n and int(n) > 0 else (os.cpu_count() or 1)
+
+
+# ----------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    times, cells = [], 0
+    for i in range(args.warmup + args.steps):
+        c, dt, desc = oracle_sample(w)
+        if i >= args.warmup:
+            times.append(dt)
+            cells = c
+    t = sum(times) / len(times)
+    value = cells / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mcells/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "Mcells/s", "cores": cpu_cores(),
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "Mcells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_apm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1410_0010_gb300.solver import Particles, Solver
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workload(args.workload)
+    levels = list(range(1 + max(g.level for g in w.grids))) if w.solve_levels is None else w.solve_levels
+
+    def make(precision):
+        s = Solver(w.grids, periodic=w.periodic, precision=precision,
+                   mass_frac_bits=w.mass_frac_bits, device=local)
+        return s, s.alloc_all()
+
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in w.particles.items()}
+    dparts = {k: v.to(dev) for k, v in host.items()}
+    P = Particles(dparts)
+    gas = None
+    if w.gas is not None:
+        gas = [None if g is None else torch.from_numpy(np.ascontiguousarray(g)).to(dev) for g in w.gas]
+    n = w.n_particles
+    cells = w.interior_cells(levels)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    def timed(fn, steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / steps)
+
+    # ---------------- FP32 (the product configuration)
+    s32, b32 = make("fp32")
+    pacc = torch.zeros((3, n), dtype=torch.float32, device=dev)
+
+    def step32():
+        s32.step(P, w.half_dt, b32, pacc, gas=gas, levels=levels)
+
+    for _ in range(args.warmup):
+        step32()
+    s32.sync_status()
+    graph = None
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step32()
+        graph.replay()
+        torch.cuda.synchronize()
+        s32.sync_status()
+    except Exception as exc:  # capture is an optimisation; eager launches are the fallback
+        print(f"# graph capture failed ({exc}); timing eager launches", file=sys.stderr)
+        graph = None
+    run = graph.replay if graph is not None else step32
+    used_graph = graph is not None
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms = timed(run, args.steps)
+    clk = clocks.stop()
+    s32.sync_status()
+
+    # per-kernel device times (tracing on, eager, same workload)
+    s32.profile(True)
+    for _ in range(args.steps):
+        step32()
+    prof = s32.profile_read()
+    s32.profile(False)
+    launches_per_step = sum(v[0] for v in prof.values()) / max(args.steps, 1)
+
+    # end to end: host inputs copied in, particle accelerations copied out, every step
+    hout = torch.empty((3, n), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        for k in dparts:
+            dparts[k].copy_(host[k], non_blocking=True)
+        step32()
+        hout.copy_(pacc, non_blocking=True)
+
+    e2e_ms = timed(e2e_step, args.steps)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = hout.numel() * hout.element_size()
+
+    # ---------------- FP64 GPU path (same kernels in double), and the FP32 error against it
+    fp64 = None
+    if not args.no_fp64:
+        phi32 = [t.clone() for t in b32[-1]["phi"]]
+        pacc32 = pacc.clone()
+        graph = None
+        run = None
+        s64, b64 = make("fp64")
+        pacc64 = torch.zeros((3, n), dtype=torch.float64, device=dev)
+
+        def step64():
+            s64.step(P, w.half_dt, b64, pacc64, gas=gas, levels=levels)
+
+        for _ in range(max(1, args.warmup // 2)):
+            step64()
+        s64.sync_status()
+        ms64 = timed(step64, max(1, args.steps // 2))
+        own = pacc64.abs().sum(0) > 0
+        e_pacc = float(torch.linalg.vector_norm((pacc32.double() - pacc64)[:, own]) /
+                       torch.linalg.vector_norm(pacc64[:, own]))
+        e_phi = float(max(torch.linalg.vector_norm(a.double() - b) / torch.linalg.vector_norm(b)
+                          for a, b in zip(phi32, b64[-1]["phi"])))
+        fp64 = {"value": cells / (ms64 / 1e3) / 1e6 * world, "ms_per_step": ms64,
+                "fp32_speedup": ms64 / ms, "fp32_rel_l2_vs_fp64": {"phi_finest": e_phi, "pacc": e_pacc}}
+        s64.close()
+
+    # ---------------- roofline of the dominant kernel
+    hbm, peak_src = peaks()
+    ab = algorithmic_bytes(s32, w, levels, 8, 4)
+    kernels = {}
+    for name, (cnt, tot) in prof.items():
+        if cnt == 0:
+            continue
+        per_launch_ms = tot / cnt
+        bytes_per_launch = ab[name] / (cnt / args.steps)
+        kernels[name] = {"launches_per_step": cnt / args.steps, "ms_per_launch": per_launch_ms,
+                         "share": tot / sum(v[1] for v in prof.values()),
+                         "GBps": bytes_per_launch / (per_launch_ms * 1e-3) / 1e9}
+    top = max(kernels, key=lambda k: kernels[k]["share"])
+    ach = kernels[top]["GBps"]
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(f"{w.name}:{top}")
+    roofline = {"bound": "hbm", "kernel": top, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": peak_src, "traffic": traffic}
+
+    # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        c, dt, desc = oracle_sample(w)
+        cpu = {"value": c / dt / 1e6, "unit": "Mcells/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": desc, "seconds": dt}
+
+    value = cells / (ms / 1e3) / 1e6 * world
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "levels": levels, "grids": len(w.grids),
+                   "interior_cells": cells, "particles": n, "periodic": w.periodic,
+                   "l2": "inputs larger than L2 (no flush)", "cuda_graph": used_graph,
+                   "parallelism": f"replicas x{world}"},
+        "particles_per_s": n / (ms / 1e3) * world,
+        "roofline": roofline,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": {"value": cells / (e2e_ms / 1e3) / 1e6 * world, "unit": "Mcells/s",
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "fp64": fp64,
+        "clocks": clk,
+    }
+    s32.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["apm", "reference"], default="apm")
+    ap.add_argument("--workload", choices=["c3", "c4", "c5"], default="c5")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_apm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

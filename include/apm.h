@@ -1,0 +1,244 @@
+/*
+ * apm.h -- C ABI of libapm: the adaptive particle-mesh (APM) gravity level
+ * solve of Passy & Bryan, "An adaptive particle-mesh gravity solver for ENZO"
+ * (arXiv:1410.0010), on NVIDIA GB300 (sm_103a).
+ *
+ * One APM solve over a static hierarchy of nested grids runs, level by level
+ * from the root down (Sec. 2 and Sec. 2.2):
+ *
+ *   apm_deposit      particles drifted half a step, TSC-deposited, plus baryons,
+ *                    into each grid's gravitating-mass field (GMF)
+ *   apm_solve_level  per-grid FFT convolution with the APM Green's function
+ *                    (periodic or isolated root, short-range on refined levels)
+ *   apm_accel        finite-difference accelerations plus the potential and
+ *                    acceleration carried (interpolated) from the parent grid
+ *   apm_interp       TSC interpolation of the accelerations back to particles
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is a DEVICE pointer unless stated otherwise; the
+ *    caller owns it.  Per-grid arguments are HOST arrays of device pointers,
+ *    one entry per grid of the level, in the order the grids appear in the
+ *    hierarchy passed to apm_set_hierarchy.
+ *  - 3-D fields are x-fastest: cell (x, y, z) of an (nx, ny, nz) box is at
+ *    x + nx * (y + ny * z).  Vector fields are 3 consecutive components
+ *    (structure of arrays) in one allocation.
+ *  - Floating-point fields (phi_short, phi, acc, acc_out) are float when the
+ *    context's precision is APM_FP32 and double for APM_FP64.
+ *  - `stream` is a cudaStream_t (NULL: the legacy default stream).  Calls are
+ *    asynchronous on it; calls on one context must be ordered (one stream, or
+ *    synchronised by the caller).  A context is not thread-safe.
+ *  - Errors detectable on the host are returned immediately and nothing is
+ *    enqueued.  Errors the kernels detect (fixed-point overflow, a particle
+ *    outside an isolated box, a wait that ran out) are latched in a device
+ *    status word and returned by apm_sync_status.
+ *  - No entry point allocates device memory after apm_set_hierarchy, and no
+ *    entry point other than apm_sync_status synchronises the stream.
+ */
+#ifndef APM_H
+#define APM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    APM_OK = 0,
+    APM_E_INVALID = 1,     /* bad argument (NULL, size, level out of range) */
+    APM_E_NESTING = 2,     /* hierarchy violates the nesting rules */
+    APM_E_NOMEM = 3,       /* device or pinned allocation failed */
+    APM_E_CUDA = 4,        /* a CUDA runtime call failed */
+    APM_E_OVERFLOW = 5,    /* |m 2^F| >= 2^62 for some particle (it was skipped) */
+    APM_E_OUT_OF_BOX = 6,  /* particle outside an isolated root (folded to its edge) */
+    APM_E_TIMEOUT = 7,     /* a bounded device wait ran out */
+    APM_E_UNSUPPORTED = 8, /* valid request this build does not implement */
+    APM_E_STATE = 9        /* call out of order (e.g. no hierarchy set) */
+} apm_status;
+
+typedef enum { APM_FP32 = 0, APM_FP64 = 1 } apm_precision;
+typedef enum { APM_BC_ISOLATED = 0, APM_BC_PERIODIC = 1 } apm_bc;
+
+/* Method parameters.  Defaults (apm_config_default) are the paper's:
+ * a = 3.4 delta_l and R = 2 (Sec. 2.2), padding factor 0.65 (Sec. 2.2),
+ * isolated root (Sec. 3), FP32 field arithmetic, 52 fraction bits. */
+typedef struct {
+    double box;              /* side of the cubic domain [0, box)^3 */
+    double a_over_dx;        /* smoothing diameter a_l / delta_l (Sec. 2.2: 3.4) */
+    int32_t refine;          /* refinement factor R between levels (Sec. 2.2: 2) */
+    double pad_factor;       /* extra cells 0.65 R a/delta (Sec. 2.2): border B =
+                                ceil(pad_factor * refine * a_over_dx) cells per side */
+    int32_t root_bc;         /* apm_bc of the root grid */
+    int32_t precision;       /* apm_precision of FFT, multiply and gradient */
+    int32_t mass_frac_bits;  /* F: GMF cells hold mass * 2^F as int64, 1 <= F <= 62 */
+    int32_t root_correction; /* isolated root: 1 adds the k-space optimal correction
+                                to the real-space kernel (see apm_set_hierarchy) */
+    int32_t device;          /* CUDA device ordinal of the context; -1: current device */
+} apm_config;
+
+/* One grid.  start: global level-`level` cell index of the first interior cell
+ * (cell i of level l covers [i, i+1) * box / (N0 R^l)); dims: interior cells.
+ * Grid 0 must be the root: level 0, parent -1, start 0, dims (N0, N0, N0). */
+typedef struct {
+    int32_t level;
+    int32_t parent;       /* index of the parent grid in the hierarchy array */
+    int64_t start[3];
+    int32_t dims[3];
+} apm_grid;
+
+/* Particles: device structure of arrays of n doubles each (positions in
+ * [0, box), velocities, masses).  The arrays are only read. */
+typedef struct {
+    int64_t n;
+    const double *x, *y, *z, *vx, *vy, *vz, *m;
+} apm_particles;
+
+/* Derived sizes of one grid (apm_get_grid_info). */
+typedef struct {
+    int32_t level;
+    int32_t border;       /* B: GMF border cells per side (0 on the root) */
+    int32_t gmf[3];       /* GMF box: dims + 2B (root: dims) */
+    int32_t fft[3];       /* FFT lengths M (isolated root 2 N0, periodic root N0,
+                             refined: smallest {2,3,5,7}-smooth >= dims + 4B) */
+    int32_t phi_short[3]; /* dims + 4: cells [-2, dims+2) */
+    int32_t field[3];     /* dims + 2: cells [-1, dims+1) of phi and each acc component */
+    int32_t level_index;  /* position of the grid among the grids of its level */
+    double delta;         /* cell size box / (N0 R^level) */
+} apm_grid_info;
+
+typedef struct apm_ctx apm_ctx;
+
+/* Fills the paper's defaults (see apm_config). */
+void apm_config_default(apm_config* cfg);
+
+/* Creates a context on cfg->device (or the current device).  Allocates only
+ * the status word.  Returns APM_E_INVALID for out-of-range parameters,
+ * APM_E_UNSUPPORTED for a refinement factor other than 2, APM_E_CUDA when no
+ * usable device is present. */
+apm_status apm_create(const apm_config* cfg, apm_ctx** out);
+
+/* Sets the static hierarchy (Sec. 3: a tree of nested grids, all grids of one
+ * resolution on one level) and prepares everything the solves need:
+ *  - validates the tree: levels 0..L each non-empty, every child's parent on the
+ *    level above, sibling interiors disjoint, and every parent cell a child
+ *    reads (its GMF border, Sec. 2, and the trilinear carry of its cells
+ *    [-1, dims]) inside the parent's interior; otherwise APM_E_NESTING;
+ *  - plans each grid's border B and FFT lengths M (FFT lengths up to 1024);
+ *  - builds on the GPU, in FP64, the Green's-function table of every distinct
+ *    (grid type, M) (Sec. 2.2 Eq. influence with the Brillouin sum of
+ *    Eq. brillouin truncated to n in [-1,1]^3, Eq. assignment, assignment2 and
+ *    reference with the TSC assignment function and the two-point FD gradient;
+ *    refined levels use the short-range reference force, the periodic root
+ *    sets the k = 0 mode to 0 (mean removed, Sec. 3.4), the isolated root
+ *    transforms the real-space S-S pair potential on the doubled grid,
+ *    Sec. 2.1, plus the optimal correction when cfg.root_correction), cached
+ *    per shape (Sec. 2.2, last paragraph), with an FP32 copy;
+ *  - allocates the FFT workspace and particle lookup tables.
+ * grids: HOST array of n_grids descriptors.  May be called again to replace
+ * the hierarchy (frees the previous one; synchronises the device). */
+apm_status apm_set_hierarchy(apm_ctx* ctx, const apm_grid* grids, int32_t n_grids);
+
+/* Checks a hierarchy against the rules of apm_set_hierarchy without touching
+ * the GPU (host only): APM_OK, APM_E_INVALID (malformed descriptors or
+ * config) or APM_E_NESTING. */
+apm_status apm_validate_hierarchy(const apm_config* cfg, const apm_grid* grids, int32_t n_grids);
+
+/* Derived sizes of grid `grid` (index into the hierarchy array). */
+apm_status apm_get_grid_info(const apm_ctx* ctx, int32_t grid, apm_grid_info* out);
+
+/* Number of levels of the current hierarchy (0 if none). */
+int32_t apm_num_levels(const apm_ctx* ctx);
+
+/* Gravitating-mass field of every grid of `level` (Sec. 2):
+ *  gmf[c] = sum over particles of rint((m w) 2^F) + rint((rho delta^3) 2^F)
+ * with w the TSC weight (27 cells, Sec. 2) of the particle position drifted by
+ * x + v * half_dt (Sec. 2, time-centred density); the centre cell of each
+ * particle receives rint(m 2^F) minus its other 26 charges, so integer mass is
+ * conserved exactly and the sums are independent of particle order.  Every
+ * particle whose cloud touches a grid's GMF box contributes (the modified
+ * deposit of Sec. 2: particles of the grid, its parent and the parent's
+ * siblings alike).  Cloud cells outside a refined grid's GMF box are dropped;
+ * on an isolated root they fold into the edge cell; on a periodic root they
+ * wrap.  Baryons: interior cells take gas[g] (density, dims^3 doubles);
+ * border cells take the parent cell's density from parent_gas (the parent's
+ * baryons copied onto the boundary, Sec. 2).
+ *  particles : device particle arrays (all particles of the simulation)
+ *  gas       : HOST array (grids of the level) of device pointers to dims^3
+ *              doubles, or NULL for no baryons; entries may be NULL
+ *  parent_gas: HOST array (grids of level-1) of device pointers to the parent
+ *              grids' interior densities, or NULL (no baryons in the border)
+ *  gmf       : HOST array (grids of the level) of device pointers to int64 GMF
+ *              boxes (apm_grid_info.gmf), fully overwritten
+ * Sums are exact modulo 2^64 (exact whenever each cell's true sum fits). */
+apm_status apm_deposit(apm_ctx* ctx, int32_t level, const apm_particles* particles,
+                       double half_dt, const double* const* gas,
+                       const double* const* parent_gas, int64_t* const* gmf, void* stream);
+
+/* Short-range (refined level) or full (root) potential of every grid of
+ * `level` (Sec. 2.2, Eq. PoissonFourier with Eq. influence): the GMF cell
+ * masses (gmf * 2^-F, converted in FP64) are zero-padded onto the grid's M
+ * grid, transformed, multiplied by the Green's table, transformed back, and
+ * the window of cells [-2, dims+2) is written:
+ *  phi_short: HOST array (grids of the level) of device pointers to
+ *             (dims+4)^3 floats/doubles (apm_grid_info.phi_short)
+ * The FFTs are hand-written mixed-radix (2,3,4,5,7,8) Stockham passes. */
+apm_status apm_solve_level(apm_ctx* ctx, int32_t level, const int64_t* const* gmf,
+                           void* const* phi_short, void* stream);
+
+/* Accelerations and carried potential on cells [-1, dims+1) of every grid of
+ * `level` (Sec. 2.2: difference the potential, then add the parent's
+ * acceleration interpolated onto the refined grid):
+ *   phi      = phi_short + I(parent phi)
+ *   acc_j    = -(phi_short(c + e_j) - phi_short(c - e_j)) / (2 delta) + I(parent acc_j)
+ * with I the trilinear interpolation from parent cell centres, in FP64.
+ *  parent_phi, parent_acc: HOST arrays (grids of level-1) of the parent level's
+ *             phi / acc outputs, or NULL at level 0 (no parent term)
+ *  phi      : HOST array of device pointers to (dims+2)^3 values
+ *  acc      : HOST array of device pointers to 3 (dims+2)^3 values (x, y, z) */
+apm_status apm_accel(apm_ctx* ctx, int32_t level, const void* const* phi_short,
+                     const void* const* parent_phi, const void* const* parent_acc,
+                     void* const* phi, void* const* acc, void* stream);
+
+/* TSC interpolation of the cell accelerations to the particles (Sec. 2, the
+ * same 27 weights as the deposit, at the same drifted position).  Only
+ * particles owned by `level` are written: those inside the interior of a grid
+ * of this level and not inside any grid of level+1 (the finest grid holding a
+ * particle supplies its acceleration).  On an isolated root the cloud folds
+ * into the edge cells as in the deposit.
+ *  acc     : HOST array (grids of the level) of the apm_accel outputs
+ *  acc_out : device array of 3 n floats/doubles (x, y, z components, n each);
+ *            may be NULL when n == 0 */
+apm_status apm_interp(apm_ctx* ctx, int32_t level, const void* const* acc,
+                      const apm_particles* particles, double half_dt, void* acc_out,
+                      void* stream);
+
+/* Kernel tracing.  While enabled, every kernel the context launches is
+ * bracketed by CUDA events recorded on the stream it runs on (events come from
+ * a pool of `capacity` pairs allocated here; launches beyond it are not
+ * timed).  apm_profile_read synchronises the device, adds the elapsed times of
+ * the recorded launches of kernel `kernel` (0 <= kernel < apm_kernel_count())
+ * to its totals and returns the totals since the last enable:
+ * launches and summed device milliseconds.  Disabling frees the pool. */
+apm_status apm_profile_enable(apm_ctx* ctx, int32_t on, int32_t capacity);
+apm_status apm_profile_read(apm_ctx* ctx, int32_t kernel, int64_t* launches, double* total_ms);
+int32_t apm_kernel_count(void);
+const char* apm_kernel_name(int32_t kernel);
+
+/* Synchronises `stream`, returns the first error the kernels latched since the
+ * last call (APM_OK if none) and clears it. */
+apm_status apm_sync_status(apm_ctx* ctx, void* stream);
+
+/* Static description of a status code. */
+const char* apm_status_string(apm_status s);
+
+/* Frees everything the context owns (synchronises the device first). */
+void apm_destroy(apm_ctx* ctx);
+
+/* Library version string. */
+const char* apm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APM_H */

@@ -1,0 +1,110 @@
+"""ctypes declarations of libapm's C ABI (include/apm.h).  Argument marshalling only."""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libapm.so")
+
+c_i32, c_i64, c_dbl, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+APM_OK = 0
+STATUS_NAMES = {0: "APM_OK", 1: "APM_E_INVALID", 2: "APM_E_NESTING", 3: "APM_E_NOMEM",
+                4: "APM_E_CUDA", 5: "APM_E_OVERFLOW", 6: "APM_E_OUT_OF_BOX", 7: "APM_E_TIMEOUT",
+                8: "APM_E_UNSUPPORTED", 9: "APM_E_STATE"}
+APM_FP32, APM_FP64 = 0, 1
+APM_BC_ISOLATED, APM_BC_PERIODIC = 0, 1
+
+
+class ApmConfig(ctypes.Structure):
+    _fields_ = [("box", c_dbl), ("a_over_dx", c_dbl), ("refine", c_i32), ("pad_factor", c_dbl),
+                ("root_bc", c_i32), ("precision", c_i32), ("mass_frac_bits", c_i32),
+                ("root_correction", c_i32), ("device", c_i32)]
+
+
+class ApmGrid(ctypes.Structure):
+    _fields_ = [("level", c_i32), ("parent", c_i32), ("start", c_i64 * 3), ("dims", c_i32 * 3)]
+
+
+class ApmParticles(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("x", c_void_p), ("y", c_void_p), ("z", c_void_p),
+                ("vx", c_void_p), ("vy", c_void_p), ("vz", c_void_p), ("m", c_void_p)]
+
+
+class ApmGridInfo(ctypes.Structure):
+    _fields_ = [("level", c_i32), ("border", c_i32), ("gmf", c_i32 * 3), ("fft", c_i32 * 3),
+                ("phi_short", c_i32 * 3), ("field", c_i32 * 3), ("level_index", c_i32),
+                ("delta", c_dbl)]
+
+
+# name -> (restype, argtypes); every function declared in include/apm.h
+SIGNATURES = {
+    "apm_config_default": (None, [ctypes.POINTER(ApmConfig)]),
+    "apm_create": (c_i32, [ctypes.POINTER(ApmConfig), ctypes.POINTER(c_void_p)]),
+    "apm_set_hierarchy": (c_i32, [c_void_p, ctypes.POINTER(ApmGrid), c_i32]),
+    "apm_validate_hierarchy": (c_i32, [ctypes.POINTER(ApmConfig), ctypes.POINTER(ApmGrid), c_i32]),
+    "apm_get_grid_info": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmGridInfo)]),
+    "apm_num_levels": (c_i32, [c_void_p]),
+    "apm_deposit": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmParticles), c_dbl,
+                            ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                            ctypes.POINTER(c_void_p), c_void_p]),
+    "apm_solve_level": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p),
+                                ctypes.POINTER(c_void_p), c_void_p]),
+    "apm_accel": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                          ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                          ctypes.POINTER(c_void_p), c_void_p]),
+    "apm_interp": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p), ctypes.POINTER(ApmParticles),
+                           c_dbl, c_void_p, c_void_p]),
+    "apm_sync_status": (c_i32, [c_void_p, c_void_p]),
+    "apm_profile_enable": (c_i32, [c_void_p, c_i32, c_i32]),
+    "apm_profile_read": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]),
+    "apm_kernel_count": (c_i32, []),
+    "apm_kernel_name": (ctypes.c_char_p, [c_i32]),
+    "apm_status_string": (ctypes.c_char_p, [c_i32]),
+    "apm_destroy": (None, [c_void_p]),
+    "apm_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class ApmError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        name = STATUS_NAMES.get(self.code, str(code))
+        msg = f"{where}: {name}"
+        try:
+            msg += f" ({lib().apm_status_string(self.code).decode()})"
+        except Exception:  # pragma: no cover
+            pass
+        super().__init__(msg)
+
+
+def lib():
+    """libapm, loaded once.  Raises if the CUDA library has not been built:
+    there is no CPU fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libapm.so not found at {LIB_PATH}: build it first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code, where):
+    if code != APM_OK:
+        raise ApmError(code, where)
+
+
+def ptr_array(ptrs):
+    """HOST array of device pointers (None -> NULL entry)."""
+    arr = (c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr

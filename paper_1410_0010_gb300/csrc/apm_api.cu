@@ -1,0 +1,896 @@
+// apm_api.cu -- the C ABI of libapm (include/apm.h): context, hierarchy
+// planning and validation, device arenas, and the per-level launch sequences.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "apm_internal.cuh"
+
+using namespace apm;
+
+namespace {
+
+constexpr int kRoles = 11;
+enum Role { R_GMF = 0, R_GAS, R_PGAS, R_GMF_IN, R_PHIS, R_PHIS_IN, R_PPHI, R_PACC, R_PHI, R_ACC, R_ACC_IN };
+constexpr int kChunkCells = 2048;
+
+// kernels, in launch order of one level
+enum Kern { K_GAS = 0, K_DEPOSIT, K_XF, K_YF, K_Z, K_YI, K_XI, K_ACCEL, K_INTERP, K_COUNT };
+const char* const kKernelNames[K_COUNT] = {"gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd",
+                                           "fft_z_green", "fft_y_inv", "fft_x_inv", "accel_carry",
+                                           "tsc_interp"};
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;          // 2 per pair
+    std::vector<int> kind;                // per used pair
+    int used = 0;
+    long long launches[K_COUNT] = {};
+    double ms[K_COUNT] = {};
+};
+
+struct Level {
+    int level = 0;
+    std::vector<int> grids;          // hierarchy indices, in order
+    std::vector<GridDev> hg;         // host copies of the descriptors
+    GridDev* d_grids = nullptr;
+    LevelDev dev{};
+    // CTA work lists
+    Chunk* d_xf = nullptr; int n_xf = 0; size_t smem_xf = 0;
+    Chunk* d_yf = nullptr; int n_yf = 0; size_t smem_yf = 0;
+    Chunk* d_z = nullptr;  int n_z = 0;  size_t smem_z = 0;
+    Chunk* d_yi = nullptr; int n_yi = 0; size_t smem_yi = 0;
+    Chunk* d_xi = nullptr; int n_xi = 0; size_t smem_xi = 0;
+    Chunk* d_gas = nullptr; int n_gas = 0;
+    Chunk* d_acc = nullptr; int n_acc = 0;
+    // pointer tables (device) + pinned mirrors + last uploaded values
+    int cap = 0;
+    void** d_ptr = nullptr;          // kRoles * cap
+    void** h_ptr = nullptr;          // pinned, kRoles * cap
+    std::vector<void*> last[kRoles];
+    cudaEvent_t ev = nullptr;
+    bool ev_pending = false;
+};
+
+}  // namespace
+
+struct apm_ctx {
+    apm_config cfg{};
+    int device = 0;
+    unsigned* d_status = nullptr;
+    bool has_hier = false;
+    std::vector<apm_grid> grids;
+    std::vector<int> level_of, index_in_level;
+    std::vector<Level> levels;
+    std::vector<void*> dev_allocs;
+    double2* tw64 = nullptr;
+    float2* tw32 = nullptr;
+    double* tab64 = nullptr;
+    float* tab32 = nullptr;
+    void* wsA = nullptr;
+    void* wsB = nullptr;
+    Profiler prof;
+};
+
+namespace {
+
+bool fault_alloc() {
+    const char* f = std::getenv("APM_FAULT_INJECT");
+    return f && std::strcmp(f, "alloc") == 0;
+}
+
+apm_status dmalloc(apm_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (fault_alloc()) return APM_E_NOMEM;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? APM_E_NOMEM : APM_E_CUDA;
+    }
+    c->dev_allocs.push_back(*p);
+    return APM_OK;
+}
+
+template <typename V>
+apm_status upload(apm_ctx* c, V** dst, const std::vector<V>& src) {
+    apm_status st = dmalloc(c, (void**)dst, src.size() * sizeof(V));
+    if (st != APM_OK) return st;
+    if (!src.empty() &&
+        cudaMemcpy(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess)
+        return APM_E_CUDA;
+    return APM_OK;
+}
+
+void free_hierarchy(apm_ctx* c) {
+    cudaDeviceSynchronize();
+    for (void* p : c->dev_allocs) cudaFree(p);
+    c->dev_allocs.clear();
+    for (Level& L : c->levels) {
+        if (L.h_ptr) cudaFreeHost(L.h_ptr);
+        if (L.ev) cudaEventDestroy(L.ev);
+    }
+    c->levels.clear();
+    c->grids.clear();
+    c->level_of.clear();
+    c->index_in_level.clear();
+    c->tw64 = nullptr; c->tw32 = nullptr; c->tab64 = nullptr; c->tab32 = nullptr;
+    c->wsA = nullptr; c->wsB = nullptr;
+    c->has_hier = false;
+}
+
+int smooth7_at_least(int n) {
+    for (int m = std::max(n, 1);; ++m) {
+        int r = m;
+        for (int p : {2, 3, 5, 7})
+            while (r % p == 0) r /= p;
+        if (r == 1) return m;
+    }
+}
+
+bool make_plan(int L, FftPlan1D* pl) {
+    pl->L = L;
+    pl->nst = 0;
+    int n = L;
+    auto push = [&](int r) {
+        if (pl->nst >= kMaxStages) return false;
+        pl->radix[pl->nst++] = (unsigned char)r;
+        n /= r;
+        return true;
+    };
+    while (n % 8 == 0) if (!push(8)) return false;
+    while (n % 4 == 0) if (!push(4)) return false;
+    while (n % 2 == 0) if (!push(2)) return false;
+    for (int p : {3, 5, 7})
+        while (n % p == 0) if (!push(p)) return false;
+    return n == 1 && L >= 2;
+}
+
+long long floor_div(long long a, long long b) {
+    long long q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+int border_cells(const apm_config& c) {
+    return (int)std::ceil(c.pad_factor * c.refine * c.a_over_dx - 1e-12);
+}
+
+int pow2_floor(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// Validates the tree (see apm_set_hierarchy).
+apm_status validate(const apm_config& cfg, const apm_grid* gr, int n) {
+    if (n < 1) return APM_E_INVALID;
+    const apm_grid& r = gr[0];
+    if (r.level != 0 || r.parent != -1 || r.start[0] || r.start[1] || r.start[2]) return APM_E_NESTING;
+    if (r.dims[0] != r.dims[1] || r.dims[0] != r.dims[2] || r.dims[0] < 4) return APM_E_INVALID;
+    int maxlev = 0;
+    for (int i = 1; i < n; ++i) {
+        const apm_grid& g = gr[i];
+        if (g.level < 1 || g.parent < 0 || g.parent >= n || g.parent == i) return APM_E_NESTING;
+        if (gr[g.parent].level != g.level - 1) return APM_E_NESTING;
+        for (int j = 0; j < 3; ++j)
+            if (g.dims[j] < 1) return APM_E_INVALID;
+        maxlev = std::max(maxlev, g.level);
+    }
+    std::vector<int> count(maxlev + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        if (gr[i].level == 0 && i != 0) return APM_E_NESTING;
+        count[gr[i].level]++;
+    }
+    for (int l = 0; l <= maxlev; ++l)
+        if (count[l] == 0) return APM_E_NESTING;
+    const int R = cfg.refine;
+    const int B = border_cells(cfg);
+    for (int i = 1; i < n; ++i) {
+        const apm_grid& g = gr[i];
+        const apm_grid& p = gr[g.parent];
+        for (int j = 0; j < 3; ++j) {
+            // parent cells read by the GMF border (baryons) and by the carry of cells [-1, N]
+            long long lo_b = floor_div(g.start[j] - B, R);
+            long long hi_b = floor_div(g.start[j] + g.dims[j] + B - 1, R);
+            long long lo_c = (long long)std::floor((g.start[j] - 1 + 0.5) / R - 0.5);
+            long long hi_c = (long long)std::floor((g.start[j] + g.dims[j] + 0.5) / R - 0.5) + 1;
+            long long lo = std::min(lo_b, lo_c), hi = std::max(hi_b, hi_c);
+            if (lo < p.start[j] || hi >= p.start[j] + p.dims[j]) return APM_E_NESTING;
+        }
+    }
+    for (int i = 1; i < n; ++i)
+        for (int k = i + 1; k < n; ++k) {
+            if (gr[i].level != gr[k].level) continue;
+            bool overlap = true;
+            for (int j = 0; j < 3; ++j)
+                if (!(gr[i].start[j] < gr[k].start[j] + gr[k].dims[j] &&
+                      gr[k].start[j] < gr[i].start[j] + gr[i].dims[j]))
+                    overlap = false;
+            if (overlap) return APM_E_NESTING;
+        }
+    return APM_OK;
+}
+
+// CSR of the grids whose box [lo, hi) (level cells) meets each tile
+void build_csr(const std::vector<std::pair<std::array<long long, 3>, std::array<long long, 3>>>& boxes,
+               const long long mlo[3], int shift, const int nt[3], std::vector<int>& off,
+               std::vector<int>& list) {
+    long long ntiles = (long long)nt[0] * nt[1] * nt[2];
+    std::vector<std::vector<int>> per(ntiles);
+    for (size_t gi = 0; gi < boxes.size(); ++gi) {
+        long long t0[3], t1[3];
+        bool empty = false;
+        for (int j = 0; j < 3; ++j) {
+            long long a = boxes[gi].first[j] - mlo[j], b = boxes[gi].second[j] - mlo[j] - 1;
+            a = std::max(a, 0LL);
+            b = std::min(b, ((long long)nt[j] << shift) - 1);
+            if (b < a) empty = true;
+            t0[j] = a >> shift;
+            t1[j] = b >> shift;
+        }
+        if (empty) continue;
+        for (long long z = t0[2]; z <= t1[2]; ++z)
+            for (long long y = t0[1]; y <= t1[1]; ++y)
+                for (long long x = t0[0]; x <= t1[0]; ++x)
+                    per[x + nt[0] * (y + (long long)nt[1] * z)].push_back((int)gi);
+    }
+    off.assign(ntiles + 1, 0);
+    list.clear();
+    for (long long t = 0; t < ntiles; ++t) {
+        off[t] = (int)list.size();
+        list.insert(list.end(), per[t].begin(), per[t].end());
+    }
+    off[ntiles] = (int)list.size();
+}
+
+apm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APM_OK : APM_E_CUDA; }
+
+// Uploads the device pointers of one role if they changed since the last call.
+apm_status set_ptrs(apm_ctx* c, Level& L, int role, const void* const* host, int count,
+                    void*** dev_out, cudaStream_t s) {
+    *dev_out = nullptr;
+    if (!host) return APM_OK;
+    if (count > L.cap) return APM_E_INVALID;
+    std::vector<void*>& last = L.last[role];
+    bool same = (int)last.size() == count;
+    for (int i = 0; same && i < count; ++i) same = last[i] == host[i];
+    void** dev = L.d_ptr + (size_t)role * L.cap;
+    if (!same) {
+        if (L.ev_pending) {
+            if (cudaEventSynchronize(L.ev) != cudaSuccess) return APM_E_CUDA;
+            L.ev_pending = false;
+        }
+        void** h = L.h_ptr + (size_t)role * L.cap;
+        for (int i = 0; i < count; ++i) h[i] = const_cast<void*>(host[i]);
+        if (cudaMemcpyAsync(dev, h, count * sizeof(void*), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return APM_E_CUDA;
+        if (cudaEventRecord(L.ev, s) != cudaSuccess) return APM_E_CUDA;
+        L.ev_pending = true;
+        last.resize(count);
+        for (int i = 0; i < count; ++i) last[i] = const_cast<void*>(host[i]);
+    }
+    *dev_out = dev;
+    return APM_OK;
+}
+
+// brackets one launch with events when tracing is on
+struct Trace {
+    apm_ctx* c;
+    int pair = -1;
+    cudaStream_t s;
+    Trace(apm_ctx* ctx, int k, cudaStream_t st) : c(ctx), s(st) {
+        Profiler& P = c->prof;
+        if (!P.on || P.used * 2 + 1 >= (int)P.ev.size()) return;
+        pair = P.used++;
+        P.kind[pair] = k;
+        cudaEventRecord(P.ev[2 * pair], s);
+    }
+    ~Trace() {
+        if (pair >= 0) cudaEventRecord(c->prof.ev[2 * pair + 1], s);
+    }
+};
+
+void profile_free(Profiler& P) {
+    for (cudaEvent_t e : P.ev) cudaEventDestroy(e);
+    P.ev.clear();
+    P.kind.clear();
+    P.used = 0;
+    P.on = false;
+}
+
+Particles to_dev(const apm_particles* p) {
+    Particles q;
+    q.n = p->n;
+    q.x = p->x; q.y = p->y; q.z = p->z;
+    q.vx = p->vx; q.vy = p->vy; q.vz = p->vz;
+    q.m = p->m;
+    return q;
+}
+
+bool particles_ok(const apm_particles* p) {
+    if (!p || p->n < 0) return false;
+    if (p->n == 0) return true;
+    return p->x && p->y && p->z && p->vx && p->vy && p->vz && p->m;
+}
+
+}  // namespace
+
+extern "C" {
+
+void apm_config_default(apm_config* cfg) {
+    if (!cfg) return;
+    cfg->box = 1.0;
+    cfg->a_over_dx = 3.4;
+    cfg->refine = 2;
+    cfg->pad_factor = 0.65;
+    cfg->root_bc = APM_BC_ISOLATED;
+    cfg->precision = APM_FP32;
+    cfg->mass_frac_bits = 52;
+    cfg->root_correction = 1;
+    cfg->device = -1;
+}
+
+const char* apm_version(void) { return "apm-gb300 0.1 (sm_103a)"; }
+
+const char* apm_status_string(apm_status s) {
+    switch (s) {
+        case APM_OK: return "ok";
+        case APM_E_INVALID: return "invalid argument";
+        case APM_E_NESTING: return "hierarchy violates the nesting rules";
+        case APM_E_NOMEM: return "out of memory";
+        case APM_E_CUDA: return "CUDA runtime error";
+        case APM_E_OVERFLOW: return "fixed-point overflow (particle skipped)";
+        case APM_E_OUT_OF_BOX: return "particle outside the isolated root (folded)";
+        case APM_E_TIMEOUT: return "device wait ran out";
+        case APM_E_UNSUPPORTED: return "unsupported request";
+        case APM_E_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+apm_status apm_create(const apm_config* cfg, apm_ctx** out) {
+    if (!cfg || !out) return APM_E_INVALID;
+    *out = nullptr;
+    if (!(cfg->box > 0) || !(cfg->a_over_dx > 0) || cfg->refine < 2 || !(cfg->pad_factor >= 0) ||
+        (cfg->root_bc != APM_BC_ISOLATED && cfg->root_bc != APM_BC_PERIODIC) ||
+        (cfg->precision != APM_FP32 && cfg->precision != APM_FP64) || cfg->mass_frac_bits < 1 ||
+        cfg->mass_frac_bits > 62)
+        return APM_E_INVALID;
+    if (cfg->refine != 2) return APM_E_UNSUPPORTED;
+    apm_ctx* c = new apm_ctx();
+    c->cfg = *cfg;
+    if (cfg->device >= 0 && cudaSetDevice(cfg->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return APM_E_CUDA;
+    }
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return APM_E_CUDA;
+    }
+    if (fault_alloc() || cudaMalloc((void**)&c->d_status, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fault_alloc() ? APM_E_NOMEM : APM_E_CUDA;
+    }
+    if (cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess || fft_configure() != cudaSuccess) {
+        cudaFree(c->d_status);
+        cudaGetLastError();
+        delete c;
+        return APM_E_CUDA;
+    }
+    *out = c;
+    return APM_OK;
+}
+
+void apm_destroy(apm_ctx* c) {
+    if (!c) return;
+    free_hierarchy(c);
+    profile_free(c->prof);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+}
+
+apm_status apm_validate_hierarchy(const apm_config* cfg, const apm_grid* grids, int32_t n) {
+    if (!cfg || !grids || cfg->refine != 2 || !(cfg->pad_factor >= 0) || !(cfg->a_over_dx > 0))
+        return APM_E_INVALID;
+    return validate(*cfg, grids, n);
+}
+
+int32_t apm_num_levels(const apm_ctx* c) { return (c && c->has_hier) ? (int32_t)c->levels.size() : 0; }
+
+apm_status apm_get_grid_info(const apm_ctx* c, int32_t grid, apm_grid_info* out) {
+    if (!c || !out) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (grid < 0 || grid >= (int)c->grids.size()) return APM_E_INVALID;
+    const Level& L = c->levels[c->level_of[grid]];
+    const GridDev& g = L.hg[c->index_in_level[grid]];
+    out->level = L.level;
+    out->border = (g.G[0] - g.N[0]) / 2;
+    for (int j = 0; j < 3; ++j) {
+        out->gmf[j] = g.G[j];
+        out->fft[j] = g.M[j];
+        out->phi_short[j] = g.W[j];
+        out->field[j] = g.N[j] + 2;
+    }
+    out->level_index = c->index_in_level[grid];
+    out->delta = g.delta;
+    return APM_OK;
+}
+
+apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
+    if (!c || !grids) return APM_E_INVALID;
+    apm_status st = validate(c->cfg, grids, n);
+    if (st != APM_OK) return st;
+    if (c->has_hier) free_hierarchy(c);
+    const apm_config& cfg = c->cfg;
+    const bool periodic = cfg.root_bc == APM_BC_PERIODIC;
+    const bool f64 = cfg.precision == APM_FP64;
+    const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
+    const int B = border_cells(cfg);
+    const int N0 = grids[0].dims[0];
+    c->grids.assign(grids, grids + n);
+    int nlev = 0;
+    for (int i = 0; i < n; ++i) nlev = std::max(nlev, grids[i].level + 1);
+    c->levels.assign(nlev, Level());
+    c->level_of.assign(n, 0);
+    c->index_in_level.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        Level& L = c->levels[grids[i].level];
+        L.level = grids[i].level;
+        c->level_of[i] = grids[i].level;
+        c->index_in_level[i] = (int)L.grids.size();
+        L.grids.push_back(i);
+    }
+    // ---- per-grid plans
+    std::map<int, int> tw_off;       // L -> offset
+    int tw_total = 0;
+    using TabKey = std::tuple<int, int, int, int, double, double, double>;
+    std::map<TabKey, long long> tab_off;
+    std::vector<std::pair<TabKey, long long>> tab_list;
+    long long tab_total = 0, tab_max = 0;
+    auto twiddle = [&](int L) {
+        auto it = tw_off.find(L);
+        if (it != tw_off.end()) return it->second;
+        int o = tw_total;
+        tw_off[L] = o;
+        tw_total += L;
+        return o;
+    };
+    size_t wsA_max = 0, wsB_max = 0;
+    for (Level& L : c->levels) {
+        long long offA = 0, offB = 0;
+        for (int gi : L.grids) {
+            const apm_grid& a = grids[gi];
+            GridDev g;
+            std::memset(&g, 0, sizeof(g));
+            const double delta = cfg.box / ((double)N0 * std::pow((double)cfg.refine, a.level));
+            const double a_lev = cfg.a_over_dx * delta;
+            g.delta = delta;
+            for (int j = 0; j < 3; ++j) {
+                g.N[j] = a.dims[j];
+                g.start[j] = a.start[j];
+                g.W[j] = a.dims[j] + 4;
+            }
+            double a_par = 0.0;
+            if (a.level == 0) {
+                g.kind = periodic ? 1 : 2;
+                g.mode = periodic ? 2 : 1;
+                for (int j = 0; j < 3; ++j) {
+                    g.G[j] = a.dims[j];
+                    g.M[j] = periodic ? a.dims[j] : 2 * a.dims[j];
+                    g.lo[j] = 0;
+                    g.s0[j] = g.M[j] - 2;
+                }
+                g.parent = -1;
+            } else {
+                g.kind = 0;
+                g.mode = 0;
+                a_par = cfg.refine * a_lev;
+                for (int j = 0; j < 3; ++j) {
+                    g.G[j] = a.dims[j] + 2 * B;
+                    g.M[j] = smooth7_at_least(a.dims[j] + 4 * B);
+                    g.lo[j] = a.start[j] - B;
+                    g.s0[j] = B - 2;
+                }
+                const apm_grid& p = grids[a.parent];
+                g.parent = c->index_in_level[a.parent];
+                for (int j = 0; j < 3; ++j) {
+                    g.pN[j] = p.dims[j];
+                    g.pstart[j] = p.start[j];
+                }
+            }
+            for (int j = 0; j < 3; ++j) {
+                if (g.M[j] > kMaxFft || g.M[j] < 2) return APM_E_UNSUPPORTED;
+            }
+            FftPlan1D* pls[3] = {&g.fx, &g.fy, &g.fz};
+            for (int j = 0; j < 3; ++j) {
+                if (!make_plan(g.M[j], pls[j])) return APM_E_UNSUPPORTED;
+                pls[j]->tw_off = twiddle(g.M[j]);
+            }
+            g.Hx = g.M[0] / 2 + 1;
+            g.Hy2 = g.M[1] / 2 + 1;
+            g.Hz2 = g.M[2] / 2 + 1;
+            g.cells_gmf = (long long)g.G[0] * g.G[1] * g.G[2];
+            const int budget = f64 ? kFftBudgetF64 : kFftBudgetF32;
+            g.np_x = std::max(1, budget / g.M[0]);
+            g.tx_y = std::min(32, pow2_floor(std::max(1, budget / g.M[1])));
+            g.tx_z = std::min(32, pow2_floor(std::max(1, budget / g.M[2])));
+            // green table (cached per shape and level parameters)
+            TabKey key{g.kind, g.M[0], g.M[1], g.M[2], delta, a_lev, a_par};
+            auto it = tab_off.find(key);
+            if (it == tab_off.end()) {
+                long long sz = (long long)g.Hx * g.Hy2 * g.Hz2;
+                tab_off[key] = tab_total;
+                tab_list.push_back({key, tab_total});
+                g.tab_off = tab_total;
+                tab_total += sz;
+                tab_max = std::max(tab_max, sz);
+            } else {
+                g.tab_off = it->second;
+            }
+            // workspace
+            const long long Hx = g.Hx;
+            long long szA = std::max((long long)g.G[1] * g.G[2], (long long)g.W[2] * g.M[1]) * Hx;
+            long long szB = std::max((long long)g.G[2] * g.M[1], (long long)g.W[2] * g.W[1]) * Hx;
+            g.wsA = offA;
+            g.wsB = offB;
+            offA += (szA + 31) / 32 * 32;
+            offB += (szB + 31) / 32 * 32;
+            L.hg.push_back(g);
+        }
+        wsA_max = std::max(wsA_max, (size_t)offA);
+        wsB_max = std::max(wsB_max, (size_t)offB);
+    }
+    // ---- device arenas
+    if ((st = dmalloc(c, (void**)&c->tw64, tw_total * sizeof(double2))) != APM_OK) return st;
+    if ((st = dmalloc(c, (void**)&c->tw32, tw_total * sizeof(float2))) != APM_OK) return st;
+    if ((st = dmalloc(c, (void**)&c->tab64, tab_total * sizeof(double))) != APM_OK) return st;
+    if (!f64 && (st = dmalloc(c, (void**)&c->tab32, tab_total * sizeof(float))) != APM_OK) return st;
+    if ((st = dmalloc(c, &c->wsA, wsA_max * csz)) != APM_OK) return st;
+    if ((st = dmalloc(c, &c->wsB, wsB_max * csz)) != APM_OK) return st;
+    double* scratch = nullptr;
+    if ((st = dmalloc(c, (void**)&scratch, tab_max * sizeof(double))) != APM_OK) return st;
+    for (auto& kv : tw_off)
+        if (launch_twiddles(c->tw64 + kv.second, c->tw32 + kv.second, kv.first, 0) != cudaSuccess)
+            return APM_E_CUDA;
+    for (auto& t : tab_list) {
+        const TabKey& k = t.first;
+        int M[3] = {std::get<1>(k), std::get<2>(k), std::get<3>(k)};
+        if (launch_green_table(std::get<0>(k), M, std::get<4>(k), std::get<5>(k), std::get<6>(k),
+                               cfg.root_correction, c->tab64 + t.second, scratch, 0) != cudaSuccess)
+            return APM_E_CUDA;
+    }
+    if (!f64 && launch_to_f32(c->tab64, c->tab32, tab_total, 0) != cudaSuccess) return APM_E_CUDA;
+    // ---- per-level device data
+    for (Level& L : c->levels) {
+        const int ng = (int)L.grids.size();
+        if ((st = upload(c, &L.d_grids, L.hg)) != APM_OK) return st;
+        std::vector<Chunk> xf, yf, zc, yi, xi, gas, acc;
+        size_t sxf = 0, syf = 0, sz = 0;
+        for (int k = 0; k < ng; ++k) {
+            const GridDev& g = L.hg[k];
+            long long pairs = ((long long)g.G[1] * g.G[2] + 1) / 2;
+            for (long long t = 0; t < (pairs + g.np_x - 1) / g.np_x; ++t) xf.push_back({k, (int)t});
+            int nky = (g.Hx + g.tx_y - 1) / g.tx_y, nkz = (g.Hx + g.tx_z - 1) / g.tx_z;
+            for (int t = 0; t < nky * g.G[2]; ++t) yf.push_back({k, t});
+            for (int t = 0; t < nkz * g.M[1]; ++t) zc.push_back({k, t});
+            for (int t = 0; t < nky * g.W[2]; ++t) yi.push_back({k, t});
+            long long pairs_o = ((long long)g.W[1] * g.W[2] + 1) / 2;
+            for (long long t = 0; t < (pairs_o + g.np_x - 1) / g.np_x; ++t) xi.push_back({k, (int)t});
+            for (long long t = 0; t < (g.cells_gmf + kChunkCells - 1) / kChunkCells; ++t) gas.push_back({k, (int)t});
+            long long ec = (long long)(g.N[0] + 2) * (g.N[1] + 2) * (g.N[2] + 2);
+            for (long long t = 0; t < (ec + kChunkCells - 1) / kChunkCells; ++t) acc.push_back({k, (int)t});
+            sxf = std::max(sxf, (size_t)g.np_x * g.M[0]);
+            syf = std::max(syf, (size_t)g.M[1] * g.tx_y);
+            sz = std::max(sz, (size_t)g.M[2] * g.tx_z);
+        }
+        // two buffers per CTA; the second starts at the fixed budget offset
+        const size_t bud = (size_t)(f64 ? kFftBudgetF64 : kFftBudgetF32);
+        (void)sxf; (void)syf; (void)sz;
+        L.smem_xf = L.smem_xi = L.smem_yf = L.smem_yi = L.smem_z = 2 * bud * csz;
+        if ((st = upload(c, &L.d_xf, xf)) != APM_OK) return st;
+        if ((st = upload(c, &L.d_yf, yf)) != APM_OK) return st;
+        if ((st = upload(c, &L.d_z, zc)) != APM_OK) return st;
+        if ((st = upload(c, &L.d_yi, yi)) != APM_OK) return st;
+        if ((st = upload(c, &L.d_xi, xi)) != APM_OK) return st;
+        if ((st = upload(c, &L.d_gas, gas)) != APM_OK) return st;
+        if ((st = upload(c, &L.d_acc, acc)) != APM_OK) return st;
+        L.n_xf = (int)xf.size(); L.n_yf = (int)yf.size(); L.n_z = (int)zc.size();
+        L.n_yi = (int)yi.size(); L.n_xi = (int)xi.size(); L.n_gas = (int)gas.size(); L.n_acc = (int)acc.size();
+        // tile map
+        LevelDev& D = L.dev;
+        std::memset(&D, 0, sizeof(D));
+        D.level = L.level;
+        D.n = ng;
+        D.is_root = L.level == 0;
+        D.refine = cfg.refine;
+        D.g = L.d_grids;
+        D.delta = L.hg[0].delta;
+        D.inv_delta = 1.0 / D.delta;
+        {
+            int ex = 0;
+            double fr = std::frexp(D.delta, &ex);
+            D.delta_pow2 = fr == 0.5 ? 1 : 0;
+            D.cull_fp32 = (cfg.box * D.inv_delta) < 4194304.0 ? 1 : 0;
+        }
+        if (L.level > 0) {
+            std::vector<std::pair<std::array<long long, 3>, std::array<long long, 3>>> dep, own;
+            long long lo[3] = {1LL << 62, 1LL << 62, 1LL << 62}, hi[3] = {-(1LL << 62), -(1LL << 62), -(1LL << 62)};
+            for (const GridDev& g : L.hg) {
+                std::array<long long, 3> a, b, ia, ib;
+                for (int j = 0; j < 3; ++j) {
+                    a[j] = g.lo[j] - 1;
+                    b[j] = g.lo[j] + g.G[j] + 1;
+                    ia[j] = g.start[j];
+                    ib[j] = g.start[j] + g.N[j];
+                    lo[j] = std::min(lo[j], a[j]);
+                    hi[j] = std::max(hi[j], b[j]);
+                }
+                dep.push_back({a, b});
+                own.push_back({ia, ib});
+            }
+            long long ext = 0;
+            for (int j = 0; j < 3; ++j) ext = std::max(ext, hi[j] - lo[j]);
+            int shift = 2;   // tiles of at least 4 cells (the FP32 culling below relies on it)
+            while ((ext >> shift) > 64) ++shift;
+            int nt[3];
+            for (int j = 0; j < 3; ++j) nt[j] = (int)(((hi[j] - lo[j]) + (1LL << shift) - 1) >> shift);
+            std::vector<int> doff, dlist, ooff, olist;
+            build_csr(dep, lo, shift, nt, doff, dlist);
+            build_csr(own, lo, shift, nt, ooff, olist);
+            // dilated occupancy: a particle whose FP32-estimated tile has no
+            // occupied neighbour cannot touch any GMF box of the level
+            std::vector<unsigned char> occ((size_t)nt[0] * nt[1] * nt[2], 0);
+            for (int z = 0; z < nt[2]; ++z)
+                for (int y = 0; y < nt[1]; ++y)
+                    for (int x = 0; x < nt[0]; ++x) {
+                        long long t = x + (long long)nt[0] * (y + (long long)nt[1] * z);
+                        if (doff[t + 1] == doff[t]) continue;
+                        for (int dz = -1; dz <= 1; ++dz)
+                            for (int dy = -1; dy <= 1; ++dy)
+                                for (int dx = -1; dx <= 1; ++dx) {
+                                    int X = x + dx, Y = y + dy, Z = z + dz;
+                                    if (X < 0 || Y < 0 || Z < 0 || X >= nt[0] || Y >= nt[1] || Z >= nt[2]) continue;
+                                    occ[X + (size_t)nt[0] * (Y + (size_t)nt[1] * Z)] = 1;
+                                }
+                    }
+            unsigned char* d_occ;
+            if ((st = upload(c, &d_occ, occ)) != APM_OK) return st;
+            D.map.occ = d_occ;
+            int *d_doff, *d_dlist, *d_ooff, *d_olist;
+            if ((st = upload(c, &d_doff, doff)) != APM_OK) return st;
+            if ((st = upload(c, &d_dlist, dlist)) != APM_OK) return st;
+            if ((st = upload(c, &d_ooff, ooff)) != APM_OK) return st;
+            if ((st = upload(c, &d_olist, olist)) != APM_OK) return st;
+            for (int j = 0; j < 3; ++j) {
+                D.map.lo[j] = lo[j];
+                D.map.nt[j] = nt[j];
+            }
+            D.map.shift = shift;
+            D.map.dep_off = d_doff; D.map.dep_list = d_dlist;
+            D.map.own_off = d_ooff; D.map.own_list = d_olist;
+        }
+        // pointer tables
+        int cap = ng;
+        if (L.level > 0) cap = std::max(cap, (int)c->levels[L.level - 1].grids.size());
+        L.cap = cap;
+        if ((st = dmalloc(c, (void**)&L.d_ptr, (size_t)kRoles * cap * sizeof(void*))) != APM_OK) return st;
+        if (cudaMallocHost((void**)&L.h_ptr, (size_t)kRoles * cap * sizeof(void*)) != cudaSuccess) {
+            L.h_ptr = nullptr;
+            cudaGetLastError();
+            return APM_E_NOMEM;
+        }
+        if (cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess) return APM_E_CUDA;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return APM_E_CUDA;
+    c->has_hier = true;
+    return APM_OK;
+}
+
+apm_status apm_deposit(apm_ctx* c, int32_t level, const apm_particles* particles, double half_dt,
+                       const double* const* gas, const double* const* parent_gas,
+                       int64_t* const* gmf, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size() || !gmf || !particles_ok(particles))
+        return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Level& L = c->levels[level];
+    const int ng = (int)L.grids.size();
+    for (int i = 0; i < ng; ++i)
+        if (!gmf[i]) return APM_E_INVALID;
+    void **d_gmf, **d_gas, **d_pgas;
+    apm_status st;
+    if ((st = set_ptrs(c, L, R_GMF, (const void* const*)gmf, ng, &d_gmf, s)) != APM_OK) return st;
+    if ((st = set_ptrs(c, L, R_GAS, (const void* const*)gas, ng, &d_gas, s)) != APM_OK) return st;
+    const GridDev* pgrids = nullptr;
+    if (level > 0 && parent_gas) {
+        Level& P = c->levels[level - 1];
+        if ((st = set_ptrs(c, L, R_PGAS, (const void* const*)parent_gas, (int)P.grids.size(), &d_pgas, s)) != APM_OK)
+            return st;
+        pgrids = P.d_grids;
+    } else {
+        d_pgas = nullptr;
+    }
+    {
+    Trace t(c, K_GAS, s);
+    if (launch_gas_init(L.dev, pgrids, (const double* const*)d_gas, (const double* const*)d_pgas,
+                        (int64_t* const*)d_gmf, L.d_gas, L.n_gas, kChunkCells, c->cfg.mass_frac_bits,
+                        s) != cudaSuccess)
+        return APM_E_CUDA;
+    }
+    Particles P = to_dev(particles);
+    Trace t(c, K_DEPOSIT, s);
+    return cuda_status(launch_deposit(L.dev, P, half_dt, c->cfg.box, c->cfg.root_bc == APM_BC_PERIODIC,
+                                      c->cfg.mass_frac_bits, (int64_t* const*)d_gmf, c->d_status, s));
+}
+
+apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
+                           void* const* phi_short, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size() || !gmf || !phi_short) return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Level& L = c->levels[level];
+    const int ng = (int)L.grids.size();
+    for (int i = 0; i < ng; ++i)
+        if (!gmf[i] || !phi_short[i]) return APM_E_INVALID;
+    void **d_gmf, **d_phis;
+    apm_status st;
+    if ((st = set_ptrs(c, L, R_GMF_IN, (const void* const*)gmf, ng, &d_gmf, s)) != APM_OK) return st;
+    if ((st = set_ptrs(c, L, R_PHIS, (const void* const*)phi_short, ng, &d_phis, s)) != APM_OK) return st;
+    const bool f64 = c->cfg.precision == APM_FP64;
+    FftArgs a;
+    a.g = L.d_grids;
+    a.tw = f64 ? (const void*)c->tw64 : (const void*)c->tw32;
+    a.tab = f64 ? (const void*)c->tab64 : (const void*)c->tab32;
+    a.wsA = c->wsA;
+    a.wsB = c->wsB;
+    a.F = c->cfg.mass_frac_bits;
+    cudaError_t e;
+    a.chunks = L.d_xf; a.n_chunks = L.n_xf; a.smem = L.smem_xf;
+    { Trace t(c, K_XF, s);
+    e = f64 ? launch_fft_xf<double>(a, (const int64_t* const*)d_gmf, s)
+            : launch_fft_xf<float>(a, (const int64_t* const*)d_gmf, s); }
+    if (e != cudaSuccess) return APM_E_CUDA;
+    a.chunks = L.d_yf; a.n_chunks = L.n_yf; a.smem = L.smem_yf;
+    { Trace t(c, K_YF, s); e = f64 ? launch_fft_yf<double>(a, s) : launch_fft_yf<float>(a, s); }
+    if (e != cudaSuccess) return APM_E_CUDA;
+    a.chunks = L.d_z; a.n_chunks = L.n_z; a.smem = L.smem_z;
+    { Trace t(c, K_Z, s); e = f64 ? launch_fft_z<double>(a, s) : launch_fft_z<float>(a, s); }
+    if (e != cudaSuccess) return APM_E_CUDA;
+    a.chunks = L.d_yi; a.n_chunks = L.n_yi; a.smem = L.smem_yi;
+    { Trace t(c, K_YI, s); e = f64 ? launch_fft_yi<double>(a, s) : launch_fft_yi<float>(a, s); }
+    if (e != cudaSuccess) return APM_E_CUDA;
+    a.chunks = L.d_xi; a.n_chunks = L.n_xi; a.smem = L.smem_xi;
+    { Trace t(c, K_XI, s); e = f64 ? launch_fft_xi<double>(a, d_phis, s) : launch_fft_xi<float>(a, d_phis, s); }
+    return cuda_status(e);
+}
+
+apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,
+                     const void* const* parent_phi, const void* const* parent_acc, void* const* phi,
+                     void* const* acc, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size() || !phi_short || !phi || !acc) return APM_E_INVALID;
+    if ((parent_phi == nullptr) != (parent_acc == nullptr)) return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Level& L = c->levels[level];
+    const int ng = (int)L.grids.size();
+    void **d_phis, **d_pphi = nullptr, **d_pacc = nullptr, **d_phi, **d_acc;
+    apm_status st;
+    if ((st = set_ptrs(c, L, R_PHIS_IN, phi_short, ng, &d_phis, s)) != APM_OK) return st;
+    if ((st = set_ptrs(c, L, R_PHI, (const void* const*)phi, ng, &d_phi, s)) != APM_OK) return st;
+    if ((st = set_ptrs(c, L, R_ACC, (const void* const*)acc, ng, &d_acc, s)) != APM_OK) return st;
+    const GridDev* pgrids = nullptr;
+    if (parent_phi && level > 0) {
+        Level& P = c->levels[level - 1];
+        int np = (int)P.grids.size();
+        if ((st = set_ptrs(c, L, R_PPHI, parent_phi, np, &d_pphi, s)) != APM_OK) return st;
+        if ((st = set_ptrs(c, L, R_PACC, parent_acc, np, &d_pacc, s)) != APM_OK) return st;
+        pgrids = P.d_grids;
+    }
+    Trace t(c, K_ACCEL, s);
+    cudaError_t e = c->cfg.precision == APM_FP64
+        ? launch_accel<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                               (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, kChunkCells, s)
+        : launch_accel<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                              (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, kChunkCells, s);
+    return cuda_status(e);
+}
+
+apm_status apm_interp(apm_ctx* c, int32_t level, const void* const* acc,
+                      const apm_particles* particles, double half_dt, void* acc_out, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size() || !acc || !particles_ok(particles) ||
+        (!acc_out && particles->n > 0))
+        return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    Level& L = c->levels[level];
+    void** d_acc;
+    apm_status st;
+    if ((st = set_ptrs(c, L, R_ACC_IN, acc, (int)L.grids.size(), &d_acc, s)) != APM_OK) return st;
+    const LevelDev* finer = level + 1 < (int)c->levels.size() ? &c->levels[level + 1].dev : nullptr;
+    Particles P = to_dev(particles);
+    const int periodic = c->cfg.root_bc == APM_BC_PERIODIC;
+    Trace t(c, K_INTERP, s);
+    cudaError_t e = c->cfg.precision == APM_FP64
+        ? launch_interp<double>(L.dev, finer, P, half_dt, c->cfg.box, periodic, (const void* const*)d_acc, acc_out, s)
+        : launch_interp<float>(L.dev, finer, P, half_dt, c->cfg.box, periodic, (const void* const*)d_acc, acc_out, s);
+    return cuda_status(e);
+}
+
+int32_t apm_kernel_count(void) { return K_COUNT; }
+
+const char* apm_kernel_name(int32_t k) { return (k >= 0 && k < K_COUNT) ? kKernelNames[k] : nullptr; }
+
+apm_status apm_profile_enable(apm_ctx* c, int32_t on, int32_t capacity) {
+    if (!c) return APM_E_INVALID;
+    cudaDeviceSynchronize();
+    profile_free(c->prof);
+    Profiler& P = c->prof;
+    for (int k = 0; k < K_COUNT; ++k) {
+        P.launches[k] = 0;
+        P.ms[k] = 0.0;
+    }
+    if (!on) return APM_OK;
+    if (capacity < 1) return APM_E_INVALID;
+    P.ev.resize(2 * (size_t)capacity);
+    P.kind.assign(capacity, 0);
+    for (cudaEvent_t& e : P.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+            profile_free(P);
+            return APM_E_CUDA;
+        }
+    P.on = true;
+    return APM_OK;
+}
+
+apm_status apm_profile_read(apm_ctx* c, int32_t kernel, int64_t* launches, double* total_ms) {
+    if (!c || kernel < 0 || kernel >= K_COUNT || !launches || !total_ms) return APM_E_INVALID;
+    Profiler& P = c->prof;
+    if (P.used > 0) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return APM_E_CUDA;
+        for (int i = 0; i < P.used; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            P.launches[P.kind[i]] += 1;
+            P.ms[P.kind[i]] += ms;
+        }
+        P.used = 0;
+    }
+    *launches = P.launches[kernel];
+    *total_ms = P.ms[kernel];
+    return APM_OK;
+}
+
+apm_status apm_sync_status(apm_ctx* c, void* stream) {
+    if (!c) return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return APM_E_CUDA;
+    unsigned h = 0;
+    if (cudaMemcpy(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return APM_E_CUDA;
+    if (h && cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) return APM_E_CUDA;
+    if (h & kStOverflow) return APM_E_OVERFLOW;
+    if (h & kStOutOfBox) return APM_E_OUT_OF_BOX;
+    if (h & kStTimeout) return APM_E_TIMEOUT;
+    return APM_OK;
+}
+
+}  // extern "C"

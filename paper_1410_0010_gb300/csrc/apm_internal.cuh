@@ -1,0 +1,154 @@
+// apm_internal.cuh -- device descriptors and kernel entry points shared by the
+// translation units of libapm (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apm.h"
+
+namespace apm {
+
+// ---------------------------------------------------------------------------
+// compile-time sizes
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 12;      // radix stages of one 1-D transform
+constexpr int kFftThreads = 256;    // threads of every FFT pass CTA
+// complex elements of each of the two shared-memory buffers of a pass CTA
+// (lines per CTA x line length); 64 KB of shared memory per CTA either way
+constexpr int kFftBudgetF32 = 4096;
+constexpr int kFftBudgetF64 = 2048;
+constexpr int kMaxFft = 1024;       // longest supported transform
+
+// device status bits (latched with atomicOr, read by apm_sync_status)
+constexpr unsigned kStOverflow = 1u;
+constexpr unsigned kStOutOfBox = 2u;
+constexpr unsigned kStTimeout = 4u;
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// One mixed-radix 1-D transform of length L (Stockham, radices in order).
+struct FftPlan1D {
+    int L;
+    int nst;
+    int tw_off;                       // offset of exp(-2 pi i t/L), t < L, in the twiddle arenas
+    unsigned char radix[kMaxStages];
+};
+
+// Everything a kernel needs to know about one grid.
+struct GridDev {
+    int kind;            // Green's table: 0 refined, 1 periodic root, 2 isolated root
+    int mode;            // deposit edge rule: 0 drop, 1 fold, 2 wrap
+    int N[3];            // interior cells
+    int G[3];            // GMF box
+    int M[3];            // FFT lengths
+    int W[3];            // window N + 4 (cells [-2, N+2))
+    int s0[3];           // M index of window cell -2, in [0, M)
+    int Hx;              // M[0]/2 + 1 (half spectrum along x)
+    int Hy2, Hz2;        // M[1]/2 + 1, M[2]/2 + 1 (octant table)
+    long long lo[3];     // global level index of GMF cell 0
+    long long start[3];  // global level index of interior cell 0
+    int parent;          // index of the parent among the grids of level - 1, or -1
+    int pN[3];
+    long long pstart[3];
+    double delta;
+    FftPlan1D fx, fy, fz;
+    long long tab_off;   // octant table offset (elements) in the table arenas
+    long long wsA, wsB;  // workspace offsets (complex elements)
+    long long cells_gmf; // G0 G1 G2
+    int np_x;            // row pairs per CTA of the x passes
+    int tx_y, tx_z;      // kx lines per CTA of the y / z passes
+};
+
+// Tile lookup: level cell -> candidate grids (CSR per tile).
+struct TileMap {
+    long long lo[3];
+    int shift;
+    int nt[3];
+    const int* dep_off;   // grids whose GMF box, grown by one cell, meets the tile
+    const int* dep_list;
+    const int* own_off;   // grids whose interior meets the tile
+    const int* own_list;
+    const unsigned char* occ;  // 1 if the tile or one of its 26 neighbours has a dep entry
+};
+
+struct Chunk { int grid; int tile; };   // one CTA of a batched pass
+
+// Per-level device view (passed by value to kernels).
+struct LevelDev {
+    int level;
+    int n;                 // grids on the level
+    int is_root;
+    int refine;
+    const GridDev* g;      // n descriptors
+    TileMap map;
+    double delta;
+    double inv_delta;      // 1/delta
+    int delta_pow2;        // delta is a power of two: x/delta == x*inv_delta exactly
+    int cull_fp32;         // level narrower than 2^22 cells: FP32 tile estimates are safe
+};
+
+struct Particles {
+    long long n;
+    const double *x, *y, *z, *vx, *vy, *vz, *m;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each returns the launch error)
+// ---------------------------------------------------------------------------
+// twiddles exp(-2 pi i t / L) for t < L, FP64 and FP32
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, int L, cudaStream_t s);
+
+// Green's tables (FP64 octant), kind 0/1 directly, kind 2 from the real-space kernel
+cudaError_t launch_green_table(int kind, const int M[3], double delta, double a_lev,
+                               double a_par, int correction, double* out, double* scratch,
+                               cudaStream_t s);
+cudaError_t launch_to_f32(const double* in, float* out, long long n, cudaStream_t s);
+
+// GMF: baryons (initialises every cell) then particles
+cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
+                            const double* const* gas, const double* const* pgas,
+                            int64_t* const* gmf, const Chunk* chunks, int n_chunks, int chunk_cells,
+                            int F, cudaStream_t s);
+cudaError_t launch_deposit(const LevelDev& L, const Particles& P, double half_dt, double box,
+                           int periodic, int F, int64_t* const* gmf, unsigned* status,
+                           cudaStream_t s);
+
+// FFT passes of one level (T = float or double)
+struct FftArgs {
+    const GridDev* g;
+    const Chunk* chunks;
+    int n_chunks;
+    const void* tw;        // complex twiddle arena of the precision
+    const void* tab;       // table arena of the precision
+    void* wsA;
+    void* wsB;
+    int F;
+    size_t smem;
+};
+cudaError_t fft_configure();
+template <typename T>
+cudaError_t launch_fft_xf(const FftArgs& a, const int64_t* const* gmf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_yf(const FftArgs& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_z(const FftArgs& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_yi(const FftArgs& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
+
+// FD accelerations + parent carry; TSC interpolation
+template <typename T>
+cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
+                         const void* const* pphi, const void* const* pacc, void* const* phi,
+                         void* const* acc, const Chunk* chunks, int n_chunks, int chunk_cells,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_interp(const LevelDev& L, const LevelDev* finer, const Particles& P,
+                          double half_dt, double box, int periodic, const void* const* acc,
+                          void* out, cudaStream_t s);
+
+}  // namespace apm

@@ -1,0 +1,294 @@
+// k_field.cu -- cell accelerations with the parent carry, and TSC interpolation
+// of the accelerations back to the particles (Sec. 2.2, Sec. 2).
+#include "apm_internal.cuh"
+
+namespace apm {
+namespace {
+
+// Error-free transformations on the FP32 units (Knuth TwoSum, FMA TwoProd):
+// a compensated sum of FP32 terms carries the rounding error of every step, so
+// hi + lo equals the FP64 evaluation of the same sum to within a few units of
+// 2^-48 relative, and rounding it once gives the FP64 result rounded to FP32.
+struct FF {
+    float hi, lo;
+};
+// (explicitly rounded intrinsics: the compiler may not contract them)
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+    float s = __fadd_rn(a.hi, b);
+    float bb = __fsub_rn(s, a.hi);
+    float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return FF{s, __fadd_rn(a.lo, err)};
+}
+__device__ __forceinline__ FF ff_fma(FF a, float w, float v) {   // a + w v
+    float p = __fmul_rn(w, v);
+    float pe = __fmaf_rn(w, v, -p);
+    FF r = ff_add(a, p);
+    r.lo = __fadd_rn(r.lo, pe);
+    return r;
+}
+
+// Trilinear weights of child cell ic from the parent cell centres, R = 2: in
+// parent units the child centre is at (ic + 1/2)/2, i.e. 3/4 (even ic) or 1/4
+// (odd ic) of a cell above the centre of parent cell i0 = floor((ic - 1) / 2),
+// so i0 weighs 1/4 for even ic and 3/4 for odd ic (i0 + 1 the rest).
+__device__ __forceinline__ void carry_axis(long long ic, long long pstart, int& i0, float& w_lo) {
+    long long a = (ic - 1) >> 1;          // floor((ic - 1) / 2)
+    i0 = (int)(a - pstart) + 1;           // +1: parent ghost offset
+    w_lo = (ic & 1) ? 0.75f : 0.25f;
+}
+
+// acc_j(c) = -(phis(c+e_j) - phis(c-e_j)) / (2 delta) + I(parent acc_j)(c)
+// phi(c)   = phis(c) + I(parent phi)(c),    c in [-1, N]^3
+// The difference is taken in T.  The carry is the trilinear interpolation from
+// the parent cell centres with exact weights (1/4, 3/4); its sum (and the
+// addition of the short-range part) is carried out in FP64 arithmetic: natively
+// for T = double, as compensated FP32 (same result, rounded once) for T = float.
+template <typename T>
+__global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __restrict__ pgrids,
+                                               const void* const* __restrict__ phis_p,
+                                               const void* const* __restrict__ pphi_p,
+                                               const void* const* __restrict__ pacc_p,
+                                               void* const* __restrict__ phi_p,
+                                               void* const* __restrict__ acc_p,
+                                               const Chunk* __restrict__ chunks, int chunk_cells) {
+    const Chunk ch = chunks[blockIdx.x];
+    const GridDev& g = L.g[ch.grid];
+    const unsigned E0 = g.N[0] + 2, E1 = g.N[1] + 2, E2 = g.N[2] + 2;
+    const unsigned ncell = E0 * E1 * E2;
+    const int W0 = g.W[0], W1 = g.W[1];
+    const T* __restrict__ phis = reinterpret_cast<const T*>(phis_p[ch.grid]);
+    T* __restrict__ phi = reinterpret_cast<T*>(phi_p[ch.grid]);
+    T* __restrict__ acc = reinterpret_cast<T*>(acc_p[ch.grid]);
+    const bool carry = pphi_p != nullptr && g.parent >= 0;
+    const T* __restrict__ pphi = carry ? reinterpret_cast<const T*>(pphi_p[g.parent]) : nullptr;
+    const T* __restrict__ pacc = carry ? reinterpret_cast<const T*>(pacc_p[g.parent]) : nullptr;
+    int P0 = 0, P1 = 0;
+    unsigned pn = 0;
+    long long ps0 = 0, ps1 = 0, ps2 = 0;
+    if (carry) {
+        const GridDev& p = pgrids[g.parent];
+        P0 = p.N[0] + 2;
+        P1 = p.N[1] + 2;
+        pn = (unsigned)P0 * P1 * (p.N[2] + 2);
+        ps0 = p.start[0]; ps1 = p.start[1]; ps2 = p.start[2];
+    }
+    const T inv2d = (T)(0.5 / g.delta);
+    const unsigned cell0 = (unsigned)ch.tile * chunk_cells;
+    for (int t = threadIdx.x; t < chunk_cells; t += blockDim.x) {
+        unsigned o = cell0 + t;
+        if (o >= ncell) break;
+        unsigned ex = o % E0;
+        unsigned r = o / E0;
+        unsigned ey = r % E1;
+        unsigned ez = r / E1;
+        // phis index of cell (ex-1, ey-1, ez-1): offset +2 in [-2, N+2)
+        unsigned ps = (ex + 1) + W0 * ((ey + 1) + W1 * (ez + 1));
+        const unsigned sy = W0, sz = W0 * W1;
+        T p0 = phis[ps];
+        T a0 = -(phis[ps + 1] - phis[ps - 1]) * inv2d;
+        T a1 = -(phis[ps + sy] - phis[ps - sy]) * inv2d;
+        T a2 = -(phis[ps + sz] - phis[ps - sz]) * inv2d;
+        if (carry) {
+            int ix, iy, iz;
+            float wx, wy, wz;
+            carry_axis(g.start[0] + (long long)ex - 1, ps0, ix, wx);
+            carry_axis(g.start[1] + (long long)ey - 1, ps1, iy, wy);
+            carry_axis(g.start[2] + (long long)ez - 1, ps2, iz, wz);
+            const unsigned base = ix + P0 * (iy + P1 * iz);
+            if constexpr (sizeof(T) == 8) {
+                double ip = 0.0, ia0 = 0.0, ia1 = 0.0, ia2 = 0.0;
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            double w = ((double)(dx ? 1.0f - wx : wx) * (double)(dy ? 1.0f - wy : wy)) *
+                                       (double)(dz ? 1.0f - wz : wz);
+                            unsigned pi = base + dx + P0 * (dy + P1 * dz);
+                            ip += w * (double)pphi[pi];
+                            ia0 += w * (double)pacc[pi];
+                            ia1 += w * (double)pacc[pn + pi];
+                            ia2 += w * (double)pacc[2 * pn + pi];
+                        }
+                p0 = (T)((double)p0 + ip);
+                a0 = (T)((double)a0 + ia0);
+                a1 = (T)((double)a1 + ia1);
+                a2 = (T)((double)a2 + ia2);
+            } else {
+                FF ip{0.f, 0.f}, ia0{0.f, 0.f}, ia1{0.f, 0.f}, ia2{0.f, 0.f};
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            // products of 1/4, 3/4: exact in FP32
+                            float w = ((dx ? 1.0f - wx : wx) * (dy ? 1.0f - wy : wy)) * (dz ? 1.0f - wz : wz);
+                            unsigned pi = base + dx + P0 * (dy + P1 * dz);
+                            ip = ff_fma(ip, w, (float)pphi[pi]);
+                            ia0 = ff_fma(ia0, w, (float)pacc[pi]);
+                            ia1 = ff_fma(ia1, w, (float)pacc[pn + pi]);
+                            ia2 = ff_fma(ia2, w, (float)pacc[2 * pn + pi]);
+                        }
+                ip = ff_add(ip, (float)p0);
+                ia0 = ff_add(ia0, (float)a0);
+                ia1 = ff_add(ia1, (float)a1);
+                ia2 = ff_add(ia2, (float)a2);
+                p0 = (T)__fadd_rn(ip.hi, ip.lo);
+                a0 = (T)__fadd_rn(ia0.hi, ia0.lo);
+                a1 = (T)__fadd_rn(ia1.hi, ia1.lo);
+                a2 = (T)__fadd_rn(ia2.hi, ia2.lo);
+            }
+        }
+        phi[o] = p0;
+        acc[o] = a0;
+        acc[ncell + o] = a1;
+        acc[2 * ncell + o] = a2;
+    }
+}
+
+__device__ __forceinline__ double drift(double x, double v, double half_dt, double box,
+                                        int periodic) {
+    double xd = __dadd_rn(x, __dmul_rn(v, half_dt));
+    if (periodic) xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
+    return xd;
+}
+
+__device__ __forceinline__ double to_cells(double xd, const LevelDev& L) {
+    return L.delta_pow2 ? __dmul_rn(xd, L.inv_delta) : __ddiv_rn(xd, L.delta);
+}
+
+// index of the grid of level L whose interior holds level cell ic, or -1
+__device__ int find_owner(const LevelDev& L, const long long ic[3]) {
+    if (L.is_root) {
+        const GridDev& g = L.g[0];
+        for (int j = 0; j < 3; ++j)
+            if (ic[j] < 0 || ic[j] >= g.N[j]) return -1;
+        return 0;
+    }
+    const TileMap& m = L.map;
+    long long t[3];
+    for (int j = 0; j < 3; ++j) {
+        long long rel = ic[j] - m.lo[j];
+        if (rel < 0) return -1;
+        t[j] = rel >> m.shift;
+        if (t[j] >= m.nt[j]) return -1;
+    }
+    long long tile = t[0] + (long long)m.nt[0] * (t[1] + (long long)m.nt[1] * t[2]);
+    for (int e = m.own_off[tile]; e < m.own_off[tile + 1]; ++e) {
+        int gi = m.own_list[e];
+        const GridDev& g = L.g[gi];
+        bool in = true;
+        for (int j = 0; j < 3; ++j)
+            if (ic[j] < g.start[j] || ic[j] >= g.start[j] + g.N[j]) in = false;
+        if (in) return gi;
+    }
+    return -1;
+}
+
+// TSC weights of one axis in T: FP64 for the FP64 path; for the FP32 path the
+// cell index and offset come from the exact FP64 position and the three
+// weights are evaluated in FP32.
+template <typename T>
+__device__ __forceinline__ void tsc_axis_t(double u, long long& i, T w[3]) {
+    double fi = floor(u);
+    i = (long long)fi;
+    T d = (T)(__dsub_rn(__dsub_rn(u, fi), 0.5));
+    T a = (T)0.5 - d, b = (T)0.5 + d;
+    w[0] = (T)0.5 * (a * a);
+    w[1] = (T)0.75 - d * d;
+    w[2] = (T)0.5 * (b * b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_finer, Particles P,
+                                                double half_dt, double box, int periodic,
+                                                const void* const* __restrict__ acc_p,
+                                                T* __restrict__ out) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P.n) return;
+    double xd[3] = {drift(P.x[p], P.vx[p], half_dt, box, periodic),
+                    drift(P.y[p], P.vy[p], half_dt, box, periodic),
+                    drift(P.z[p], P.vz[p], half_dt, box, periodic)};
+    long long ic[3];
+    T w[3][3];
+    for (int j = 0; j < 3; ++j) tsc_axis_t<T>(to_cells(xd[j], L), ic[j], w[j]);
+    int gi = find_owner(L, ic);
+    if (gi < 0) return;
+    if (has_finer) {
+        long long fc[3];
+        for (int j = 0; j < 3; ++j) fc[j] = (long long)floor(to_cells(xd[j], F));
+        if (find_owner(F, fc) >= 0) return;
+    }
+    const GridDev& g = L.g[gi];
+    const T* __restrict__ A = reinterpret_cast<const T*>(acc_p[gi]);
+    const int E0 = g.N[0] + 2, E1 = g.N[1] + 2;
+    const unsigned ncell = (unsigned)E0 * E1 * (g.N[2] + 2);
+    const bool fold = g.mode == 1;
+    int lc[3];
+    for (int j = 0; j < 3; ++j) lc[j] = (int)(ic[j] - g.start[j]);
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        int z = lc[2] + c - 1;
+        if (fold) z = z < 0 ? 0 : (z >= g.N[2] ? g.N[2] - 1 : z);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            int y = lc[1] + b - 1;
+            if (fold) y = y < 0 ? 0 : (y >= g.N[1] ? g.N[1] - 1 : y);
+            T wyz = w[1][b] * w[2][c];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int x = lc[0] + a - 1;
+                if (fold) x = x < 0 ? 0 : (x >= g.N[0] ? g.N[0] - 1 : x);
+                T wt = w[0][a] * wyz;
+                unsigned idx = (unsigned)(x + 1) + (unsigned)E0 * ((unsigned)(y + 1) + (unsigned)E1 * (unsigned)(z + 1));
+                a0 += wt * A[idx];
+                a1 += wt * A[ncell + idx];
+                a2 += wt * A[2 * ncell + idx];
+            }
+        }
+    }
+    out[p] = a0;
+    out[P.n + p] = a1;
+    out[2 * P.n + p] = a2;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
+                         const void* const* pphi, const void* const* pacc, void* const* phi,
+                         void* const* acc, const Chunk* chunks, int n_chunks, int chunk_cells,
+                         cudaStream_t s) {
+    if (n_chunks <= 0) return cudaSuccess;
+    k_accel<T><<<n_chunks, 256, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks,
+                                        chunk_cells);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_interp(const LevelDev& L, const LevelDev* finer, const Particles& P,
+                          double half_dt, double box, int periodic, const void* const* acc,
+                          void* out, cudaStream_t s) {
+    if (P.n <= 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((P.n + 255) / 256);
+    LevelDev F = finer ? *finer : L;
+    k_interp<T><<<blocks, 256, 0, s>>>(L, F, finer ? 1 : 0, P, half_dt, box, periodic, acc,
+                                       reinterpret_cast<T*>(out));
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_accel<float>(const LevelDev&, const GridDev*, const void* const*,
+                                         const void* const*, const void* const*, void* const*,
+                                         void* const*, const Chunk*, int, int, cudaStream_t);
+template cudaError_t launch_accel<double>(const LevelDev&, const GridDev*, const void* const*,
+                                          const void* const*, const void* const*, void* const*,
+                                          void* const*, const Chunk*, int, int, cudaStream_t);
+template cudaError_t launch_interp<float>(const LevelDev&, const LevelDev*, const Particles&, double,
+                                          double, int, const void* const*, void*, cudaStream_t);
+template cudaError_t launch_interp<double>(const LevelDev&, const LevelDev*, const Particles&, double,
+                                           double, int, const void* const*, void*, cudaStream_t);
+
+}  // namespace apm

@@ -1,0 +1,191 @@
+"""Python face of libapm: the four C-ABI calls with torch tensors as device
+memory and torch streams.  Every step of the solve runs in the library's CUDA
+kernels; this module only marshals pointers and allocates output buffers.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import ApmConfig, ApmGrid, ApmGridInfo, ApmParticles, check, lib, ptr_array
+
+PARTICLE_KEYS = ("x", "y", "z", "vx", "vy", "vz", "m")
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Particles:
+    """Device particle arrays (float64, contiguous) and their C view."""
+
+    def __init__(self, arrays):
+        self.t = {}
+        n = None
+        for k in PARTICLE_KEYS:
+            a = arrays[k]
+            if not a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+                raise ValueError(f"particle array {k} must be a contiguous float64 CUDA tensor")
+            n = a.numel() if n is None else n
+            if a.numel() != n:
+                raise ValueError("particle arrays differ in length")
+            self.t[k] = a
+        self.n = int(n)
+        self.c = ApmParticles(self.n, *[self.t[k].data_ptr() for k in PARTICLE_KEYS])
+
+
+class Solver:
+    """One APM context on one GPU with a static grid hierarchy.
+
+    grids: sequence of (level, parent, start(3), dims(3)); grid 0 is the root.
+    """
+
+    def __init__(self, grids, periodic=False, precision="fp32", mass_frac_bits=52,
+                 root_correction=True, a_over_dx=3.4, pad_factor=0.65, box=1.0, device=None):
+        L = lib()
+        cfg = ApmConfig()
+        L.apm_config_default(ctypes.byref(cfg))
+        cfg.box = box
+        cfg.a_over_dx = a_over_dx
+        cfg.pad_factor = pad_factor
+        cfg.root_bc = _lib.APM_BC_PERIODIC if periodic else _lib.APM_BC_ISOLATED
+        cfg.precision = _lib.APM_FP64 if precision == "fp64" else _lib.APM_FP32
+        cfg.mass_frac_bits = int(mass_frac_bits)
+        cfg.root_correction = 1 if root_correction else 0
+        dev = torch.cuda.current_device() if device is None else int(device)
+        cfg.device = dev
+        self.device = torch.device("cuda", dev)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.precision = precision
+        self._ctx = ctypes.c_void_p()
+        check(L.apm_create(ctypes.byref(cfg), ctypes.byref(self._ctx)), "apm_create")
+        self.grids = [tuple(g) for g in grids]
+        arr = (ApmGrid * len(self.grids))()
+        for i, (lev, par, start, dims) in enumerate(self.grids):
+            arr[i].level = int(lev)
+            arr[i].parent = int(par)
+            for j in range(3):
+                arr[i].start[j] = int(start[j])
+                arr[i].dims[j] = int(dims[j])
+        try:
+            check(L.apm_set_hierarchy(self._ctx, arr, len(self.grids)), "apm_set_hierarchy")
+        except Exception:
+            L.apm_destroy(self._ctx)
+            self._ctx = None
+            raise
+        self.n_levels = L.apm_num_levels(self._ctx)
+        self.info = []
+        for i in range(len(self.grids)):
+            gi = ApmGridInfo()
+            check(L.apm_get_grid_info(self._ctx, i, ctypes.byref(gi)), "apm_get_grid_info")
+            self.info.append(dict(level=gi.level, border=gi.border, gmf=tuple(gi.gmf),
+                                  fft=tuple(gi.fft), phi_short=tuple(gi.phi_short),
+                                  field=tuple(gi.field), level_index=gi.level_index,
+                                  delta=gi.delta))
+        self.level_grids = [[i for i, g in enumerate(self.grids) if g[0] == lev]
+                            for lev in range(self.n_levels)]
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().apm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ buffers
+    def alloc_level(self, level):
+        """Output buffers of one level: gmf (int64), phi_short, phi, acc ([3, ...])."""
+        out = dict(gmf=[], phis=[], phi=[], acc=[])
+        for gi in self.level_grids[level]:
+            inf = self.info[gi]
+            out["gmf"].append(torch.empty(inf["gmf"][::-1], dtype=torch.int64, device=self.device))
+            out["phis"].append(torch.empty(inf["phi_short"][::-1], dtype=self.dtype, device=self.device))
+            out["phi"].append(torch.empty(inf["field"][::-1], dtype=self.dtype, device=self.device))
+            out["acc"].append(torch.empty((3,) + inf["field"][::-1], dtype=self.dtype, device=self.device))
+        return out
+
+    def alloc_all(self):
+        return [self.alloc_level(lev) for lev in range(self.n_levels)]
+
+    # ------------------------------------------------------------------ C-ABI calls
+    def deposit(self, level, particles, half_dt, gmf, gas=None, parent_gas=None, stream=None):
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        g = ptr_array([_ptr(t) for t in gmf])
+        ga = None if gas is None else ptr_array([_ptr(t) for t in gas])
+        pg = None if parent_gas is None else ptr_array([_ptr(t) for t in parent_gas])
+        check(lib().apm_deposit(self._ctx, level, ctypes.byref(P.c), float(half_dt), ga, pg, g,
+                                _stream_handle(stream)), "apm_deposit")
+
+    def solve_level(self, level, gmf, phis, stream=None):
+        check(lib().apm_solve_level(self._ctx, level, ptr_array([_ptr(t) for t in gmf]),
+                                    ptr_array([_ptr(t) for t in phis]), _stream_handle(stream)),
+              "apm_solve_level")
+
+    def accel(self, level, phis, phi, acc, parent_phi=None, parent_acc=None, stream=None):
+        pp = None if parent_phi is None else ptr_array([_ptr(t) for t in parent_phi])
+        pa = None if parent_acc is None else ptr_array([_ptr(t) for t in parent_acc])
+        check(lib().apm_accel(self._ctx, level, ptr_array([_ptr(t) for t in phis]), pp, pa,
+                              ptr_array([_ptr(t) for t in phi]), ptr_array([_ptr(t) for t in acc]),
+                              _stream_handle(stream)), "apm_accel")
+
+    def interp(self, level, acc, particles, half_dt, out, stream=None):
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        check(lib().apm_interp(self._ctx, level, ptr_array([_ptr(t) for t in acc]),
+                               ctypes.byref(P.c), float(half_dt), out.data_ptr(),
+                               _stream_handle(stream)), "apm_interp")
+
+    def profile(self, on, capacity=65536):
+        """Turns kernel tracing on (event pool of `capacity` launches) or off."""
+        check(lib().apm_profile_enable(self._ctx, 1 if on else 0, int(capacity)), "apm_profile_enable")
+
+    def profile_read(self):
+        """{kernel name: (launches, total device ms)} since tracing was enabled."""
+        L = lib()
+        out = {}
+        for k in range(L.apm_kernel_count()):
+            n = ctypes.c_int64()
+            ms = ctypes.c_double()
+            check(L.apm_profile_read(self._ctx, k, ctypes.byref(n), ctypes.byref(ms)), "apm_profile_read")
+            out[L.apm_kernel_name(k).decode()] = (int(n.value), float(ms.value))
+        return out
+
+    def sync_status(self, stream=None):
+        check(lib().apm_sync_status(self._ctx, _stream_handle(stream)), "apm_sync_status")
+
+    # ------------------------------------------------------------------ one solve
+    def step(self, particles, half_dt, bufs, pacc, gas=None, levels=None, stream=None):
+        """One APM solve over the hierarchy (Sec. 2, 2.2), levels top-down:
+        deposit -> solve -> accel per level, then interpolation on every level.
+        bufs: from alloc_all(); pacc: (3, n) tensor of the context precision;
+        gas: None or a list with one device density tensor (or None) per grid."""
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        levs = range(self.n_levels) if levels is None else levels
+        for lev in levs:
+            b = bufs[lev]
+            ids = self.level_grids[lev]
+            g = None if gas is None else [gas[i] for i in ids]
+            pg = None
+            if gas is not None and lev > 0:
+                pg = [gas[i] for i in self.level_grids[lev - 1]]
+                if all(t is None for t in pg):
+                    pg = None
+            if g is not None and all(t is None for t in g):
+                g = None
+            self.deposit(lev, P, half_dt, b["gmf"], g, pg, stream)
+            self.solve_level(lev, b["gmf"], b["phis"], stream)
+            if lev > 0 and (levels is None or (lev - 1) in levs):
+                self.accel(lev, b["phis"], b["phi"], b["acc"], bufs[lev - 1]["phi"],
+                           bufs[lev - 1]["acc"], stream)
+            else:
+                self.accel(lev, b["phis"], b["phi"], b["acc"], stream=stream)
+        for lev in levs:
+            self.interp(lev, bufs[lev]["acc"], P, half_dt, pacc, stream)

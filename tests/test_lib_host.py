@@ -1,0 +1,132 @@
+"""Host-side checks of libapm that need no GPU: the library builds and loads,
+exports every function include/apm.h declares, and its host-only entry points
+(defaults, status strings, hierarchy validation, argument checks) behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1410_0010_gb300 import _lib, buildlib
+    buildlib.build()
+    return _lib.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "apm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(apm_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_function(L):
+    from paper_1410_0010_gb300 import _lib
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in _lib.SIGNATURES, f"binding lacks {n}"
+
+
+def test_defaults_are_the_papers(L):
+    from paper_1410_0010_gb300._lib import ApmConfig
+    c = ApmConfig()
+    L.apm_config_default(ctypes.byref(c))
+    assert c.a_over_dx == 3.4 and c.refine == 2 and c.pad_factor == 0.65   # Sec. 2.2
+    assert c.box == 1.0 and c.root_bc == 0 and c.mass_frac_bits == 52 and c.device == -1
+    assert L.apm_version().startswith(b"apm-gb300")
+    for code in range(10):
+        assert len(L.apm_status_string(code)) >= 2
+    assert L.apm_status_string(99) == b"unknown status"
+
+
+def test_create_rejects_bad_config_before_touching_cuda(L):
+    from paper_1410_0010_gb300._lib import ApmConfig
+    c = ApmConfig()
+    L.apm_config_default(ctypes.byref(c))
+    ctx = ctypes.c_void_p()
+    bad = [("box", -1.0), ("mass_frac_bits", 63), ("mass_frac_bits", 0), ("root_bc", 5),
+           ("precision", 7), ("refine", 1)]
+    for field, value in bad:
+        cc = ApmConfig()
+        ctypes.pointer(cc)[0] = c
+        setattr(cc, field, value)
+        assert L.apm_create(ctypes.byref(cc), ctypes.byref(ctx)) == 1, field
+    cc = ApmConfig()
+    ctypes.pointer(cc)[0] = c
+    cc.refine = 4
+    assert L.apm_create(ctypes.byref(cc), ctypes.byref(ctx)) == 8   # unsupported
+
+
+def test_calls_without_context_fail_cleanly(L):
+    assert L.apm_deposit(None, 0, None, 0.0, None, None, None, None) == 1
+    assert L.apm_solve_level(None, 0, None, None, None) == 1
+    assert L.apm_accel(None, 0, None, None, None, None, None, None) == 1
+    assert L.apm_interp(None, 0, None, None, 0.0, None, None) == 1
+    assert L.apm_sync_status(None, None) == 1
+    assert L.apm_num_levels(None) == 0
+    L.apm_destroy(None)
+
+
+def _grids(descs):
+    from paper_1410_0010_gb300._lib import ApmGrid
+    arr = (ApmGrid * len(descs))()
+    for i, (lev, par, st, dm) in enumerate(descs):
+        arr[i].level, arr[i].parent = lev, par
+        for j in range(3):
+            arr[i].start[j], arr[i].dims[j] = st[j], dm[j]
+    return arr
+
+
+def _validate(L, descs):
+    from paper_1410_0010_gb300._lib import ApmConfig
+    c = ApmConfig()
+    L.apm_config_default(ctypes.byref(c))
+    return L.apm_validate_hierarchy(ctypes.byref(c), _grids(descs), len(descs))
+
+
+ROOT32 = (0, -1, (0, 0, 0), (32, 32, 32))
+
+
+def test_validation_accepts_the_papers_hierarchies(L):
+    import apm_inputs as W
+    for bounds in (W.FIG1_BOUNDS, W.POINT_SOURCE_CENTRE, W.POINT_SOURCE_CORNER, W.SINE_WAVE_BOUNDS):
+        root = 64 if bounds is W.SINE_WAVE_BOUNDS else 32
+        descs = [tuple(g) for g in W.grids_from_bounds(root, bounds)]
+        assert _validate(L, descs) == 0, bounds
+
+
+def test_validation_nesting_rules(L):
+    ok = [ROOT32, (1, 0, (12, 12, 12), (20, 20, 20))]
+    assert _validate(L, ok) == 0
+    # parent cells of the border: child start 10 -> border cells from 5 -> parent 2: ok;
+    # start 4 -> border from -1 -> parent -1: outside the root
+    assert _validate(L, [ROOT32, (1, 0, (4, 12, 12), (8, 8, 8))]) == 2
+    assert _validate(L, [ROOT32, (1, 0, (6, 12, 12), (8, 8, 8))]) == 0
+    # upper edge: parent cell floor((start + N + B - 1)/2) must be < 32
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 52), (8, 8, 8))]) == 2
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 52), (8, 8, 6))]) == 0
+    # overlapping siblings
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 12), (10, 10, 10)),
+                         (1, 0, (20, 20, 20), (10, 10, 10))]) == 2
+    # touching siblings are fine
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 12), (10, 10, 10)),
+                         (1, 0, (22, 12, 12), (10, 10, 10))]) == 0
+    # wrong parent level, missing level, second root, bad root
+    assert _validate(L, [ROOT32, (2, 0, (40, 40, 40), (8, 8, 8))]) == 2
+    assert _validate(L, [ROOT32, ROOT32]) == 2
+    assert _validate(L, [(0, -1, (0, 0, 0), (32, 32, 16))]) == 1
+    assert _validate(L, [(0, -1, (1, 0, 0), (32, 32, 32))]) == 2
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 12), (0, 4, 4))]) == 1
+
+
+def test_package_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1410_0010_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not found"):
+        _lib.lib()
