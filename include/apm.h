@@ -224,6 +224,29 @@ apm_status apm_profile_read(apm_ctx* ctx, int32_t kernel, int64_t* launches, dou
 int32_t apm_kernel_count(void);
 const char* apm_kernel_name(int32_t kernel);
 
+/* Potential of one periodic root grid without allocating anything.
+ * The paper has no counterpart: this is a convenience for callers that cannot
+ * call cudaMalloc (code running where the CUDA runtime may not allocate, such
+ * as host callbacks or graph-capture regions, or programs whose memory pool
+ * owns the whole device).  It needs no context: it computes what apm_solve_level
+ * computes for a periodic root of n^3 cells (box side `box`, smoothing
+ * a = a_over_dx * box / n), in FP32, with every intermediate (twiddles, the
+ * Green's table, the FFT spectra) kept in one fixed 24 MiB device array that
+ * each GPU loading the library holds until the process exits.
+ *  gmf       : device, n^3 int64 cell masses * 2^mass_frac_bits (x fastest)
+ *  phi_short : device, (n+4)^3 floats, cells [-2, n+2) (periodic wrap)
+ * n must be {2,3,5,7}-smooth with 4 <= n <= 128; larger or non-smooth n return
+ * APM_E_INVALID (the fixed array holds at most a 128^3 grid).
+ * The first call on a device looks up the array's device address and sets the
+ * FFT kernels' shared-memory limit (host-side set-up, once per device, with that
+ * device current); make that first call before any stream capture.
+ * All calls share the one array: each call rebuilds everything it reads, but
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race on it and must be serialised by the caller. */
+apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a_over_dx,
+                                      int32_t mass_frac_bits, const int64_t* gmf,
+                                      float* phi_short, void* stream);
+
 /* Synchronises `stream`, returns the first error the kernels latched since the
  * last call (APM_OK if none) and clears it. */
 apm_status apm_sync_status(apm_ctx* ctx, void* stream);

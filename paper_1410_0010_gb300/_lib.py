@@ -59,6 +59,7 @@ SIGNATURES = {
     "apm_profile_read": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]),
     "apm_kernel_count": (c_i32, []),
     "apm_kernel_name": (ctypes.c_char_p, [c_i32]),
+    "apm_solve_periodic_noalloc": (c_i32, [c_i32, c_dbl, c_dbl, c_i32, c_void_p, c_void_p, c_void_p]),
     "apm_status_string": (ctypes.c_char_p, [c_i32]),
     "apm_destroy": (None, [c_void_p]),
     "apm_version": (ctypes.c_char_p, []),

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libapm.so")
 
-SOURCES = ["apm_api.cu", "k_green.cu", "k_deposit.cu", "k_fft.cu", "k_field.cu"]
+SOURCES = ["apm_api.cu", "k_green.cu", "k_deposit.cu", "k_fft.cu", "k_field.cu", "apm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
           "--expt-relaxed-constexpr"]
