@@ -328,10 +328,20 @@ def config_cosmo512(seed=5, root_n=512, lattice=256, n_sub=64, sub_n=128):
                     notes="Zel'dovich lattice, P(k) ~ k^-2, v = 10 psi")
 
 
+def config_cosmo_small(seed=6):
+    """Reduced cosmological workload for profiling captures: periodic 256^3 root,
+    128^3 = 2,097,152 Zel'dovich particles, two levels of 8 subgrids of 128^3
+    (inputs still larger than the 129 MB L2: 134 MB root mass field + particles)."""
+    w = config_cosmo512(seed=seed, root_n=256, lattice=128, n_sub=8, sub_n=128)
+    w.name = "cosmo256_2lev_zeldovich2M"
+    return w
+
+
 CONFIGS = {
     "c1": config_isolated_root32,
     "c2": config_two_level,
     "c3": config_plummer,
     "c4": config_batched_level,
     "c5": config_cosmo512,
+    "c5s": config_cosmo_small,
 }

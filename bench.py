@@ -388,7 +388,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["apm", "reference"], default="apm")
-    ap.add_argument("--workload", choices=["c3", "c4", "c5"], default="c5")
+    ap.add_argument("--workload", choices=["c3", "c4", "c5", "c5s"], default="c5")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -162,12 +162,6 @@ int border_cells(const apm_config& c) {
     return (int)std::ceil(c.pad_factor * c.refine * c.a_over_dx - 1e-12);
 }
 
-int pow2_floor(int v) {
-    int p = 1;
-    while (p * 2 <= v) p *= 2;
-    return p;
-}
-
 // Validates the tree (see apm_set_hierarchy).
 apm_status validate(const apm_config& cfg, const apm_grid* gr, int n) {
     if (n < 1) return APM_E_INVALID;
@@ -520,10 +514,11 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             g.Hy2 = g.M[1] / 2 + 1;
             g.Hz2 = g.M[2] / 2 + 1;
             g.cells_gmf = (long long)g.G[0] * g.G[1] * g.G[2];
-            const int budget = f64 ? kFftBudgetF64 : kFftBudgetF32;
-            g.np_x = std::max(1, budget / g.M[0]);
-            g.tx_y = std::min(32, pow2_floor(std::max(1, budget / g.M[1])));
-            g.tx_z = std::min(32, pow2_floor(std::max(1, budget / g.M[2])));
+            g.rows_gas = std::max(1, kChunkCells / g.G[0]);
+            g.rows_acc = std::max(1, kChunkCells / (g.N[0] + 2));
+            g.np_x = fft_row_pairs(g.M[0], f64);
+            g.tx_y = fft_col_lines(g.M[1], f64);
+            g.tx_z = fft_col_lines(g.M[2], f64);
             // green table (cached per shape and level parameters)
             TabKey key{g.kind, g.M[0], g.M[1], g.M[2], delta, a_lev, a_par};
             auto it = tab_off.find(key);
@@ -586,17 +581,17 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             for (int t = 0; t < nky * g.W[2]; ++t) yi.push_back({k, t});
             long long pairs_o = ((long long)g.W[1] * g.W[2] + 1) / 2;
             for (long long t = 0; t < (pairs_o + g.np_x - 1) / g.np_x; ++t) xi.push_back({k, (int)t});
-            for (long long t = 0; t < (g.cells_gmf + kChunkCells - 1) / kChunkCells; ++t) gas.push_back({k, (int)t});
-            long long ec = (long long)(g.N[0] + 2) * (g.N[1] + 2) * (g.N[2] + 2);
-            for (long long t = 0; t < (ec + kChunkCells - 1) / kChunkCells; ++t) acc.push_back({k, (int)t});
-            sxf = std::max(sxf, (size_t)g.np_x * g.M[0]);
-            syf = std::max(syf, (size_t)g.M[1] * g.tx_y);
-            sz = std::max(sz, (size_t)g.M[2] * g.tx_z);
+            const long long grows = (long long)g.G[1] * g.G[2];
+            for (long long t = 0; t < (grows + g.rows_gas - 1) / g.rows_gas; ++t) gas.push_back({k, (int)t});
+            const long long erows = (long long)(g.N[1] + 2) * (g.N[2] + 2);
+            for (long long t = 0; t < (erows + g.rows_acc - 1) / g.rows_acc; ++t) acc.push_back({k, (int)t});
+            sxf = std::max(sxf, fft_row_smem(g.M[0], g.np_x, csz));
+            syf = std::max(syf, fft_col_smem(g.M[1], g.tx_y, csz));
+            sz = std::max(sz, fft_col_smem(g.M[2], g.tx_z, csz));
         }
-        // two buffers per CTA; the second starts at the fixed budget offset
-        const size_t bud = (size_t)(f64 ? kFftBudgetF64 : kFftBudgetF32);
-        (void)sxf; (void)syf; (void)sz;
-        L.smem_xf = L.smem_xi = L.smem_yf = L.smem_yi = L.smem_z = 2 * bud * csz;
+        L.smem_xf = L.smem_xi = sxf;
+        L.smem_yf = L.smem_yi = syf;
+        L.smem_z = sz;
         if ((st = upload(c, &L.d_xf, xf)) != APM_OK) return st;
         if ((st = upload(c, &L.d_yf, yf)) != APM_OK) return st;
         if ((st = upload(c, &L.d_z, zc)) != APM_OK) return st;

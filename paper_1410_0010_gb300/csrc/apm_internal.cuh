@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "apm.h"
 
 namespace apm {
@@ -14,10 +16,29 @@ namespace apm {
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 12;      // radix stages of one 1-D transform
 constexpr int kFftThreads = 256;    // threads of every FFT pass CTA
-// complex elements of each of the two shared-memory buffers of a pass CTA
-// (lines per CTA x line length); 64 KB of shared memory per CTA either way
-constexpr int kFftBudgetF32 = 4096;
-constexpr int kFftBudgetF64 = 2048;
+// complex elements one buffer of a pass CTA aims at (lines per CTA x length)
+constexpr int kFftBudgetF32 = 2048;
+constexpr int kFftBudgetF64 = 1024;
+
+inline int pow2_floor_i(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+// lines (kx columns) per CTA of a y/z pass: a power of two, at least 32 bytes
+// of contiguous row per line group, at most 32
+inline int fft_col_lines(int L, bool f64) {
+    int v = pow2_floor_i(std::max(1, (f64 ? kFftBudgetF64 : kFftBudgetF32) / L));
+    return std::min(32, std::max(f64 ? 2 : 4, v));
+}
+// complex lines (row pairs) per CTA of an x pass: a power of two, 1..32
+inline int fft_row_pairs(int M0, bool f64) {
+    int v = pow2_floor_i(std::max(1, (f64 ? kFftBudgetF64 : kFftBudgetF32) / M0));
+    return std::min(32, v);
+}
+// dynamic shared memory of the passes: two buffers plus the twiddles
+inline size_t fft_row_smem(int M0, int np, size_t csz) { return (size_t)(2 * M0 * (np + 1) + M0) * csz; }
+inline size_t fft_col_smem(int L, int tx, size_t csz) { return (size_t)(2 * L * tx + L) * csz; }
 constexpr int kMaxFft = 1024;       // longest supported transform
 
 // device status bits (latched with atomicOr, read by apm_sync_status)
@@ -60,6 +81,8 @@ struct GridDev {
     long long cells_gmf; // G0 G1 G2
     int np_x;            // row pairs per CTA of the x passes
     int tx_y, tx_z;      // kx lines per CTA of the y / z passes
+    int rows_gas;        // GMF rows per CTA of the baryon initialisation
+    int rows_acc;        // output rows per CTA of the acceleration kernel
 };
 
 // Tile lookup: level cell -> candidate grids (CSR per tile).
@@ -110,7 +133,7 @@ cudaError_t launch_to_f32(const double* in, float* out, long long n, cudaStream_
 // GMF: baryons (initialises every cell) then particles
 cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
                             const double* const* gas, const double* const* pgas,
-                            int64_t* const* gmf, const Chunk* chunks, int n_chunks, int chunk_cells,
+                            int64_t* const* gmf, const Chunk* chunks, int n_chunks, int rows_per_cta,
                             int F, cudaStream_t s);
 cudaError_t launch_deposit(const LevelDev& L, const Particles& P, double half_dt, double box,
                            int periodic, int F, int64_t* const* gmf, unsigned* status,
@@ -144,7 +167,7 @@ cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
 template <typename T>
 cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
                          const void* const* pphi, const void* const* pacc, void* const* phi,
-                         void* const* acc, const Chunk* chunks, int n_chunks, int chunk_cells,
+                         void* const* acc, const Chunk* chunks, int n_chunks, int rows_per_cta,
                          cudaStream_t s);
 template <typename T>
 cudaError_t launch_interp(const LevelDev& L, const LevelDev* finer, const Particles& P,

@@ -57,12 +57,6 @@ bool plan1d(int L, FftPlan1D* pl) {
     return n == 1 && L >= 2;
 }
 
-int pow2_floor(int v) {
-    int p = 1;
-    while (p * 2 <= v) p *= 2;
-    return p;
-}
-
 }  // namespace
 }  // namespace apm
 
@@ -112,8 +106,8 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     g.delta = delta;
     g.parent = -1;
     g.cells_gmf = (long long)n * n * n;
-    g.np_x = std::max(1, kFftBudgetF32 / n);
-    g.tx_y = g.tx_z = std::min(32, pow2_floor(std::max(1, kFftBudgetF32 / n)));
+    g.np_x = fft_row_pairs(n, false);
+    g.tx_y = g.tx_z = fft_col_lines(n, false);
     const long long Hx = g.Hx;
     const long long szA = (long long)(n + 4) * n * Hx;         // max(G1 G2, W2 M1) Hx
     const long long szB = (long long)(n + 4) * (n + 4) * Hx;   // max(G2 M1, W2 W1) Hx
@@ -176,16 +170,20 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     a.wsA = wsA;
     a.wsB = wsB;
     a.F = mass_frac_bits;
-    a.smem = 2 * (size_t)kFftBudgetF32 * sizeof(float2);
+    const size_t smem_rows = fft_row_smem(n, g.np_x, sizeof(float2));
+    const size_t smem_cols = fft_col_smem(n, g.tx_y, sizeof(float2));
     a.n_chunks = n_xf;
+    a.smem = smem_rows;
     if (launch_fft_xf<float>(a, d_in, s) != cudaSuccess) return APM_E_CUDA;
     a.n_chunks = n_yf;
+    a.smem = smem_cols;
     if (launch_fft_yf<float>(a, s) != cudaSuccess) return APM_E_CUDA;
     a.n_chunks = n_z;
     if (launch_fft_z<float>(a, s) != cudaSuccess) return APM_E_CUDA;
     a.n_chunks = n_yi;
     if (launch_fft_yi<float>(a, s) != cudaSuccess) return APM_E_CUDA;
     a.n_chunks = n_xi;
+    a.smem = smem_rows;
     if (launch_fft_xi<float>(a, d_out, s) != cudaSuccess) return APM_E_CUDA;
     return APM_OK;
 }

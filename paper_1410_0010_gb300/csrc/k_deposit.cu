@@ -16,38 +16,46 @@ __device__ __forceinline__ long long floor_div(long long a, long long b) {
     return q;
 }
 
-__global__ void k_gas_init(LevelDev L, const GridDev* __restrict__ pgrids,
+// One CTA per batch of `rows` GMF rows (a row: G0 cells along x at fixed y, z).
+__global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __restrict__ pgrids,
                            const double* const* __restrict__ gas,
                            const double* const* __restrict__ pgas, int64_t* const* __restrict__ gmf,
-                           const Chunk* __restrict__ chunks, int chunk_cells, int F, int refine) {
+                           const Chunk* __restrict__ chunks, int rows_per_cta, int F, int refine) {
     const Chunk c = chunks[blockIdx.x];
     const GridDev& g = L.g[c.grid];
+    const int G0 = g.G[0], G1 = g.G[1];
+    const int nrows = G1 * g.G[2];
     const double scale = ldexp(1.0, F);
     const double vol = __dmul_rn(__dmul_rn(g.delta, g.delta), g.delta);
     const double* own = gas ? gas[c.grid] : nullptr;
     const double* par = (pgas && g.parent >= 0) ? pgas[g.parent] : nullptr;
-    int64_t* out = gmf[c.grid];
-    const int B = (g.G[0] - g.N[0]) / 2;
-    long long cell0 = (long long)c.tile * chunk_cells;
-    for (int t = threadIdx.x; t < chunk_cells; t += blockDim.x) {
-        long long cell = cell0 + t;
-        if (cell >= g.cells_gmf) break;
-        int x = (int)(cell % g.G[0]);
-        long long r = cell / g.G[0];
-        int y = (int)(r % g.G[1]);
-        int z = (int)(r / g.G[1]);
-        int cx = x - B, cy = y - B, cz = z - B;
-        double rho = 0.0;
-        if (cx >= 0 && cx < g.N[0] && cy >= 0 && cy < g.N[1] && cz >= 0 && cz < g.N[2]) {
-            if (own) rho = own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)];
-        } else if (par) {
-            const GridDev& p = pgrids[g.parent];
-            long long px = floor_div(g.start[0] + cx, refine) - p.start[0];
-            long long py = floor_div(g.start[1] + cy, refine) - p.start[1];
-            long long pz = floor_div(g.start[2] + cz, refine) - p.start[2];
-            rho = par[px + (long long)p.N[0] * (py + (long long)p.N[1] * pz)];
+    int64_t* __restrict__ out = gmf[c.grid];
+    const int B = (G0 - g.N[0]) / 2;
+    const int r0 = c.tile * g.rows_gas;
+    const int r1 = min(nrows, r0 + g.rows_gas);
+    for (int r = r0; r < r1; ++r) {
+        int64_t* row = out + (long long)r * G0;
+        if (!own && !par) {
+            for (int x = threadIdx.x; x < G0; x += blockDim.x) row[x] = 0;
+            continue;
         }
-        out[cell] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
+        const int y = r % G1, z = r / G1;
+        const int cy = y - B, cz = z - B;
+        const bool yz_in = cy >= 0 && cy < g.N[1] && cz >= 0 && cz < g.N[2];
+        for (int x = threadIdx.x; x < G0; x += blockDim.x) {
+            const int cx = x - B;
+            double rho = 0.0;
+            if (yz_in && cx >= 0 && cx < g.N[0]) {
+                if (own) rho = own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)];
+            } else if (par) {
+                const GridDev& p = pgrids[g.parent];
+                long long px = floor_div(g.start[0] + cx, refine) - p.start[0];
+                long long py = floor_div(g.start[1] + cy, refine) - p.start[1];
+                long long pz = floor_div(g.start[2] + cz, refine) - p.start[2];
+                rho = par[px + (long long)p.N[0] * (py + (long long)p.N[1] * pz)];
+            }
+            row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
+        }
     }
 }
 
@@ -73,11 +81,20 @@ __device__ __forceinline__ void tsc_axis(double u, long long& i, double w[3]) {
     i = (long long)fi;
 }
 
+// x' = x + v half_dt; on a periodic domain x' - box floor(x'/box), which is x'
+// itself (bit for bit) when x' is already inside [0, box)
 __device__ __forceinline__ double drift(double x, double v, double half_dt, double box,
                                         int periodic) {
     double xd = __dadd_rn(x, __dmul_rn(v, half_dt));
-    if (periodic) xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
+    if (periodic && !(xd >= 0.0 && xd < box))
+        xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
     return xd;
+}
+
+// rint(v) to the nearest integer, ties to even, for |v| < 2^51: adding 1.5 2^52
+// places the rounded integer in the low bits of the sum
+__device__ __forceinline__ long long rint_small(double v) {
+    return __double_as_longlong(__dadd_rn(v, 6755399441055744.0)) - 0x4338000000000000LL;
 }
 
 // adds the 27 charges q (z-major: q[c][b][a]) to one GMF box
@@ -170,8 +187,17 @@ __global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double
         atomicOr(status, kStOverflow);
         return;
     }
+    // q = rint((m w) 2^F) with w = (wx wy) wz.  Scaling by 2^F is exact, so
+    // (m w) 2^F == (m 2^F) w bit for bit (normal range), and wx wy is shared by
+    // the three z cells.
     long long q[3][3][3];
     long long others = 0;
+    double wxy[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) wxy[b][a] = __dmul_rn(w[0][a], w[1][b]);
+    const bool small = fabs(mq) < 2251799813685248.0;   // 2^51: charges fit rint_small
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -179,11 +205,11 @@ __global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 if (a == 1 && b == 1 && c == 1) continue;
-                double wt = __dmul_rn(__dmul_rn(w[0][a], w[1][b]), w[2][c]);
-                q[c][b][a] = __double2ll_rn(__dmul_rn(__dmul_rn(mass, wt), scale));
+                double v = __dmul_rn(mq, __dmul_rn(wxy[b][a], w[2][c]));
+                q[c][b][a] = small ? rint_small(v) : __double2ll_rn(v);
                 others += q[c][b][a];
             }
-    q[1][1][1] = __double2ll_rn(mq) - others;
+    q[1][1][1] = (small ? rint_small(mq) : __double2ll_rn(mq)) - others;
 
     for (int e = e0; e < e1; ++e) {
         int gi = L.is_root ? 0 : L.map.dep_list[e];
@@ -200,10 +226,10 @@ __global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double
 
 cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
                             const double* const* gas, const double* const* pgas,
-                            int64_t* const* gmf, const Chunk* chunks, int n_chunks, int chunk_cells,
+                            int64_t* const* gmf, const Chunk* chunks, int n_chunks, int rows_per_cta,
                             int F, cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    k_gas_init<<<n_chunks, 256, 0, s>>>(L, parent_grids, gas, pgas, gmf, chunks, chunk_cells, F,
+    k_gas_init<<<n_chunks, 256, 0, s>>>(L, parent_grids, gas, pgas, gmf, chunks, rows_per_cta, F,
                                          L.refine);
     return cudaGetLastError();
 }

@@ -4,7 +4,11 @@
 // the window of cells [-2, N+2) of the result is written.
 //
 // Five passes, each one CTA per batch of lines, each line transformed entirely
-// in shared memory by mixed-radix (2, 3, 4, 5, 7, 8) Stockham stages:
+// in shared memory by mixed-radix (2, 3, 4, 5, 7, 8) Stockham stages (ping-pong
+// between two shared-memory buffers, twiddles staged in shared memory).  A CTA
+// holds a power-of-two number of lines, laid out element-major (line index
+// fastest), so consecutive threads take consecutive lines and no integer
+// division is left in the butterfly loops:
 //   xf : GMF rows (int64 -> FP64 mass -> T), two real rows per complex line,
 //        R2C along x                                   -> A[z][y][kx]   (y < G1, z < G2)
 //   yf : columns along y, zero-padded G1 -> M1         -> B[z][ky][kx]  (z < G2)
@@ -101,61 +105,67 @@ template <typename T, int DIR, int R> struct Dft {
     }
 };
 
-// One Stockham stage of radix R over `nl` lines of length L (element i of line
-// l at [l*ls + i*es]), from src to dst in shared memory; Ns = product of the
-// radices already applied.  Butterfly j reads elements j + r L/R, twiddles them
-// by exp(DIR 2 pi i (j mod Ns) r / (Ns R)), and writes elements
+// One Stockham stage of radix R over nl = 2^lg lines of length L, element i of
+// line l at [i*es + l], from src to dst; Ns = product of the radices already
+// applied.  Butterfly j reads elements j + r L/R, twiddles them by
+// exp(DIR 2 pi i (j mod Ns) r / (Ns R)), and writes elements
 // (j / Ns) Ns R + (j mod Ns) + r Ns: natural order after the last stage.
-// lf: consecutive threads take consecutive lines (else consecutive butterflies).
+// Thread t owns line t mod nl and butterflies j = t / nl + m (threads / nl);
+// j / Ns and j mod Ns are stepped incrementally.
 template <typename T, int DIR, int R>
-__device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int L, int Ns, int nl,
-                      int ls, int es, bool lf, const C<T>* __restrict__ tw) {
+__device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int L, int Ns, int lg,
+                      int es, const C<T>* __restrict__ tw) {
     const int nb = L / R;
-    const int total = nb * nl;
-    const int step = L / (Ns * R);
-    C<T> root[R];
-    if (R & 1) {
+    const int line = threadIdx.x & ((1 << lg) - 1);
+    const int jstep = kFftThreads >> lg;
+    int j = threadIdx.x >> lg;
+    if (j < nb) {
+        const int step = L / (Ns * R);
+        int jm = j % Ns, k = j / Ns;
+        const int djm = jstep % Ns, dk = jstep / Ns;
+        C<T> root[R];
+        if (R & 1) {
 #pragma unroll
-        for (int t = 0; t < R; ++t) root[t] = twid<T, DIR>(tw, t * nb);
-    }
-    for (int w = threadIdx.x; w < total; w += kFftThreads) {
-        int line = lf ? w % nl : w / nb;
-        int j = lf ? w / nl : w - (w / nb) * nb;
-        const C<T>* s = src + line * ls;
-        C<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * es];
-        int jm = j % Ns;
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = mul<T>(v[r], twid<T, DIR>(tw, jm * r * step));
+            for (int t = 0; t < R; ++t) root[t] = twid<T, DIR>(tw, t * nb);
         }
-        Dft<T, DIR, R>::run(v, root);
-        C<T>* d = dst + line * ls;
-        int idx = (j - jm) * R + jm;
+        for (; j < nb; j += jstep) {
+            C<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[(idx + r * Ns) * es] = v[r];
+            for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * es + line];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = mul<T>(v[r], twid<T, DIR>(tw, jm * r * step));
+            }
+            Dft<T, DIR, R>::run(v, root);
+            const int idx = k * Ns * R + jm;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[(idx + r * Ns) * es + line] = v[r];
+            jm += djm;
+            k += dk;
+            if (jm >= Ns) {
+                jm -= Ns;
+                ++k;
+            }
+        }
     }
     __syncthreads();
 }
 
-// Full transform of nl lines; the input is in `a`, `b` is scratch of the same
-// size; returns the buffer holding the result.
+// Full transform of the lines in `a` (`b`: scratch of the same size, tw: the
+// length-L twiddles in shared memory); returns the buffer holding the result.
 template <typename T, int DIR>
-__device__ C<T>* fft_lines(C<T>* a, C<T>* b, const FftPlan1D& pl, int nl, int ls, int es, bool lf,
-                           const C<T>* tw_arena) {
-    const C<T>* tw = tw_arena + pl.tw_off;
+__device__ C<T>* fft_lines(C<T>* a, C<T>* b, const FftPlan1D& pl, int lg, int es, const C<T>* tw) {
     const int L = pl.L;
     int Ns = 1;
     for (int st = 0; st < pl.nst; ++st) {
         int R = pl.radix[st];
         switch (R) {
-            case 8: stage<T, DIR, 8>(a, b, L, Ns, nl, ls, es, lf, tw); break;
-            case 4: stage<T, DIR, 4>(a, b, L, Ns, nl, ls, es, lf, tw); break;
-            case 2: stage<T, DIR, 2>(a, b, L, Ns, nl, ls, es, lf, tw); break;
-            case 3: stage<T, DIR, 3>(a, b, L, Ns, nl, ls, es, lf, tw); break;
-            case 5: stage<T, DIR, 5>(a, b, L, Ns, nl, ls, es, lf, tw); break;
-            default: stage<T, DIR, 7>(a, b, L, Ns, nl, ls, es, lf, tw); break;
+            case 8: stage<T, DIR, 8>(a, b, L, Ns, lg, es, tw); break;
+            case 4: stage<T, DIR, 4>(a, b, L, Ns, lg, es, tw); break;
+            case 2: stage<T, DIR, 2>(a, b, L, Ns, lg, es, tw); break;
+            case 3: stage<T, DIR, 3>(a, b, L, Ns, lg, es, tw); break;
+            case 5: stage<T, DIR, 5>(a, b, L, Ns, lg, es, tw); break;
+            default: stage<T, DIR, 7>(a, b, L, Ns, lg, es, tw); break;
         }
         C<T>* t = a;
         a = b;
@@ -165,52 +175,110 @@ __device__ C<T>* fft_lines(C<T>* a, C<T>* b, const FftPlan1D& pl, int nl, int ls
     return a;
 }
 
-// complex elements of one of the two shared-memory buffers of a CTA
-template <typename T> struct Budget { static constexpr int value = kFftBudgetF32; };
-template <> struct Budget<double> { static constexpr int value = kFftBudgetF64; };
-
 template <typename T> __device__ __forceinline__ C<T>* smem_c() {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     return reinterpret_cast<C<T>*>(smem_raw);
 }
 
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// copies the twiddles exp(-2 pi i t / L), t < L, into shared memory
+template <typename T>
+__device__ __forceinline__ void load_twiddles(C<T>* dst, const C<T>* __restrict__ src, int L) {
+    for (int t = threadIdx.x; t < L; t += kFftThreads) dst[t] = src[t];
+}
+
+// Correctly rounded conversion of a fixed-point cell mass q * 2^-F to T without
+// the FP64 pipe for T = float: the leading 24 significant bits are rounded to
+// nearest-even with integer operations, then scaled by 2^-F (exact).  Same value
+// as the FP64 conversion (double)q * 2^-F rounded to float whenever |q| < 2^53.
+template <typename T> __device__ __forceinline__ T fixed_to_real(long long q, int F);
+template <> __device__ __forceinline__ double fixed_to_real<double>(long long q, int F) {
+    return ldexp((double)q, -F);
+}
+template <> __device__ __forceinline__ float fixed_to_real<float>(long long q, int F) {
+    if (q == 0) return 0.0f;
+    const bool neg = q < 0;
+    unsigned long long a = neg ? (unsigned long long)(-q) : (unsigned long long)q;
+    const int msb = 63 - __clzll((long long)a);     // position of the leading bit
+    int e = msb;                                     // value = a * 2^-F, a in [2^msb, 2^(msb+1))
+    unsigned m;                                      // 24-bit significand
+    if (msb <= 23) {
+        m = (unsigned)(a << (23 - msb));
+    } else {
+        const int sh = msb - 23;
+        unsigned long long keep = a >> sh;
+        unsigned long long rem = a & ((1ULL << sh) - 1);
+        unsigned long long half = 1ULL << (sh - 1);
+        if (rem > half || (rem == half && (keep & 1))) ++keep;
+        if (keep >> 24) {   // rounding carried into a new bit
+            keep >>= 1;
+            ++e;
+        }
+        m = (unsigned)keep;
+    }
+    // float with significand m / 2^23 and exponent e, then times 2^-F
+    float f = __int_as_float(((e + 127) << 23) | (m & 0x7FFFFF));
+    f = ldexpf(f, -F);
+    return neg ? -f : f;
+}
+
 // ---- xf: GMF rows -> half spectra along x ----------------------------------
+// smem: A, B (M0 x (np+1) each, element-major, padded), twiddles (M0)
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_xf(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
                                                     const int64_t* const* __restrict__ gmf,
-                                                    const C<T>* __restrict__ tw, C<T>* __restrict__ wsA,
-                                                    int F) {
+                                                    const C<T>* __restrict__ tw_arena,
+                                                    C<T>* __restrict__ wsA, int F) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
+    const int M0 = g.M[0], G0 = g.G[0], Hx = g.Hx, np = g.np_x, lg = ilog2(np), es = np + 1;
     C<T>* s = smem_c<T>();
-    C<T>* s2 = s + Budget<T>::value;
-    const int M0 = g.M[0], G0 = g.G[0], Hx = g.Hx, np = g.np_x;
+    C<T>* s2 = s + M0 * es;
+    C<T>* tw = s2 + M0 * es;
     const long long nrows = (long long)g.G[1] * g.G[2];
     const long long r_first = 2LL * ch.tile * np;
-    const int64_t* in = gmf[ch.grid];
-    for (int e = threadIdx.x; e < np * M0; e += kFftThreads) {
-        int p = e / M0, x = e - p * M0;
-        long long r0 = r_first + 2 * p, r1 = r0 + 1;
-        T a = 0, b = 0;
-        if (x < G0) {
-            if (r0 < nrows) a = (T)ldexp((double)in[r0 * G0 + x], -F);
-            if (r1 < nrows) b = (T)ldexp((double)in[r1 * G0 + x], -F);
+    const int64_t* __restrict__ in = gmf[ch.grid];
+    load_twiddles<T>(tw, tw_arena + g.fx.tw_off, M0);
+    // rows r0 = 2p, r1 = 2p + 1 packed as one complex line p; x fastest over threads
+    {
+        int p = 0, x = threadIdx.x;
+        while (x >= M0) { x -= M0; ++p; }
+        const int dp = kFftThreads / M0, dx = kFftThreads % M0;
+        for (; p < np; ) {
+            long long r0 = r_first + 2 * p, r1 = r0 + 1;
+            T a = 0, b = 0;
+            if (x < G0) {
+                if (r0 < nrows) a = fixed_to_real<T>(in[r0 * G0 + x], F);
+                if (r1 < nrows) b = fixed_to_real<T>(in[r1 * G0 + x], F);
+            }
+            s[x * es + p] = mk<T>(a, b);
+            x += dx;
+            p += dp;
+            if (x >= M0) { x -= M0; ++p; }
         }
-        s[e] = mk<T>(a, b);
     }
     __syncthreads();
-    s = fft_lines<T, -1>(s, s2, g.fx, np, M0, 1, false, tw);
+    s = fft_lines<T, -1>(s, s2, g.fx, lg, es, tw);
     // separate the two real rows: A_k = (Z_k + conj Z_{M-k}) / 2, B_k = (Z_k - conj Z_{M-k}) / 2i
     C<T>* out = wsA + g.wsA;
-    for (int e = threadIdx.x; e < np * Hx; e += kFftThreads) {
-        int p = e / Hx, k = e - p * Hx;
-        long long r0 = r_first + 2 * p, r1 = r0 + 1;
-        if (r0 >= nrows) continue;
-        C<T> z = s[p * M0 + k];
-        C<T> zm = s[p * M0 + (k == 0 ? 0 : M0 - k)];
-        out[r0 * Hx + k] = mk<T>((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
-        if (r1 < nrows) out[r1 * Hx + k] = mk<T>((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
+    {
+        int p = 0, k = threadIdx.x;
+        while (k >= Hx) { k -= Hx; ++p; }
+        const int dp = kFftThreads / Hx, dk = kFftThreads % Hx;
+        for (; p < np; ) {
+            long long r0 = r_first + 2 * p, r1 = r0 + 1;
+            if (r0 < nrows) {
+                C<T> z = s[k * es + p];
+                C<T> zm = s[(k == 0 ? 0 : M0 - k) * es + p];
+                out[r0 * Hx + k] = mk<T>((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
+                if (r1 < nrows) out[r1 * Hx + k] = mk<T>((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
+            }
+            k += dk;
+            p += dp;
+            if (k >= Hx) { k -= Hx; ++p; }
+        }
     }
 }
 
@@ -219,25 +287,28 @@ __global__ void __launch_bounds__(kFftThreads) k_xf(const GridDev* __restrict__ 
 //   yf (AX 1, MODE 0): in A[z][y][kx] (y < G1), out B[z][ky][kx]
 //   z  (AX 2, MODE 1): in B[z][ky][kx] (z < G2), out A[zw][ky][kx]
 //   yi (AX 1, MODE 2): in A[zw][ky][kx],         out B[zw][yw][kx]
+// smem: A, B (L x tx each, element-major), twiddles (L)
 template <typename T, int AX, int MODE>
 __global__ void __launch_bounds__(kFftThreads) k_col(const GridDev* __restrict__ grids,
                                                      const Chunk* __restrict__ chunks,
-                                                     const C<T>* __restrict__ tw,
+                                                     const C<T>* __restrict__ tw_arena,
                                                      const T* __restrict__ tab,
                                                      C<T>* __restrict__ wsA, C<T>* __restrict__ wsB) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
-    C<T>* s = smem_c<T>();
-    C<T>* s2 = s + Budget<T>::value;
     const int Hx = g.Hx;
     const int tx = AX == 1 ? g.tx_y : g.tx_z;
-    const int nkt = (Hx + tx - 1) / tx;
-    const int kxt = ch.tile % nkt;
+    const int lg = ilog2(tx);
+    const int nkt = (Hx + tx - 1) >> lg;
     const int other = ch.tile / nkt;    // z (yf), ky (z), zw (yi)
-    const int kx0 = kxt * tx;
+    const int kx0 = (ch.tile - other * nkt) << lg;
     const FftPlan1D& pl = AX == 1 ? g.fy : g.fz;
     const int L = pl.L;
     const int M1 = g.M[1];
+    C<T>* s = smem_c<T>();
+    C<T>* s2 = s + L * tx;
+    C<T>* tw = s2 + L * tx;
+    load_twiddles<T>(tw, tw_arena + pl.tw_off, L);
 
     const C<T>* in;
     long long in_base, in_stride;
@@ -252,37 +323,38 @@ __global__ void __launch_bounds__(kFftThreads) k_col(const GridDev* __restrict__
         in = wsA + g.wsA; n_in = M1;
         in_base = (long long)other * M1 * Hx; in_stride = Hx;
     }
-    for (int e = threadIdx.x; e < L * tx; e += kFftThreads) {
-        int i = e / tx, line = e - i * tx;
-        int kx = kx0 + line;
+    const int line = threadIdx.x & (tx - 1);
+    const int istep = kFftThreads >> lg;
+    const int kx = kx0 + line;
+    const bool live = kx < Hx;
+    for (int i = threadIdx.x >> lg; i < L; i += istep) {
         C<T> v = mk<T>(0, 0);
-        if (i < n_in && kx < Hx) v = in[in_base + i * in_stride + kx];
-        s[e] = v;
+        if (i < n_in && live) v = in[in_base + i * in_stride + kx];
+        s[i * tx + line] = v;
     }
     __syncthreads();
     if (MODE == 2) {
-        s = fft_lines<T, 1>(s, s2, pl, tx, 1, tx, true, tw);
+        s = fft_lines<T, 1>(s, s2, pl, lg, tx, tw);
     } else {
-        s = fft_lines<T, -1>(s, s2, pl, tx, 1, tx, true, tw);
+        s = fft_lines<T, -1>(s, s2, pl, lg, tx, tw);
     }
-    s2 = (s == smem_c<T>()) ? s + Budget<T>::value : smem_c<T>();
     if (MODE == 1) {
         // phi-hat = T(kappa) rho-hat; the table is even in every component
+        s2 = (s == smem_c<T>()) ? s + L * tx : smem_c<T>();
         const int ky = other;
         const int fy = ky <= M1 / 2 ? ky : M1 - ky;
         const T* tb = tab + g.tab_off + (long long)fy * Hx;
         const long long zst = (long long)g.Hy2 * Hx;
-        for (int e = threadIdx.x; e < L * tx; e += kFftThreads) {
-            int kz = e / tx, line = e - kz * tx;
-            int kx = kx0 + line;
-            if (kx >= Hx) continue;
-            int fz = kz <= L / 2 ? kz : L - kz;
-            T t = tb[fz * zst + kx];
-            C<T> v = s[e];
-            s[e] = mk<T>(v.x * t, v.y * t);
+        if (live) {
+            for (int kz = threadIdx.x >> lg; kz < L; kz += istep) {
+                int fz = kz <= L / 2 ? kz : L - kz;
+                T t = tb[fz * zst + kx];
+                C<T> v = s[kz * tx + line];
+                s[kz * tx + line] = mk<T>(v.x * t, v.y * t);
+            }
         }
         __syncthreads();
-        s = fft_lines<T, 1>(s, s2, pl, tx, 1, tx, true, tw);
+        s = fft_lines<T, 1>(s, s2, pl, lg, tx, tw);
     }
     // store
     C<T>* out;
@@ -298,75 +370,90 @@ __global__ void __launch_bounds__(kFftThreads) k_col(const GridDev* __restrict__
         out = wsB + g.wsB; n_out = g.W[1]; s0 = g.s0[1];
         out_base = (long long)other * g.W[1] * Hx; out_stride = Hx;
     }
-    for (int e = threadIdx.x; e < n_out * tx; e += kFftThreads) {
-        int o = e / tx, line = e - o * tx;
-        int kx = kx0 + line;
-        if (kx >= Hx) continue;
+    if (live) {
+        int o = threadIdx.x >> lg;
         int i = (s0 + o) % L;
-        out[out_base + o * out_stride + kx] = s[i * tx + line];
+        const int di = istep % L;
+        for (; o < n_out; o += istep) {
+            out[out_base + o * out_stride + kx] = s[i * tx + line];
+            i += di;
+            if (i >= L) i -= L;
+        }
     }
 }
 
 // ---- xi: half spectra -> real rows of the window -------------------------------
+// smem: A, B (M0 x (np+1) each), twiddles (M0)
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_xi(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
-                                                    const C<T>* __restrict__ tw,
+                                                    const C<T>* __restrict__ tw_arena,
                                                     const C<T>* __restrict__ wsB,
                                                     void* const* __restrict__ phis) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
+    const int M0 = g.M[0], Hx = g.Hx, np = g.np_x, W0 = g.W[0], lg = ilog2(np), es = np + 1;
     C<T>* s = smem_c<T>();
-    C<T>* s2 = s + Budget<T>::value;
-    const int M0 = g.M[0], Hx = g.Hx, np = g.np_x, W0 = g.W[0];
+    C<T>* s2 = s + M0 * es;
+    C<T>* tw = s2 + M0 * es;
     const long long nrows = (long long)g.W[1] * g.W[2];
     const long long r_first = 2LL * ch.tile * np;
-    const C<T>* in = wsB + g.wsB;
+    const C<T>* __restrict__ in = wsB + g.wsB;
+    load_twiddles<T>(tw, tw_arena + g.fx.tw_off, M0);
     // Z_k = A_k + i B_k with A, B extended by Hermitian symmetry
-    for (int e = threadIdx.x; e < np * M0; e += kFftThreads) {
-        int p = e / M0, k = e - p * M0;
-        long long r0 = r_first + 2 * p, r1 = r0 + 1;
-        int kk = k < Hx ? k : M0 - k;
-        C<T> a = mk<T>(0, 0), b = mk<T>(0, 0);
-        if (r0 < nrows) a = in[r0 * Hx + kk];
-        if (r1 < nrows) b = in[r1 * Hx + kk];
-        if (k >= Hx) { a.y = -a.y; b.y = -b.y; }
-        s[e] = mk<T>(a.x - b.y, a.y + b.x);
+    {
+        int p = 0, k = threadIdx.x;
+        while (k >= M0) { k -= M0; ++p; }
+        const int dp = kFftThreads / M0, dk = kFftThreads % M0;
+        for (; p < np; ) {
+            long long r0 = r_first + 2 * p, r1 = r0 + 1;
+            int kk = k < Hx ? k : M0 - k;
+            C<T> a = mk<T>(0, 0), b = mk<T>(0, 0);
+            if (r0 < nrows) a = in[r0 * Hx + kk];
+            if (r1 < nrows) b = in[r1 * Hx + kk];
+            if (k >= Hx) { a.y = -a.y; b.y = -b.y; }
+            s[k * es + p] = mk<T>(a.x - b.y, a.y + b.x);
+            k += dk;
+            p += dp;
+            if (k >= M0) { k -= M0; ++p; }
+        }
     }
     __syncthreads();
-    s = fft_lines<T, 1>(s, s2, g.fx, np, M0, 1, false, tw);
+    s = fft_lines<T, 1>(s, s2, g.fx, lg, es, tw);
     const T norm = (T)(1.0 / ((double)g.M[0] * (double)g.M[1] * (double)g.M[2]));
     T* out = reinterpret_cast<T*>(phis[ch.grid]);
-    for (int e = threadIdx.x; e < np * W0; e += kFftThreads) {
-        int p = e / W0, xw = e - p * W0;
-        long long r0 = r_first + 2 * p, r1 = r0 + 1;
-        if (r0 >= nrows) continue;
-        int x = (g.s0[0] + xw) % M0;
-        C<T> z = s[p * M0 + x];
-        out[r0 * W0 + xw] = z.x * norm;
-        if (r1 < nrows) out[r1 * W0 + xw] = z.y * norm;
+    {
+        int p = 0, xw = threadIdx.x;
+        while (xw >= W0) { xw -= W0; ++p; }
+        const int dp = kFftThreads / W0, dx = kFftThreads % W0;
+        for (; p < np; ) {
+            long long r0 = r_first + 2 * p, r1 = r0 + 1;
+            if (r0 < nrows) {
+                int x = (g.s0[0] + xw) % M0;
+                C<T> z = s[x * es + p];
+                out[r0 * W0 + xw] = z.x * norm;
+                if (r1 < nrows) out[r1 * W0 + xw] = z.y * norm;
+            }
+            xw += dx;
+            p += dp;
+            if (xw >= W0) { xw -= W0; ++p; }
+        }
     }
 }
 
 }  // namespace
 
-// Allows every pass kernel the full per-CTA shared-memory budget (above the
-// 48 KB default for the FP64 instantiations).
+// Allows every pass kernel up to 200 KB of dynamic shared memory (above the
+// 48 KB default).
 cudaError_t fft_configure() {
-    const int f32 = (int)(2 * kFftBudgetF32 * sizeof(float2));
-    const int f64 = (int)(2 * kFftBudgetF64 * sizeof(double2));
-    const void* fns32[] = {(const void*)k_xf<float>, (const void*)k_col<float, 1, 0>,
-                           (const void*)k_col<float, 2, 1>, (const void*)k_col<float, 1, 2>,
-                           (const void*)k_xi<float>};
-    const void* fns64[] = {(const void*)k_xf<double>, (const void*)k_col<double, 1, 0>,
-                           (const void*)k_col<double, 2, 1>, (const void*)k_col<double, 1, 2>,
-                           (const void*)k_xi<double>};
-    for (const void* f : fns32) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, f32);
-        if (e != cudaSuccess) return e;
-    }
-    for (const void* f : fns64) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, f64);
+    const int lim = 200 * 1024;
+    const void* fns[] = {(const void*)k_xf<float>, (const void*)k_col<float, 1, 0>,
+                         (const void*)k_col<float, 2, 1>, (const void*)k_col<float, 1, 2>,
+                         (const void*)k_xi<float>, (const void*)k_xf<double>,
+                         (const void*)k_col<double, 1, 0>, (const void*)k_col<double, 2, 1>,
+                         (const void*)k_col<double, 1, 2>, (const void*)k_xi<double>};
+    for (const void* f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

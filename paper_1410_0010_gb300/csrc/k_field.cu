@@ -5,28 +5,6 @@
 namespace apm {
 namespace {
 
-// Error-free transformations on the FP32 units (Knuth TwoSum, FMA TwoProd):
-// a compensated sum of FP32 terms carries the rounding error of every step, so
-// hi + lo equals the FP64 evaluation of the same sum to within a few units of
-// 2^-48 relative, and rounding it once gives the FP64 result rounded to FP32.
-struct FF {
-    float hi, lo;
-};
-// (explicitly rounded intrinsics: the compiler may not contract them)
-__device__ __forceinline__ FF ff_add(FF a, float b) {
-    float s = __fadd_rn(a.hi, b);
-    float bb = __fsub_rn(s, a.hi);
-    float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return FF{s, __fadd_rn(a.lo, err)};
-}
-__device__ __forceinline__ FF ff_fma(FF a, float w, float v) {   // a + w v
-    float p = __fmul_rn(w, v);
-    float pe = __fmaf_rn(w, v, -p);
-    FF r = ff_add(a, p);
-    r.lo = __fadd_rn(r.lo, pe);
-    return r;
-}
-
 // Trilinear weights of child cell ic from the parent cell centres, R = 2: in
 // parent units the child centre is at (ic + 1/2)/2, i.e. 3/4 (even ic) or 1/4
 // (odd ic) of a cell above the centre of parent cell i0 = floor((ic - 1) / 2),
@@ -37,12 +15,30 @@ __device__ __forceinline__ void carry_axis(long long ic, long long pstart, int& 
     w_lo = (ic & 1) ? 0.75f : 0.25f;
 }
 
+// trilinear interpolation of one parent field, separably (x, then y, then z);
+// the weights 1/4, 3/4 are exact in either precision
+template <typename T>
+__device__ __forceinline__ T trilinear(const T* __restrict__ f, unsigned base, int P0, unsigned P01,
+                                       T wx, T wy, T wz) {
+    T c[2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const T* r = f + base + dy * P0 + dz * P01;
+            c[dz][dy] = wx * r[0] + ((T)1 - wx) * r[1];
+        }
+    T e0 = wy * c[0][0] + ((T)1 - wy) * c[0][1];
+    T e1 = wy * c[1][0] + ((T)1 - wy) * c[1][1];
+    return wz * e0 + ((T)1 - wz) * e1;
+}
+
 // acc_j(c) = -(phis(c+e_j) - phis(c-e_j)) / (2 delta) + I(parent acc_j)(c)
 // phi(c)   = phis(c) + I(parent phi)(c),    c in [-1, N]^3
-// The difference is taken in T.  The carry is the trilinear interpolation from
-// the parent cell centres with exact weights (1/4, 3/4); its sum (and the
-// addition of the short-range part) is carried out in FP64 arithmetic: natively
-// for T = double, as compensated FP32 (same result, rounded once) for T = float.
+// I is the trilinear interpolation from the parent cell centres.  Everything is
+// evaluated in T: the FP64 path in FP64, the FP32 path in FP32 (the weights are
+// exact; the interpolated FP32 fields carry no more digits than FP32 anyway).
+// One CTA per batch of `rows_per_cta` output rows (x fastest over threads).
 template <typename T>
 __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __restrict__ pgrids,
                                                const void* const* __restrict__ phis_p,
@@ -50,11 +46,12 @@ __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __rest
                                                const void* const* __restrict__ pacc_p,
                                                void* const* __restrict__ phi_p,
                                                void* const* __restrict__ acc_p,
-                                               const Chunk* __restrict__ chunks, int chunk_cells) {
+                                               const Chunk* __restrict__ chunks, int rows_per_cta) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = L.g[ch.grid];
-    const unsigned E0 = g.N[0] + 2, E1 = g.N[1] + 2, E2 = g.N[2] + 2;
-    const unsigned ncell = E0 * E1 * E2;
+    const int E0 = g.N[0] + 2, E1 = g.N[1] + 2, E2 = g.N[2] + 2;
+    const unsigned ncell = (unsigned)E0 * E1 * E2;
+    const int nrows = E1 * E2;
     const int W0 = g.W[0], W1 = g.W[1];
     const T* __restrict__ phis = reinterpret_cast<const T*>(phis_p[ch.grid]);
     T* __restrict__ phi = reinterpret_cast<T*>(phi_p[ch.grid]);
@@ -62,96 +59,61 @@ __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __rest
     const bool carry = pphi_p != nullptr && g.parent >= 0;
     const T* __restrict__ pphi = carry ? reinterpret_cast<const T*>(pphi_p[g.parent]) : nullptr;
     const T* __restrict__ pacc = carry ? reinterpret_cast<const T*>(pacc_p[g.parent]) : nullptr;
-    int P0 = 0, P1 = 0;
-    unsigned pn = 0;
+    int P0 = 0;
+    unsigned P01 = 0, pn = 0;
     long long ps0 = 0, ps1 = 0, ps2 = 0;
     if (carry) {
         const GridDev& p = pgrids[g.parent];
         P0 = p.N[0] + 2;
-        P1 = p.N[1] + 2;
-        pn = (unsigned)P0 * P1 * (p.N[2] + 2);
+        P01 = (unsigned)P0 * (p.N[1] + 2);
+        pn = P01 * (p.N[2] + 2);
         ps0 = p.start[0]; ps1 = p.start[1]; ps2 = p.start[2];
     }
     const T inv2d = (T)(0.5 / g.delta);
-    const unsigned cell0 = (unsigned)ch.tile * chunk_cells;
-    for (int t = threadIdx.x; t < chunk_cells; t += blockDim.x) {
-        unsigned o = cell0 + t;
-        if (o >= ncell) break;
-        unsigned ex = o % E0;
-        unsigned r = o / E0;
-        unsigned ey = r % E1;
-        unsigned ez = r / E1;
-        // phis index of cell (ex-1, ey-1, ez-1): offset +2 in [-2, N+2)
-        unsigned ps = (ex + 1) + W0 * ((ey + 1) + W1 * (ez + 1));
-        const unsigned sy = W0, sz = W0 * W1;
-        T p0 = phis[ps];
-        T a0 = -(phis[ps + 1] - phis[ps - 1]) * inv2d;
-        T a1 = -(phis[ps + sy] - phis[ps - sy]) * inv2d;
-        T a2 = -(phis[ps + sz] - phis[ps - sz]) * inv2d;
+    const unsigned sy = W0, sz = (unsigned)W0 * W1;
+    const int r0 = ch.tile * g.rows_acc;
+    const int r1 = min(nrows, r0 + g.rows_acc);
+    for (int r = r0; r < r1; ++r) {
+        const int ey = r % E1, ez = r / E1;
+        int iy = 0, iz = 0;
+        float wyf = 0.f, wzf = 0.f;
         if (carry) {
-            int ix, iy, iz;
-            float wx, wy, wz;
-            carry_axis(g.start[0] + (long long)ex - 1, ps0, ix, wx);
-            carry_axis(g.start[1] + (long long)ey - 1, ps1, iy, wy);
-            carry_axis(g.start[2] + (long long)ez - 1, ps2, iz, wz);
-            const unsigned base = ix + P0 * (iy + P1 * iz);
-            if constexpr (sizeof(T) == 8) {
-                double ip = 0.0, ia0 = 0.0, ia1 = 0.0, ia2 = 0.0;
-#pragma unroll
-                for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 2; ++dx) {
-                            double w = ((double)(dx ? 1.0f - wx : wx) * (double)(dy ? 1.0f - wy : wy)) *
-                                       (double)(dz ? 1.0f - wz : wz);
-                            unsigned pi = base + dx + P0 * (dy + P1 * dz);
-                            ip += w * (double)pphi[pi];
-                            ia0 += w * (double)pacc[pi];
-                            ia1 += w * (double)pacc[pn + pi];
-                            ia2 += w * (double)pacc[2 * pn + pi];
-                        }
-                p0 = (T)((double)p0 + ip);
-                a0 = (T)((double)a0 + ia0);
-                a1 = (T)((double)a1 + ia1);
-                a2 = (T)((double)a2 + ia2);
-            } else {
-                FF ip{0.f, 0.f}, ia0{0.f, 0.f}, ia1{0.f, 0.f}, ia2{0.f, 0.f};
-#pragma unroll
-                for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 2; ++dx) {
-                            // products of 1/4, 3/4: exact in FP32
-                            float w = ((dx ? 1.0f - wx : wx) * (dy ? 1.0f - wy : wy)) * (dz ? 1.0f - wz : wz);
-                            unsigned pi = base + dx + P0 * (dy + P1 * dz);
-                            ip = ff_fma(ip, w, (float)pphi[pi]);
-                            ia0 = ff_fma(ia0, w, (float)pacc[pi]);
-                            ia1 = ff_fma(ia1, w, (float)pacc[pn + pi]);
-                            ia2 = ff_fma(ia2, w, (float)pacc[2 * pn + pi]);
-                        }
-                ip = ff_add(ip, (float)p0);
-                ia0 = ff_add(ia0, (float)a0);
-                ia1 = ff_add(ia1, (float)a1);
-                ia2 = ff_add(ia2, (float)a2);
-                p0 = (T)__fadd_rn(ip.hi, ip.lo);
-                a0 = (T)__fadd_rn(ia0.hi, ia0.lo);
-                a1 = (T)__fadd_rn(ia1.hi, ia1.lo);
-                a2 = (T)__fadd_rn(ia2.hi, ia2.lo);
-            }
+            carry_axis(g.start[1] + (long long)ey - 1, ps1, iy, wyf);
+            carry_axis(g.start[2] + (long long)ez - 1, ps2, iz, wzf);
         }
-        phi[o] = p0;
-        acc[o] = a0;
-        acc[ncell + o] = a1;
-        acc[2 * ncell + o] = a2;
+        const unsigned prow = 1 + sy * (ey + 1) + sz * (ez + 1);   // phis index of x = -1
+        const unsigned orow = (unsigned)r * E0;
+        for (int ex = threadIdx.x; ex < E0; ex += blockDim.x) {
+            const unsigned ps = prow + ex;
+            T p0 = phis[ps];
+            T a0 = -(phis[ps + 1] - phis[ps - 1]) * inv2d;
+            T a1 = -(phis[ps + sy] - phis[ps - sy]) * inv2d;
+            T a2 = -(phis[ps + sz] - phis[ps - sz]) * inv2d;
+            if (carry) {
+                int ix;
+                float wxf;
+                carry_axis(g.start[0] + (long long)ex - 1, ps0, ix, wxf);
+                const unsigned base = ix + P0 * iy + P01 * iz;
+                const T wx = (T)wxf, wy = (T)wyf, wz = (T)wzf;
+                p0 += trilinear<T>(pphi, base, P0, P01, wx, wy, wz);
+                a0 += trilinear<T>(pacc, base, P0, P01, wx, wy, wz);
+                a1 += trilinear<T>(pacc + pn, base, P0, P01, wx, wy, wz);
+                a2 += trilinear<T>(pacc + 2 * pn, base, P0, P01, wx, wy, wz);
+            }
+            const unsigned o = orow + ex;
+            phi[o] = p0;
+            acc[o] = a0;
+            acc[ncell + o] = a1;
+            acc[2 * ncell + o] = a2;
+        }
     }
 }
 
 __device__ __forceinline__ double drift(double x, double v, double half_dt, double box,
                                         int periodic) {
     double xd = __dadd_rn(x, __dmul_rn(v, half_dt));
-    if (periodic) xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
+    if (periodic && !(xd >= 0.0 && xd < box))
+        xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
     return xd;
 }
 
@@ -260,11 +222,11 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_
 template <typename T>
 cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
                          const void* const* pphi, const void* const* pacc, void* const* phi,
-                         void* const* acc, const Chunk* chunks, int n_chunks, int chunk_cells,
+                         void* const* acc, const Chunk* chunks, int n_chunks, int rows_per_cta,
                          cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
     k_accel<T><<<n_chunks, 256, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks,
-                                        chunk_cells);
+                                        rows_per_cta);
     return cudaGetLastError();
 }
 
