@@ -34,9 +34,22 @@
  *   R8  FD gradient: two-point centred difference, D_j = sin(k_j delta)/delta.
  *   R10 Parent carry: potential and acceleration, trilinear interpolation from
  *       parent cell centres in FP64 (Sec. 2.2, last paragraph).
- *   Fixed point: cell masses are int64 with F fractional bits; each particle's
- *   27 contributions are rint((m*w)*2^F) with the centre cell receiving
- *   rint(m*2^F) minus the other 26, so integer mass is conserved exactly.
+ *   R11 TSC weights in fixed point (the paper fixes the TSC assignment of
+ *       Sec. 2, not its arithmetic): the drifted coordinate in root cells is
+ *       rounded once to X = rint(x/delta0 2^31), the same for every level; on
+ *       level l (2^l cells per root cell) the cell is i = floor(X / 2^(31-l))
+ *       and t = (X mod 2^(31-l)) / 2^(31-l) the offset from its lower face;
+ *       the three weights of the cells i-1, i, i+1 are (1-t)^2/2,
+ *       3/4 - (t-1/2)^2, t^2/2, computed as
+ *       exact integers on the scale 2^63 (they sum to 2^63 exactly); the 3-D
+ *       weight of the 26 outer cells is the product x, then y, then z, each
+ *       product rounded half up to the scale 2^63, and the centre cell's weight
+ *       is 2^63 minus theirs (deposit and interpolation weights sum to one
+ *       exactly).
+ *   Fixed point: cell masses are int64 with F fractional bits.  With
+ *   M = rint(m 2^F), each of the 26 outer cells receives (|M| w + 2^62) >> 63
+ *   (sign of M), the centre cell M minus the other 26, so integer mass is
+ *   conserved exactly and the sum is independent of particle order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,7 +63,7 @@
 
 /* status bits returned by the deposit routines */
 #define ORC_ST_OVERFLOW 1  /* |m 2^F| >= 2^62: particle skipped */
-#define ORC_ST_OUT_OF_BOX 2 /* isolated root: particle outside [0, N delta) */
+#define ORC_ST_OUT_OF_BOX 2 /* isolated root: drifted particle outside [0, box) */
 
 static int64_t floor_div(int64_t a, int64_t b) {
     int64_t q = a / b;
@@ -320,17 +333,59 @@ double orc_drift(double x, double v, double half_dt, double box, int periodic) {
     return xd;
 }
 
-/* TSC weights along one axis (Sec. 2, n = 3^3 cells): cell i = floor(x/delta)  */
-/* holds the particle, d = (u - i) - 1/2 its offset from that cell's centre.   */
-/* w[0], w[1], w[2] go to cells i-1, i, i+1.                                    */
+/* Fixed-point position (reading R11): the drifted coordinate in root cells,
+ * u0 = x / delta0, rounded to X = rint(u0 2^31).  Every level reads the same X:
+ * level l has 2^l cells per root cell, so its cell index and offset are the
+ * high and low bits of X with 31 - l fraction bits. */
+#define ORC_POS_BITS 31
+int64_t orc_position_fixed(double x, double delta0) {
+    return (int64_t)rint(ldexp(x / delta0, ORC_POS_BITS));
+}
+
+/* The fixed-point position of a drifted coordinate xd, made canonical: on a
+ * periodic domain X is taken modulo the box (N0 2^31); on an isolated domain a
+ * coordinate inside [0, box) that rounds onto the upper face stays in the last
+ * root cell. */
+static int64_t pos_fixed(double xd, double delta0, double box, int periodic) {
+    int64_t X = orc_position_fixed(xd, delta0);
+    int64_t span = (int64_t)llround(box / delta0) << ORC_POS_BITS;
+    if (periodic) {
+        X %= span;
+        if (X < 0) X += span;
+    } else if (xd >= 0.0 && xd < box && X >= span) {
+        X = span - 1;
+    }
+    return X;
+}
+
+/* Fixed-point TSC weights along one axis (Sec. 2, n = 3^3 cells; reading R11)
+ * of the fixed-point position X on level `level`.  Returns the cell i holding
+ * the particle; w[0], w[1], w[2] (scale 2^63) go to cells i-1, i, i+1. */
+int64_t orc_tsc_fixed(int64_t X, int level, uint64_t w[3]) {
+    int P = ORC_POS_BITS - level;                        /* fraction bits */
+    int64_t i = X >> P;                                  /* floor(X / 2^P) */
+    uint64_t f = (uint64_t)(X - (i << P));               /* in [0, 2^P) */
+    uint64_t S = (uint64_t)1 << P;
+    int up = 62 - 2 * P;                                 /* scale 2^(2P+1) -> 2^63 */
+    w[2] = (f * f) << up;                                /* t^2/2            * 2^63 */
+    w[0] = ((S - f) * (S - f)) << up;                    /* (1-t)^2/2        * 2^63 */
+    w[1] = ((uint64_t)1 << 63) - w[0] - w[2];            /* 3/4 - (t-1/2)^2  * 2^63 */
+    return i;
+}
+
+/* product of two weights on the scale 2^63, rounded half up */
+static uint64_t wmul(uint64_t a, uint64_t b) {
+    unsigned __int128 p = (unsigned __int128)a * b + ((unsigned __int128)1 << 62);
+    return (uint64_t)(p >> 63);
+}
+
+/* TSC weights as doubles (w / 2^63 rounded to double) of a position x on a
+ * root grid of cell delta, for the pins */
 int64_t orc_tsc_weights(double x, double delta, double w[3]) {
-    double u = x / delta;
-    double fi = floor(u);
-    double d = (u - fi) - 0.5;
-    w[0] = 0.5 * ((0.5 - d) * (0.5 - d));
-    w[1] = 0.75 - d * d;
-    w[2] = 0.5 * ((0.5 + d) * (0.5 + d));
-    return (int64_t)fi;
+    uint64_t wi[3];
+    int64_t i = orc_tsc_fixed(orc_position_fixed(x, delta), 0, wi);
+    for (int k = 0; k < 3; ++k) w[k] = ldexp((double)wi[k], -63);
+    return i;
 }
 
 /* CIC weights with a cloud of one cell (Sec. 2): cells i0, i0+1.              */
@@ -349,34 +404,36 @@ int64_t orc_cic_weights(double x, double delta, double w[2]) {
 /* the box contributes).  The box spans global level cells                    */
 /* [lo_j, lo_j + G_j).  mode 0: cloud cells outside the box are dropped        */
 /* (refined grid); mode 1: folded into [0, G) (isolated root, reading R7);    */
-/* mode 2: wrapped modulo G (periodic root).  gmf is accumulated (+=).        */
+/* mode 2: wrapped modulo G (periodic root).  delta0: root cell; level: the    */
+/* grid's level (reading R11).  gmf is accumulated (+=).                      */
 /* Returns status bits (ORC_ST_*).                                            */
 /* ------------------------------------------------------------------------ */
 int orc_deposit(int64_t n, const double* px, const double* py, const double* pz,
                 const double* pvx, const double* pvy, const double* pvz, const double* pm,
-                double half_dt, double box, int periodic, double delta, const int64_t lo[3],
-                const int64_t G[3], int mode, int F, int64_t* gmf) {
+                double half_dt, double box, int periodic, double delta0, int level,
+                const int64_t lo[3], const int64_t G[3], int mode, int F, int64_t* gmf) {
     int status = 0;
     double scale = ldexp(1.0, F);
     double limit = ldexp(1.0, 62);
     for (int64_t p = 0; p < n; ++p) {
         double pos[3] = {px[p], py[p], pz[p]};
         double vel[3] = {pvx[p], pvy[p], pvz[p]};
-        double w[3][3];
+        uint64_t w[3][3];
         int64_t ic[3];
+        int outside = 0;
         for (int j = 0; j < 3; ++j) {
             double xd = orc_drift(pos[j], vel[j], half_dt, box, periodic);
-            ic[j] = orc_tsc_weights(xd, delta, w[j]);
+            if (!(xd >= 0.0 && xd < box)) outside = 1;
+            ic[j] = orc_tsc_fixed(pos_fixed(xd, delta0, box, periodic), level, w[j]);
         }
         double mq = pm[p] * scale;
         if (!(fabs(mq) < limit)) {
             status |= ORC_ST_OVERFLOW;
             continue;
         }
-        if (mode == 1) {
-            for (int j = 0; j < 3; ++j)
-                if (ic[j] < 0 || ic[j] >= G[j]) status |= ORC_ST_OUT_OF_BOX;
-        }
+        if (mode == 1 && outside) status |= ORC_ST_OUT_OF_BOX;
+        int64_t M = (int64_t)rint(mq);
+        uint64_t aM = (uint64_t)(M < 0 ? -M : M);
         /* fixed-point charges; centre cell takes the remainder */
         int64_t q[3][3][3];
         int64_t others = 0;
@@ -384,11 +441,11 @@ int orc_deposit(int64_t n, const double* px, const double* py, const double* pz,
             for (int b = 0; b < 3; ++b)
                 for (int a = 0; a < 3; ++a) {
                     if (a == 1 && b == 1 && c == 1) continue;
-                    double wt = (w[0][a] * w[1][b]) * w[2][c];
-                    q[c][b][a] = (int64_t)rint((pm[p] * wt) * scale);
+                    int64_t v = (int64_t)wmul(aM, wmul(wmul(w[0][a], w[1][b]), w[2][c]));
+                    q[c][b][a] = M < 0 ? -v : v;
                     others += q[c][b][a];
                 }
-        q[1][1][1] = (int64_t)rint(mq) - others;
+        q[1][1][1] = M - others;
         for (int c = 0; c < 3; ++c)
             for (int b = 0; b < 3; ++b)
                 for (int a = 0; a < 3; ++a) {
@@ -560,20 +617,33 @@ void orc_accel(const double* phis, const int64_t N[3], double delta, const int64
 /* ------------------------------------------------------------------------ */
 void orc_interp(int64_t n, const double* px, const double* py, const double* pz,
                 const double* pvx, const double* pvy, const double* pvz, double half_dt,
-                double box, int periodic, double delta, const int64_t start[3], const int64_t N[3],
-                int mode, const double* acc, const int32_t* owner, int32_t grid_id, double* out) {
+                double box, int periodic, double delta0, int level, const int64_t start[3],
+                const int64_t N[3], int mode, const double* acc, const int32_t* owner,
+                int32_t grid_id, double* out) {
     int64_t E[3] = {N[0] + 2, N[1] + 2, N[2] + 2};
     int64_t ncell = E[0] * E[1] * E[2];
     for (int64_t p = 0; p < n; ++p) {
         if (owner[p] != grid_id) continue;
         double pos[3] = {px[p], py[p], pz[p]};
         double vel[3] = {pvx[p], pvy[p], pvz[p]};
-        double w[3][3];
+        uint64_t w[3][3];
         int64_t ic[3];
         for (int j = 0; j < 3; ++j) {
             double xd = orc_drift(pos[j], vel[j], half_dt, box, periodic);
-            ic[j] = orc_tsc_weights(xd, delta, w[j]) - start[j];
+            ic[j] = orc_tsc_fixed(pos_fixed(xd, delta0, box, periodic), level, w[j]) - start[j];
         }
+        /* the 27 weights of the deposit: the centre takes 2^63 minus the other 26,
+           so the weights sum to one exactly, as the charges sum to the mass */
+        uint64_t wq[3][3][3];
+        uint64_t wsum = 0;
+        for (int c = 0; c < 3; ++c)
+            for (int b = 0; b < 3; ++b)
+                for (int aa = 0; aa < 3; ++aa) {
+                    if (aa == 1 && b == 1 && c == 1) continue;
+                    wq[c][b][aa] = wmul(wmul(w[0][aa], w[1][b]), w[2][c]);
+                    wsum += wq[c][b][aa];
+                }
+        wq[1][1][1] = ((uint64_t)1 << 63) - wsum;
         double a[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c < 3; ++c)
             for (int b = 0; b < 3; ++b)
@@ -584,7 +654,7 @@ void orc_interp(int64_t n, const double* px, const double* py, const double* pz,
                             if (g[j] < 0) g[j] = 0;
                             if (g[j] >= N[j]) g[j] = N[j] - 1;
                         }
-                    double wt = (w[0][aa] * w[1][b]) * w[2][c];
+                    double wt = ldexp((double)wq[c][b][aa], -63);
                     int64_t idx = (g[0] + 1) + E[0] * ((g[1] + 1) + E[1] * (g[2] + 1));
                     for (int j = 0; j < 3; ++j) a[j] += wt * acc[j * ncell + idx];
                 }
@@ -594,17 +664,18 @@ void orc_interp(int64_t n, const double* px, const double* py, const double* pz,
     }
 }
 
-/* Global level-cell index of a drifted position (used to find the finest     */
-/* grid that holds each particle, reading C11 of the design notes).           */
+/* Global level-cell index of a drifted position, the cell the TSC cloud is    */
+/* centred on (used to find the finest grid that holds each particle).        */
 void orc_cells(int64_t n, const double* px, const double* py, const double* pz,
                const double* pvx, const double* pvy, const double* pvz, double half_dt,
-               double box, int periodic, double delta, int64_t* cells /* 3 x n */) {
+               double box, int periodic, double delta0, int level, int64_t* cells /* 3 x n */) {
     for (int64_t p = 0; p < n; ++p) {
         double pos[3] = {px[p], py[p], pz[p]};
         double vel[3] = {pvx[p], pvy[p], pvz[p]};
         for (int j = 0; j < 3; ++j) {
             double xd = orc_drift(pos[j], vel[j], half_dt, box, periodic);
-            cells[j * n + p] = (int64_t)floor(xd / delta);
+            uint64_t w[3];
+            cells[j * n + p] = orc_tsc_fixed(pos_fixed(xd, delta0, box, periodic), level, w);
         }
     }
 }

@@ -54,7 +54,7 @@ def lib():
         L.orc_cic_weights.restype = i64
         L.orc_cic_weights.argtypes = [d, d, P]
         L.orc_deposit.restype = ci
-        L.orc_deposit.argtypes = [i64, P, P, P, P, P, P, P, d, d, ci, d, P, P, ci, ci, P]
+        L.orc_deposit.argtypes = [i64, P, P, P, P, P, P, P, d, d, ci, d, ci, P, P, ci, ci, P]
         L.orc_gas.restype = None
         L.orc_gas.argtypes = [P, P, i64, P, P, P, P, ci, d, ci, P]
         L.orc_solve.restype = None
@@ -62,9 +62,9 @@ def lib():
         L.orc_accel.restype = None
         L.orc_accel.argtypes = [P, P, d, P, P, P, P, P, ci, P, P]
         L.orc_interp.restype = None
-        L.orc_interp.argtypes = [i64, P, P, P, P, P, P, d, d, ci, d, P, P, ci, P, P, i32, P]
+        L.orc_interp.argtypes = [i64, P, P, P, P, P, P, d, d, ci, d, ci, P, P, ci, P, P, i32, P]
         L.orc_cells.restype = None
-        L.orc_cells.argtypes = [i64, P, P, P, P, P, P, d, d, ci, d, P]
+        L.orc_cells.argtypes = [i64, P, P, P, P, P, P, d, d, ci, d, ci, P]
         _lib = L
     return _lib
 
@@ -192,6 +192,11 @@ class Plan:
     kind: int      # green table kind: 0 refined, 1 periodic root, 2 isolated root
 
 
+def root_delta(cfg, grids):
+    """Root cell size; fixed-point positions are counted in 2^-31 root cells."""
+    return cfg.box / grids[0].dims[0]
+
+
 def plan_grid(cfg, grids, gi):
     g = grids[gi]
     N0 = grids[0].dims[0]
@@ -267,8 +272,9 @@ def deposit(cfg, grids, gi, particles, half_dt, gas=None, parent_gas=None):
                       cfg.refine, plan.delta, cfg.mass_frac_bits, _p(gmf))
     (x, y, z, vx, vy, vz, m), n = _parts(particles)
     st = lib().orc_deposit(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(m), float(half_dt),
-                           cfg.box, int(cfg.periodic), plan.delta, _p(_i64(plan.lo)),
-                           _p(_i64(plan.G)), plan.mode, cfg.mass_frac_bits, _p(gmf))
+                           cfg.box, int(cfg.periodic), root_delta(cfg, grids), plan.level,
+                           _p(_i64(plan.lo)), _p(_i64(plan.G)), plan.mode, cfg.mass_frac_bits,
+                           _p(gmf))
     return gmf, st
 
 
@@ -314,10 +320,9 @@ def owners(cfg, grids, particles, half_dt):
     levels = sorted(set(g.level for g in grids))
     cells = {}
     for lev in levels:
-        delta = cfg.box / (N0 * cfg.refine ** lev)
         c = np.zeros((3, n), dtype=np.int64)
         lib().orc_cells(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), float(half_dt), cfg.box,
-                        int(cfg.periodic), delta, _p(c))
+                        int(cfg.periodic), root_delta(cfg, grids), lev, _p(c))
         cells[lev] = c
     for gi, g in enumerate(grids):
         c = cells[g.level]
@@ -339,8 +344,8 @@ def interp(cfg, grids, gi, acc, particles, half_dt, owner, out):
     own = np.ascontiguousarray(owner, dtype=np.int32)
     mode = 1 if plan.mode == 1 else 0
     lib().orc_interp(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), float(half_dt), cfg.box,
-                     int(cfg.periodic), plan.delta, _p(_i64(g.start)), _p(_i64(g.dims)), mode,
-                     _p(a), _p(own), int(gi), _p(out))
+                     int(cfg.periodic), root_delta(cfg, grids), plan.level, _p(_i64(g.start)),
+                     _p(_i64(g.dims)), mode, _p(a), _p(own), int(gi), _p(out))
 
 
 @dataclass

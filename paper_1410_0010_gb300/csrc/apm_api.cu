@@ -424,6 +424,13 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
     if (!c || !grids) return APM_E_INVALID;
     apm_status st = validate(c->cfg, grids, n);
     if (st != APM_OK) return st;
+    // fixed-point positions: 2^-31 root cells, at least 11 fraction bits on the
+    // finest level, |x / delta0| 2^31 < 2^51
+    {
+        int maxlev = 0;
+        for (int i = 0; i < n; ++i) maxlev = std::max(maxlev, grids[i].level);
+        if (maxlev > 20 || grids[0].dims[0] > (1 << 20)) return APM_E_UNSUPPORTED;
+    }
     if (c->has_hier) free_hierarchy(c);
     const apm_config& cfg = c->cfg;
     const bool periodic = cfg.root_bc == APM_BC_PERIODIC;
@@ -611,12 +618,17 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
         D.g = L.d_grids;
         D.delta = L.hg[0].delta;
         D.inv_delta = 1.0 / D.delta;
+        D.cull_fp32 = (cfg.box * D.inv_delta) < 4194304.0 ? 1 : 0;
+        D.delta0 = cfg.box / N0;
+        D.inv_delta0 = 1.0 / D.delta0;
         {
             int ex = 0;
-            double fr = std::frexp(D.delta, &ex);
-            D.delta_pow2 = fr == 0.5 ? 1 : 0;
-            D.cull_fp32 = (cfg.box * D.inv_delta) < 4194304.0 ? 1 : 0;
+            D.delta0_pow2 = std::frexp(D.delta0, &ex) == 0.5 ? 1 : 0;
         }
+        D.frac_bits = kPosBits - L.level;
+        D.span = (long long)N0 << kPosBits;
+        D.box = cfg.box;
+        D.periodic = periodic ? 1 : 0;
         if (L.level > 0) {
             std::vector<std::pair<std::array<long long, 3>, std::array<long long, 3>>> dep, own;
             long long lo[3] = {1LL << 62, 1LL << 62, 1LL << 62}, hi[3] = {-(1LL << 62), -(1LL << 62), -(1LL << 62)};

@@ -109,9 +109,61 @@ struct LevelDev {
     TileMap map;
     double delta;
     double inv_delta;      // 1/delta
-    int delta_pow2;        // delta is a power of two: x/delta == x*inv_delta exactly
     int cull_fp32;         // level narrower than 2^22 cells: FP32 tile estimates are safe
+    double delta0;         // root cell: fixed-point positions count 2^-31 root cells
+    double inv_delta0;
+    int delta0_pow2;       // delta0 is a power of two: x/delta0 == x*inv_delta0 exactly
+    int frac_bits;         // 31 - level: fraction bits of a position on this level
+    long long span;        // N0 2^31: the box in fixed-point units
+    double box;
+    int periodic;
 };
+
+// Fixed-point TSC (shared by the deposit and the interpolation).  A drifted
+// coordinate x becomes X = rint(x/delta0 2^31) once; on a level with P fraction
+// bits the cell is X >> P and t = (X mod 2^P)/2^P; the weights of cells i-1, i,
+// i+1 are (1-t)^2/2, 3/4 - (t-1/2)^2, t^2/2 as exact integers on the scale 2^63.
+constexpr int kPosBits = 31;
+constexpr unsigned long long kOne63 = 1ULL << 63;
+
+// canonical: modulo the box on a periodic domain; on an isolated domain a
+// coordinate inside [0, box) that rounds onto the upper face stays in the last cell
+__device__ __forceinline__ long long fixed_position(double xd, const LevelDev& L) {
+    double u0 = L.delta0_pow2 ? __dmul_rn(xd, L.inv_delta0) : __ddiv_rn(xd, L.delta0);
+    // rint(u0 2^31) for |u0 2^31| < 2^51: adding 1.5 2^52 leaves the integer in the low bits
+    double v = __dadd_rn(__dmul_rn(u0, 2147483648.0), 6755399441055744.0);
+    long long X = __double_as_longlong(v) - 0x4338000000000000LL;
+    if (L.periodic) {
+        if (X < 0 || X >= L.span) {
+            X %= L.span;
+            if (X < 0) X += L.span;
+        }
+    } else if (X >= L.span && xd >= 0.0 && xd < L.box) {
+        X = L.span - 1;
+    }
+    return X;
+}
+
+__device__ __forceinline__ long long tsc_fixed(long long X, int P, unsigned long long w[3]) {
+    long long i = X >> P;
+    unsigned f = (unsigned)(X - (i << P));
+    unsigned S1 = (1u << P) - f;            // 2^P - f, at most 2^31
+    const int up = 62 - 2 * P;
+    w[2] = ((unsigned long long)f * f) << up;
+    w[0] = ((unsigned long long)S1 * S1) << up;
+    w[1] = kOne63 - w[0] - w[2];
+    return i;
+}
+
+// (a b + 2^62) >> 63 for a, b < 2^63: product of two weights on the scale 2^63,
+// rounded half up
+__device__ __forceinline__ unsigned long long wmul63(unsigned long long a, unsigned long long b) {
+    unsigned long long lo = a * b;
+    unsigned long long hi = __umul64hi(a, b);
+    unsigned long long lo2 = lo + (1ULL << 62);
+    hi += (lo2 < lo) ? 1ULL : 0ULL;
+    return (hi << 1) | (lo2 >> 63);
+}
 
 struct Particles {
     long long n;

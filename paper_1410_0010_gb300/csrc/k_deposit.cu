@@ -59,28 +59,6 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
     }
 }
 
-struct Tsc {
-    long long i[3];   // cell holding the particle, per axis
-    double w[3][3];   // weights of cells i-1, i, i+1
-};
-
-// u = x / delta; when delta is a power of two the product with 1/delta is the
-// same number (exact scaling) and avoids the FP64 division
-__device__ __forceinline__ double to_cells(double xd, const LevelDev& L) {
-    return L.delta_pow2 ? __dmul_rn(xd, L.inv_delta) : __ddiv_rn(xd, L.delta);
-}
-
-__device__ __forceinline__ void tsc_axis(double u, long long& i, double w[3]) {
-    double fi = floor(u);
-    double d = __dsub_rn(__dsub_rn(u, fi), 0.5);
-    double a = __dsub_rn(0.5, d);
-    double b = __dadd_rn(0.5, d);
-    w[0] = __dmul_rn(0.5, __dmul_rn(a, a));
-    w[1] = __dsub_rn(0.75, __dmul_rn(d, d));
-    w[2] = __dmul_rn(0.5, __dmul_rn(b, b));
-    i = (long long)fi;
-}
-
 // x' = x + v half_dt; on a periodic domain x' - box floor(x'/box), which is x'
 // itself (bit for bit) when x' is already inside [0, box)
 __device__ __forceinline__ double drift(double x, double v, double half_dt, double box,
@@ -89,12 +67,6 @@ __device__ __forceinline__ double drift(double x, double v, double half_dt, doub
     if (periodic && !(xd >= 0.0 && xd < box))
         xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
     return xd;
-}
-
-// rint(v) to the nearest integer, ties to even, for |v| < 2^51: adding 1.5 2^52
-// places the rounded integer in the low bits of the sum
-__device__ __forceinline__ long long rint_small(double v) {
-    return __double_as_longlong(__dadd_rn(v, 6755399441055744.0)) - 0x4338000000000000LL;
 }
 
 // adds the 27 charges q (z-major: q[c][b][a]) to one GMF box
@@ -156,11 +128,14 @@ __global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double
         }
         if (!m.occ[t[0] + (long long)m.nt[0] * (t[1] + (long long)m.nt[1] * t[2])]) return;
     }
+    // fixed-point position and weights (the same for every level)
     long long ic[3];
-    double w[3][3];
-    tsc_axis(to_cells(drift(x, vx, half_dt, box, periodic), L), ic[0], w[0]);
-    tsc_axis(to_cells(drift(y, vy, half_dt, box, periodic), L), ic[1], w[1]);
-    tsc_axis(to_cells(drift(z, vz, half_dt, box, periodic), L), ic[2], w[2]);
+    unsigned long long w[3][3];
+    const int PB = L.frac_bits;
+    const double xd[3] = {drift(x, vx, half_dt, box, periodic), drift(y, vy, half_dt, box, periodic),
+                          drift(z, vz, half_dt, box, periodic)};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ic[j] = tsc_fixed(fixed_position(xd[j], L), PB, w[j]);
 
     // candidate grids
     int e0 = 0, e1 = 1;
@@ -180,24 +155,22 @@ __global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double
         if (e0 == e1) return;
     }
 
-    const double scale = ldexp(1.0, F);
-    const double mass = P.m[p];
-    const double mq = __dmul_rn(mass, scale);
+    const double mq = __dmul_rn(P.m[p], ldexp(1.0, F));
     if (!(fabs(mq) < 4611686018427387904.0)) {   // 2^62
         atomicOr(status, kStOverflow);
         return;
     }
-    // q = rint((m w) 2^F) with w = (wx wy) wz.  Scaling by 2^F is exact, so
-    // (m w) 2^F == (m 2^F) w bit for bit (normal range), and wx wy is shared by
-    // the three z cells.
+    const long long M = __double2ll_rn(mq);
+    const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
+    // charges (|M| w + 2^62) >> 63 of the 26 outer cells, w = ((wx wy) wz) each
+    // product rounded half up; the centre takes M minus the others
     long long q[3][3][3];
     long long others = 0;
-    double wxy[3][3];
+    unsigned long long wxy[3][3];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) wxy[b][a] = __dmul_rn(w[0][a], w[1][b]);
-    const bool small = fabs(mq) < 2251799813685248.0;   // 2^51: charges fit rint_small
+        for (int a = 0; a < 3; ++a) wxy[b][a] = wmul63(w[0][a], w[1][b]);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -205,18 +178,18 @@ __global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 if (a == 1 && b == 1 && c == 1) continue;
-                double v = __dmul_rn(mq, __dmul_rn(wxy[b][a], w[2][c]));
-                q[c][b][a] = small ? rint_small(v) : __double2ll_rn(v);
+                long long v = (long long)wmul63(aM, wmul63(wxy[b][a], w[2][c]));
+                q[c][b][a] = M < 0 ? -v : v;
                 others += q[c][b][a];
             }
-    q[1][1][1] = (small ? rint_small(mq) : __double2ll_rn(mq)) - others;
+    q[1][1][1] = M - others;
 
     for (int e = e0; e < e1; ++e) {
         int gi = L.is_root ? 0 : L.map.dep_list[e];
         const GridDev& g = L.g[gi];
         if (g.mode == 1) {
             for (int j = 0; j < 3; ++j)
-                if (ic[j] < 0 || ic[j] >= g.G[j]) atomicOr(status, kStOutOfBox);
+                if (!(xd[j] >= 0.0 && xd[j] < box)) atomicOr(status, kStOutOfBox);
         }
         scatter(g, gmf[gi], ic, q);
     }

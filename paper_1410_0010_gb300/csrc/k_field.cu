@@ -117,10 +117,6 @@ __device__ __forceinline__ double drift(double x, double v, double half_dt, doub
     return xd;
 }
 
-__device__ __forceinline__ double to_cells(double xd, const LevelDev& L) {
-    return L.delta_pow2 ? __dmul_rn(xd, L.inv_delta) : __ddiv_rn(xd, L.delta);
-}
-
 // index of the grid of level L whose interior holds level cell ic, or -1
 __device__ int find_owner(const LevelDev& L, const long long ic[3]) {
     if (L.is_root) {
@@ -149,20 +145,18 @@ __device__ int find_owner(const LevelDev& L, const long long ic[3]) {
     return -1;
 }
 
-// TSC weights of one axis in T: FP64 for the FP64 path; for the FP32 path the
-// cell index and offset come from the exact FP64 position and the three
-// weights are evaluated in FP32.
-template <typename T>
-__device__ __forceinline__ void tsc_axis_t(double u, long long& i, T w[3]) {
-    double fi = floor(u);
-    i = (long long)fi;
-    T d = (T)(__dsub_rn(__dsub_rn(u, fi), 0.5));
-    T a = (T)0.5 - d, b = (T)0.5 + d;
-    w[0] = (T)0.5 * (a * a);
-    w[1] = (T)0.75 - d * d;
-    w[2] = (T)0.5 * (b * b);
+// weight W / 2^63 in T (FP64: exact conversion; FP32: from its top 24 bits)
+template <typename T> __device__ __forceinline__ T weight63(unsigned long long W);
+template <> __device__ __forceinline__ double weight63<double>(unsigned long long W) {
+    return __ull2double_rn(W) * 1.0842021724855044e-19;    // 2^-63
+}
+template <> __device__ __forceinline__ float weight63<float>(unsigned long long W) {
+    return __uint2float_rn((unsigned)(W >> 39)) * 5.9604644775390625e-08f;   // 2^-24
 }
 
+// TSC interpolation with the deposit's fixed-point weights: the 26 outer
+// weights are the rounded products ((wx wy) wz), the centre weight is one minus
+// their sum, exactly as the deposit distributes a particle's mass.
 template <typename T>
 __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_finer, Particles P,
                                                 double half_dt, double box, int periodic,
@@ -170,19 +164,38 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_
                                                 T* __restrict__ out) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P.n) return;
-    double xd[3] = {drift(P.x[p], P.vx[p], half_dt, box, periodic),
-                    drift(P.y[p], P.vy[p], half_dt, box, periodic),
-                    drift(P.z[p], P.vz[p], half_dt, box, periodic)};
+    long long X[3];
+    X[0] = fixed_position(drift(P.x[p], P.vx[p], half_dt, box, periodic), L);
+    X[1] = fixed_position(drift(P.y[p], P.vy[p], half_dt, box, periodic), L);
+    X[2] = fixed_position(drift(P.z[p], P.vz[p], half_dt, box, periodic), L);
     long long ic[3];
-    T w[3][3];
-    for (int j = 0; j < 3; ++j) tsc_axis_t<T>(to_cells(xd[j], L), ic[j], w[j]);
+    for (int j = 0; j < 3; ++j) ic[j] = X[j] >> L.frac_bits;
     int gi = find_owner(L, ic);
     if (gi < 0) return;
     if (has_finer) {
         long long fc[3];
-        for (int j = 0; j < 3; ++j) fc[j] = (long long)floor(to_cells(xd[j], F));
+        for (int j = 0; j < 3; ++j) fc[j] = X[j] >> F.frac_bits;
         if (find_owner(F, fc) >= 0) return;
     }
+    unsigned long long w[3][3];
+    for (int j = 0; j < 3; ++j) tsc_fixed(X[j], L.frac_bits, w[j]);
+    unsigned long long wq[3][3][3];
+    unsigned long long wsum = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a == 1 && b == 1 && c == 1) {
+                    wq[c][b][a] = 0;
+                    continue;
+                }
+                wq[c][b][a] = wmul63(wmul63(w[0][a], w[1][b]), w[2][c]);
+                wsum += wq[c][b][a];
+            }
+        }
+    wq[1][1][1] = kOne63 - wsum;
     const GridDev& g = L.g[gi];
     const T* __restrict__ A = reinterpret_cast<const T*>(acc_p[gi]);
     const int E0 = g.N[0] + 2, E1 = g.N[1] + 2;
@@ -199,12 +212,11 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_
         for (int b = 0; b < 3; ++b) {
             int y = lc[1] + b - 1;
             if (fold) y = y < 0 ? 0 : (y >= g.N[1] ? g.N[1] - 1 : y);
-            T wyz = w[1][b] * w[2][c];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 int x = lc[0] + a - 1;
                 if (fold) x = x < 0 ? 0 : (x >= g.N[0] ? g.N[0] - 1 : x);
-                T wt = w[0][a] * wyz;
+                const T wt = weight63<T>(wq[c][b][a]);
                 unsigned idx = (unsigned)(x + 1) + (unsigned)E0 * ((unsigned)(y + 1) + (unsigned)E1 * (unsigned)(z + 1));
                 a0 += wt * A[idx];
                 a1 += wt * A[ncell + idx];

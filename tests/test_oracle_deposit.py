@@ -19,15 +19,32 @@ def _tsc_shape(s):
 
 
 def test_tsc_weights_match_shape_function(oracle_mod):
+    """The fixed-point weights (reading R11) are the TSC shape function of the
+    particle-centre distance up to the position rounding (2^-32 cell, slopes <= 1)."""
     rng = np.random.default_rng(0)
     delta = 1.0 / 64
-    for x in rng.random(200):
+    tol = 2.0 ** -32 + 2.0 ** -52
+    for x in rng.random(400):
         i, w = oracle_mod.tsc_weights(x, delta)
-        assert i == math.floor(x / delta)
+        assert i in (math.floor(x / delta), math.floor(x / delta + 2.0 ** -32))
         for o in range(3):
             centre = (i + o - 1 + 0.5) * delta
-            assert abs(w[o] - _tsc_shape((x - centre) / delta)) < 4e-16
-        assert abs(w.sum() - 1.0) <= 2 * np.finfo(float).eps
+            assert abs(w[o] - _tsc_shape((x - centre) / delta)) < tol
+        assert abs(w.sum() - 1.0) <= 4 * 2.0 ** -53
+
+
+def test_tsc_weights_exact_at_dyadic_offsets(oracle_mod):
+    # offsets that are multiples of 2^-31 cell are represented exactly: the
+    # weights equal the shape function
+    delta = 1.0 / 32
+    for t in (0.0, 0.25, 0.5, 0.75, 0.125, 1.0 / 3.0):
+        x = (7 + t) * delta
+        i, w = oracle_mod.tsc_weights(x, delta)
+        tq = round(t * 2 ** 31) / 2 ** 31
+        exact = [0.5 * (1 - tq) ** 2, 0.75 - (tq - 0.5) ** 2, 0.5 * tq ** 2]
+        assert i == 7
+        for k in range(3):
+            assert abs(w[k] - exact[k]) <= 2.0 ** -53
 
 
 def test_cic_and_tsc_agree_at_cell_corner(oracle_mod):
@@ -105,8 +122,8 @@ def test_deposit_matches_brute_force_shape_function(oracle_mod):
     """Independent statement of the deposit: each of the 27 cells around each
     particle gets rint(m W(sx) W(sy) W(sz) 2^F) with the TSC shape function of the
     particle-centre distance; the centre cell takes the remainder; cells outside
-    the GMF box are dropped.  Weights may round differently, so allow 1 unit per
-    contribution; integer totals must agree exactly."""
+    the GMF box are dropped.  The charges agree to the fixed-point weight
+    resolution; integer totals must agree exactly."""
     cfg, grids = _child_setup(oracle_mod)
     plan = oracle_mod.plan_grid(cfg, grids, 1)
     rng = np.random.default_rng(4)
@@ -134,7 +151,10 @@ def test_deposit_matches_brute_force_shape_function(oracle_mod):
             if np.all(g >= 0) and np.all(g < np.array(plan.G)):
                 ref[g[2], g[1], g[0]] += v
                 kept += v
-    assert np.max(np.abs(gmf - ref)) <= 2 * n
+    # the shape function and the fixed-point weights (reading R11) differ by at
+    # most 2^-32 per axis (position rounding), so a charge by at most 3 2^-32 m 2^F
+    tol = sum(3 * 2.0 ** -32 * mp * 2.0 ** F for mp in m) + 2 * n
+    assert np.max(np.abs(gmf - ref)) <= tol
     fully_inside = all(np.all(np.floor(pos[:, p] / plan.delta) - 1 >= plan.lo) and
                        np.all(np.floor(pos[:, p] / plan.delta) + 1 < np.array(plan.lo) + plan.G)
                        for p in range(n))
