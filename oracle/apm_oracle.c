@@ -47,9 +47,10 @@
  *       is 2^63 minus theirs (deposit and interpolation weights sum to one
  *       exactly).
  *   Fixed point: cell masses are int64 with F fractional bits.  With
- *   M = rint(m 2^F), each of the 26 outer cells receives (|M| w + 2^62) >> 63
- *   (sign of M), the centre cell M minus the other 26, so integer mass is
- *   conserved exactly and the sum is independent of particle order.
+ *   M = rint(m 2^F), each of the 26 outer cells receives ((|M| wx) wy) wz,
+ *   every product (a b + 2^62) >> 63 (sign of M), the centre cell M minus the
+ *   other 26, so integer mass is conserved exactly and the sum is independent
+ *   of particle order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -441,7 +442,7 @@ int orc_deposit(int64_t n, const double* px, const double* py, const double* pz,
             for (int b = 0; b < 3; ++b)
                 for (int a = 0; a < 3; ++a) {
                     if (a == 1 && b == 1 && c == 1) continue;
-                    int64_t v = (int64_t)wmul(aM, wmul(wmul(w[0][a], w[1][b]), w[2][c]));
+                    int64_t v = (int64_t)wmul(wmul(wmul(aM, w[0][a]), w[1][b]), w[2][c]);
                     q[c][b][a] = M < 0 ? -v : v;
                     others += q[c][b][a];
                 }

@@ -512,6 +512,10 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             for (int j = 0; j < 3; ++j) {
                 if (g.M[j] > kMaxFft || g.M[j] < 2) return APM_E_UNSUPPORTED;
             }
+            // 32-bit cell indices inside the kernels
+            if ((long long)g.G[0] * g.G[1] * g.G[2] >= (1LL << 31) ||
+                (long long)(g.N[0] + 4) * (g.N[1] + 4) * (g.N[2] + 4) >= (1LL << 31))
+                return APM_E_UNSUPPORTED;
             FftPlan1D* pls[3] = {&g.fx, &g.fy, &g.fz};
             for (int j = 0; j < 3; ++j) {
                 if (!make_plan(g.M[j], pls[j])) return APM_E_UNSUPPORTED;
@@ -521,6 +525,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             g.Hy2 = g.M[1] / 2 + 1;
             g.Hz2 = g.M[2] / 2 + 1;
             g.cells_gmf = (long long)g.G[0] * g.G[1] * g.G[2];
+            g.inv2d = 0.5 / delta;
             g.rows_gas = std::max(1, kChunkCells / g.G[0]);
             g.rows_acc = std::max(1, kChunkCells / (g.N[0] + 2));
             g.np_x = fft_row_pairs(g.M[0], f64);

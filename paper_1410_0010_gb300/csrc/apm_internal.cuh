@@ -83,6 +83,32 @@ struct GridDev {
     int tx_y, tx_z;      // kx lines per CTA of the y / z passes
     int rows_gas;        // GMF rows per CTA of the baryon initialisation
     int rows_acc;        // output rows per CTA of the acceleration kernel
+    double inv2d;        // 1 / (2 delta)
+};
+
+// Threads of a CTA walking a batch of rows [r0, r1) of length n in row-major
+// order: thread t starts at element t and strides by the block size, the
+// (row, x) pair stepped incrementally (no division per element).
+struct RowWalk {
+    int r, x, dr, dx, n;
+    __device__ RowWalk(int r0, int n_) : n(n_) {
+        r = r0;
+        x = threadIdx.x;
+        while (x >= n) {
+            x -= n;
+            ++r;
+        }
+        dr = blockDim.x / n;
+        dx = blockDim.x - dr * n;
+    }
+    __device__ void next() {
+        x += dx;
+        r += dr;
+        if (x >= n) {
+            x -= n;
+            ++r;
+        }
+    }
 };
 
 // Tile lookup: level cell -> candidate grids (CSR per tile).

@@ -33,29 +33,33 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
     const int B = (G0 - g.N[0]) / 2;
     const int r0 = c.tile * g.rows_gas;
     const int r1 = min(nrows, r0 + g.rows_gas);
-    for (int r = r0; r < r1; ++r) {
+    const GridDev* p = par ? &pgrids[g.parent] : nullptr;
+    int last = -1, cy = 0, cz = 0;
+    bool yz_in = false;
+    for (RowWalk it(r0, G0); it.r < r1; it.next()) {
+        const int r = it.r, x = it.x;
         int64_t* row = out + (long long)r * G0;
         if (!own && !par) {
-            for (int x = threadIdx.x; x < G0; x += blockDim.x) row[x] = 0;
+            row[x] = 0;
             continue;
         }
-        const int y = r % G1, z = r / G1;
-        const int cy = y - B, cz = z - B;
-        const bool yz_in = cy >= 0 && cy < g.N[1] && cz >= 0 && cz < g.N[2];
-        for (int x = threadIdx.x; x < G0; x += blockDim.x) {
-            const int cx = x - B;
-            double rho = 0.0;
-            if (yz_in && cx >= 0 && cx < g.N[0]) {
-                if (own) rho = own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)];
-            } else if (par) {
-                const GridDev& p = pgrids[g.parent];
-                long long px = floor_div(g.start[0] + cx, refine) - p.start[0];
-                long long py = floor_div(g.start[1] + cy, refine) - p.start[1];
-                long long pz = floor_div(g.start[2] + cz, refine) - p.start[2];
-                rho = par[px + (long long)p.N[0] * (py + (long long)p.N[1] * pz)];
-            }
-            row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
+        if (r != last) {
+            last = r;
+            cy = r % G1 - B;
+            cz = r / G1 - B;
+            yz_in = cy >= 0 && cy < g.N[1] && cz >= 0 && cz < g.N[2];
         }
+        const int cx = x - B;
+        double rho = 0.0;
+        if (yz_in && cx >= 0 && cx < g.N[0]) {
+            if (own) rho = own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)];
+        } else if (par) {
+            long long px = floor_div(g.start[0] + cx, refine) - p->start[0];
+            long long py = floor_div(g.start[1] + cy, refine) - p->start[1];
+            long long pz = floor_div(g.start[2] + cz, refine) - p->start[2];
+            rho = par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
+        }
+        row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
     }
 }
 
@@ -69,38 +73,22 @@ __device__ __forceinline__ double drift(double x, double v, double half_dt, doub
     return xd;
 }
 
-// adds the 27 charges q (z-major: q[c][b][a]) to one GMF box
-__device__ __forceinline__ void scatter(const GridDev& g, int64_t* __restrict__ out,
-                                        const long long ic[3], const long long q[3][3][3]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        long long z = ic[2] + c - 1 - g.lo[2];
-        if (g.mode == 1) z = z < 0 ? 0 : (z >= g.G[2] ? g.G[2] - 1 : z);
-        else if (g.mode == 2) { z %= g.G[2]; if (z < 0) z += g.G[2]; }
-        else if (z < 0 || z >= g.G[2]) continue;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            long long y = ic[1] + b - 1 - g.lo[1];
-            if (g.mode == 1) y = y < 0 ? 0 : (y >= g.G[1] ? g.G[1] - 1 : y);
-            else if (g.mode == 2) { y %= g.G[1]; if (y < 0) y += g.G[1]; }
-            else if (y < 0 || y >= g.G[1]) continue;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                long long x = ic[0] + a - 1 - g.lo[0];
-                if (g.mode == 1) x = x < 0 ? 0 : (x >= g.G[0] ? g.G[0] - 1 : x);
-                else if (g.mode == 2) { x %= g.G[0]; if (x < 0) x += g.G[0]; }
-                else if (x < 0 || x >= g.G[0]) continue;
-                long long q0 = q[c][b][a];
-                if (q0 != 0)
-                    atomicAdd(reinterpret_cast<unsigned long long*>(
-                                  out + (x + (long long)g.G[0] * (y + (long long)g.G[1] * z))),
-                              (unsigned long long)q0);
-            }
-        }
+// GMF-local index of one cloud cell per axis under the grid's edge rule
+// (mode 0 drop: -1 when outside, 1 fold, 2 wrap)
+__device__ __forceinline__ int edge_rule(long long v, int G, int mode) {
+    if (mode == 1) return v < 0 ? 0 : (v >= G ? G - 1 : (int)v);
+    if (mode == 2) {
+        v %= G;
+        return (int)(v < 0 ? v + G : v);
     }
+    return (v < 0 || v >= G) ? -1 : (int)v;
 }
 
-__global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double half_dt,
+__device__ __forceinline__ void add_charge(int64_t* __restrict__ out, unsigned idx, long long q) {
+    if (q != 0) atomicAdd(reinterpret_cast<unsigned long long*>(out + idx), (unsigned long long)q);
+}
+
+__global__ void __launch_bounds__(256, 2) k_deposit(LevelDev L, Particles P, double half_dt,
                                                  double box, int periodic, int F,
                                                  int64_t* const* __restrict__ gmf,
                                                  unsigned* __restrict__ status) {
@@ -162,36 +150,50 @@ __global__ void __launch_bounds__(256) k_deposit(LevelDev L, Particles P, double
     }
     const long long M = __double2ll_rn(mq);
     const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
-    // charges (|M| w + 2^62) >> 63 of the 26 outer cells, w = ((wx wy) wz) each
-    // product rounded half up; the centre takes M minus the others
-    long long q[3][3][3];
-    long long others = 0;
-    unsigned long long wxy[3][3];
+    // charges ((|M| wx) wy) wz of the 26 outer cells, every product rounded half
+    // up on the scale 2^63; the centre takes M minus the others
+    unsigned long long mxy[3][3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+        const unsigned long long mx = wmul63(aM, w[0][a]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) wxy[b][a] = wmul63(w[0][a], w[1][b]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (a == 1 && b == 1 && c == 1) continue;
-                long long v = (long long)wmul63(aM, wmul63(wxy[b][a], w[2][c]));
-                q[c][b][a] = M < 0 ? -v : v;
-                others += q[c][b][a];
-            }
-    q[1][1][1] = M - others;
-
+        for (int b = 0; b < 3; ++b) mxy[b][a] = wmul63(mx, w[1][b]);
+    }
     for (int e = e0; e < e1; ++e) {
-        int gi = L.is_root ? 0 : L.map.dep_list[e];
+        const int gi = L.is_root ? 0 : L.map.dep_list[e];
         const GridDev& g = L.g[gi];
         if (g.mode == 1) {
             for (int j = 0; j < 3; ++j)
                 if (!(xd[j] >= 0.0 && xd[j] < box)) atomicOr(status, kStOutOfBox);
         }
-        scatter(g, gmf[gi], ic, q);
+        int64_t* __restrict__ out = gmf[gi];
+        // GMF boxes hold fewer than 2^31 cells (checked on the host)
+        int cx[3], cy[3], cz[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            cx[k] = edge_rule(ic[0] + k - 1 - g.lo[0], g.G[0], g.mode);
+            cy[k] = edge_rule(ic[1] + k - 1 - g.lo[1], g.G[1], g.mode);
+            cz[k] = edge_rule(ic[2] + k - 1 - g.lo[2], g.G[2], g.mode);
+        }
+        const unsigned G0 = g.G[0], G01 = (unsigned)g.G[0] * g.G[1];
+        long long others = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const bool ok = cy[b] >= 0 && cz[c] >= 0;
+                const unsigned row = G0 * (unsigned)cy[b] + G01 * (unsigned)cz[c];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (a == 1 && b == 1 && c == 1) continue;
+                    long long v = (long long)wmul63(mxy[b][a], w[2][c]);
+                    v = M < 0 ? -v : v;
+                    others += v;
+                    if (ok && cx[a] >= 0) add_charge(out, row + (unsigned)cx[a], v);
+                }
+            }
+        if (cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0)
+            add_charge(out, (unsigned)cx[1] + G0 * (unsigned)cy[1] + G01 * (unsigned)cz[1], M - others);
     }
 }
 

@@ -69,46 +69,51 @@ __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __rest
         pn = P01 * (p.N[2] + 2);
         ps0 = p.start[0]; ps1 = p.start[1]; ps2 = p.start[2];
     }
-    const T inv2d = (T)(0.5 / g.delta);
+    const T inv2d = (T)g.inv2d;
     const unsigned sy = W0, sz = (unsigned)W0 * W1;
     const int r0 = ch.tile * g.rows_acc;
     const int r1 = min(nrows, r0 + g.rows_acc);
-    for (int r = r0; r < r1; ++r) {
-        const int ey = r % E1, ez = r / E1;
-        int iy = 0, iz = 0;
-        float wyf = 0.f, wzf = 0.f;
-        if (carry) {
-            carry_axis(g.start[1] + (long long)ey - 1, ps1, iy, wyf);
-            carry_axis(g.start[2] + (long long)ez - 1, ps2, iz, wzf);
-        }
-        const unsigned prow = 1 + sy * (ey + 1) + sz * (ez + 1);   // phis index of x = -1
-        const unsigned orow = (unsigned)r * E0;
-        for (int ex = threadIdx.x; ex < E0; ex += blockDim.x) {
-            const unsigned ps = prow + ex;
-            T p0 = phis[ps];
-            T a0 = -(phis[ps + 1] - phis[ps - 1]) * inv2d;
-            T a1 = -(phis[ps + sy] - phis[ps - sy]) * inv2d;
-            T a2 = -(phis[ps + sz] - phis[ps - sz]) * inv2d;
+    int last = -1, iy = 0, iz = 0;
+    float wyf = 0.f, wzf = 0.f;
+    unsigned prow = 0, orow = 0;
+    for (RowWalk it(r0, E0); it.r < r1; it.next()) {
+        const int r = it.r, ex = it.x;
+        if (r != last) {
+            last = r;
+            const int ey = r % E1, ez = r / E1;
             if (carry) {
-                int ix;
-                float wxf;
-                carry_axis(g.start[0] + (long long)ex - 1, ps0, ix, wxf);
-                const unsigned base = ix + P0 * iy + P01 * iz;
-                const T wx = (T)wxf, wy = (T)wyf, wz = (T)wzf;
-                p0 += trilinear<T>(pphi, base, P0, P01, wx, wy, wz);
-                a0 += trilinear<T>(pacc, base, P0, P01, wx, wy, wz);
-                a1 += trilinear<T>(pacc + pn, base, P0, P01, wx, wy, wz);
-                a2 += trilinear<T>(pacc + 2 * pn, base, P0, P01, wx, wy, wz);
+                carry_axis(g.start[1] + (long long)ey - 1, ps1, iy, wyf);
+                carry_axis(g.start[2] + (long long)ez - 1, ps2, iz, wzf);
             }
-            const unsigned o = orow + ex;
-            phi[o] = p0;
-            acc[o] = a0;
-            acc[ncell + o] = a1;
-            acc[2 * ncell + o] = a2;
+            prow = 1 + sy * (ey + 1) + sz * (ez + 1);   // phis index of x = -1
+            orow = (unsigned)r * E0;
         }
+        const unsigned ps = prow + ex;
+        T p0 = phis[ps];
+        T a0 = -(phis[ps + 1] - phis[ps - 1]) * inv2d;
+        T a1 = -(phis[ps + sy] - phis[ps - sy]) * inv2d;
+        T a2 = -(phis[ps + sz] - phis[ps - sz]) * inv2d;
+        if (carry) {
+            int ix;
+            float wxf;
+            carry_axis(g.start[0] + (long long)ex - 1, ps0, ix, wxf);
+            const unsigned base = ix + P0 * iy + P01 * iz;
+            const T wx = (T)wxf, wy = (T)wyf, wz = (T)wzf;
+            p0 += trilinear<T>(pphi, base, P0, P01, wx, wy, wz);
+            a0 += trilinear<T>(pacc, base, P0, P01, wx, wy, wz);
+            a1 += trilinear<T>(pacc + pn, base, P0, P01, wx, wy, wz);
+            a2 += trilinear<T>(pacc + 2 * pn, base, P0, P01, wx, wy, wz);
+        }
+        const unsigned o = orow + ex;
+        phi[o] = p0;
+        acc[o] = a0;
+        acc[ncell + o] = a1;
+        acc[2 * ncell + o] = a2;
     }
 }
 
+// x' = x + v half_dt; on a periodic domain x' - box floor(x'/box), which is x'
+// itself when x' is already inside [0, box)
 __device__ __forceinline__ double drift(double x, double v, double half_dt, double box,
                                         int periodic) {
     double xd = __dadd_rn(x, __dmul_rn(v, half_dt));
@@ -145,7 +150,6 @@ __device__ int find_owner(const LevelDev& L, const long long ic[3]) {
     return -1;
 }
 
-// weight W / 2^63 in T (FP64: exact conversion; FP32: from its top 24 bits)
 template <typename T> __device__ __forceinline__ T weight63(unsigned long long W);
 template <> __device__ __forceinline__ double weight63<double>(unsigned long long W) {
     return __ull2double_rn(W) * 1.0842021724855044e-19;    // 2^-63
