@@ -36,7 +36,10 @@ def _stale(target, deps):
 
 
 def build(force=False, verbose=False, extra=()):
+    """Compile the stale translation units and link libapm.so.  Extra nvcc
+    flags come from `extra` and the APM_NVCC_FLAGS environment variable."""
     os.makedirs(OUT_DIR, exist_ok=True)
+    extra = list(extra) + os.environ.get("APM_NVCC_FLAGS", "").split()
     headers = [os.path.join(CSRC, "apm_internal.cuh"), os.path.join(INCLUDE, "apm.h")]
     objs, jobs = [], []
     for src in SOURCES:

@@ -134,28 +134,18 @@ int smooth7_at_least(int n) {
     }
 }
 
-bool make_plan(int L, FftPlan1D* pl) {
-    pl->L = L;
-    pl->nst = 0;
-    int n = L;
-    auto push = [&](int r) {
-        if (pl->nst >= kMaxStages) return false;
-        pl->radix[pl->nst++] = (unsigned char)r;
-        n /= r;
-        return true;
-    };
-    while (n % 8 == 0) if (!push(8)) return false;
-    while (n % 4 == 0) if (!push(4)) return false;
-    while (n % 2 == 0) if (!push(2)) return false;
-    for (int p : {3, 5, 7})
-        while (n % p == 0) if (!push(p)) return false;
-    return n == 1 && L >= 2;
-}
-
 long long floor_div(long long a, long long b) {
     long long q = a / b;
     if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
     return q;
+}
+
+// largest FFT stage radix of the FP32 path (16; APM_FFT_MAX_RADIX overrides it,
+// 8 restricts the plans to the simple radices)
+int fft_max_radix() {
+    const char* e = std::getenv("APM_FFT_MAX_RADIX");
+    int v = e ? std::atoi(e) : 16;
+    return v < 8 ? 8 : (v > 16 ? 16 : v);
 }
 
 int border_cells(const apm_config& c) {
@@ -518,7 +508,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
                 return APM_E_UNSUPPORTED;
             FftPlan1D* pls[3] = {&g.fx, &g.fy, &g.fz};
             for (int j = 0; j < 3; ++j) {
-                if (!make_plan(g.M[j], pls[j])) return APM_E_UNSUPPORTED;
+                if (!fft_plan(g.M[j], f64 ? 8 : fft_max_radix(), pls[j])) return APM_E_UNSUPPORTED;
                 pls[j]->tw_off = twiddle(g.M[j]);
             }
             g.Hx = g.M[0] / 2 + 1;

@@ -58,6 +58,32 @@ struct FftPlan1D {
     unsigned char radix[kMaxStages];
 };
 
+// Stage radices of a length-L transform: greedily the largest allowed radix
+// (at most max_radix) that divides what is left.  Radices above 8 are
+// composites of two of 2, 3, 4, 5, 7, 8 run in registers (FP32 path only).
+inline bool fft_plan(int L, int max_radix, FftPlan1D* pl) {
+    static const int kSimple[] = {8, 7, 5, 4, 3, 2};
+    static const int kWithComposite[] = {16, 15, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2};
+    pl->L = L;
+    pl->nst = 0;
+    if (L < 2) return false;
+    int n = L;
+    while (n > 1) {
+        int pick = 0;
+        if (max_radix <= 8) {
+            for (int r : kSimple)
+                if (n % r == 0) { pick = r; break; }
+        } else {
+            for (int r : kWithComposite)
+                if (r <= max_radix && n % r == 0) { pick = r; break; }
+        }
+        if (!pick || pl->nst >= kMaxStages) return false;
+        pl->radix[pl->nst++] = (unsigned char)pick;
+        n /= pick;
+    }
+    return true;
+}
+
 // Everything a kernel needs to know about one grid.
 struct GridDev {
     int kind;            // Green's table: 0 refined, 1 periodic root, 2 isolated root

@@ -44,19 +44,6 @@ __global__ void k_noalloc_setup(GridDev g, GridDev* dst, Chunk* chunks, int n, c
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-bool plan1d(int L, FftPlan1D* pl) {
-    pl->L = L;
-    pl->nst = 0;
-    int n = L;
-    for (int r : {8, 4, 2, 3, 5, 7})
-        while (n % r == 0) {
-            if (pl->nst >= kMaxStages) return false;
-            pl->radix[pl->nst++] = (unsigned char)r;
-            n /= r;
-        }
-    return n == 1 && L >= 2;
-}
-
 }  // namespace
 }  // namespace apm
 
@@ -70,7 +57,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
         return APM_E_INVALID;
     GridDev g;
     std::memset(&g, 0, sizeof(g));
-    if (!plan1d(n, &g.fx)) return APM_E_INVALID;   // n must be {2,3,5,7}-smooth
+    if (!fft_plan(n, 16, &g.fx)) return APM_E_INVALID;   // n must be {2,3,5,7}-smooth
     g.fy = g.fx;
     g.fz = g.fx;
     cudaStream_t s = (cudaStream_t)stream;

@@ -26,6 +26,13 @@ namespace {
 
 template <typename T> using C = typename Cplx<T>::type;
 
+// minimum resident CTAs per SM the pass kernels are compiled for
+#ifndef APM_FFT_MIN_CTAS
+#define APM_FFT_MIN_CTAS 4
+#endif
+template <typename T> struct MinCtas { static constexpr int value = APM_FFT_MIN_CTAS; };
+template <> struct MinCtas<double> { static constexpr int value = 1; };
+
 template <typename T> __device__ __forceinline__ C<T> mk(T a, T b) { C<T> r; r.x = a; r.y = b; return r; }
 template <typename T> __device__ __forceinline__ C<T> add(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ C<T> sub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
@@ -105,6 +112,52 @@ template <typename T, int DIR, int R> struct Dft {
     }
 };
 
+// Composite radix R = R1 R2 in registers (Cooley-Tukey inside the butterfly):
+// with n = R2 n1 + n2 and k = k1 + R1 k2,
+//   X[k1 + R1 k2] = sum_n2 w_R2^(n2 k2) w_R^(n2 k1) sum_n1 v[R2 n1 + n2] w_R1^(n1 k1),
+// w_m = exp(DIR 2 pi i / m); powers of w_R come from the length-L twiddles
+// (w_R^t = tw[t L/R]).
+template <typename T, int DIR, int R1, int R2>
+struct DftC {
+    __device__ static void run(C<T>* v, const C<T>* __restrict__ tw, int sR) {
+        constexpr int R = R1 * R2;
+        C<T> r1[R1], r2[R2];
+        if (R1 & 1) {
+#pragma unroll
+            for (int t = 0; t < R1; ++t) r1[t] = twid<T, DIR>(tw, ((t * R2) % R) * sR);
+        }
+        if (R2 & 1) {
+#pragma unroll
+            for (int t = 0; t < R2; ++t) r2[t] = twid<T, DIR>(tw, ((t * R1) % R) * sR);
+        }
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) {
+            C<T> t[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[R2 * n1 + n2];
+            Dft<T, DIR, R1>::run(t, r1);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                C<T> y = t[k1];
+                if (k1 > 0 && n2 > 0) y = mul<T>(y, twid<T, DIR>(tw, ((n2 * k1) % R) * sR));
+                v[R2 * k1 + n2] = y;
+            }
+        }
+        C<T> out[R];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            C<T> t[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) t[n2] = v[R2 * k1 + n2];
+            Dft<T, DIR, R2>::run(t, r2);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) out[k1 + R1 * k2] = t[k2];
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = out[q];
+    }
+};
+
 // One Stockham stage of radix R over nl = 2^lg lines of length L, element i of
 // line l at [i*es + l], from src to dst; Ns = product of the radices already
 // applied.  Butterfly j reads elements j + r L/R, twiddles them by
@@ -112,9 +165,10 @@ template <typename T, int DIR, int R> struct Dft {
 // (j / Ns) Ns R + (j mod Ns) + r Ns: natural order after the last stage.
 // Thread t owns line t mod nl and butterflies j = t / nl + m (threads / nl);
 // j / Ns and j mod Ns are stepped incrementally.
-template <typename T, int DIR, int R>
+template <typename T, int DIR, int R1, int R2>
 __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int L, int Ns, int lg,
                       int es, const C<T>* __restrict__ tw) {
+    constexpr int R = R1 * R2;
     const int nb = L / R;
     const int line = threadIdx.x & ((1 << lg) - 1);
     const int jstep = kFftThreads >> lg;
@@ -123,8 +177,8 @@ __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int 
         const int step = L / (Ns * R);
         int jm = j % Ns, k = j / Ns;
         const int djm = jstep % Ns, dk = jstep / Ns;
-        C<T> root[R];
-        if (R & 1) {
+        C<T> root[R2 == 1 ? R : 1];
+        if (R2 == 1 && (R & 1)) {
 #pragma unroll
             for (int t = 0; t < R; ++t) root[t] = twid<T, DIR>(tw, t * nb);
         }
@@ -136,7 +190,8 @@ __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int 
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[r] = mul<T>(v[r], twid<T, DIR>(tw, jm * r * step));
             }
-            Dft<T, DIR, R>::run(v, root);
+            if (R2 == 1) Dft<T, DIR, R1>::run(v, root);
+            else DftC<T, DIR, R1, R2>::run(v, tw, nb);
             const int idx = k * Ns * R + jm;
 #pragma unroll
             for (int r = 0; r < R; ++r) dst[(idx + r * Ns) * es + line] = v[r];
@@ -151,21 +206,41 @@ __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int 
     __syncthreads();
 }
 
+// composite stage radices (FP32 plans only)
+template <typename T, int DIR>
+__device__ __forceinline__ void stage_composite(int R, const C<T>* a, C<T>* b, int L, int Ns, int lg,
+                                                int es, const C<T>* tw) {
+    switch (R) {
+        case 6: stage<T, DIR, 3, 2>(a, b, L, Ns, lg, es, tw); break;
+        case 9: stage<T, DIR, 3, 3>(a, b, L, Ns, lg, es, tw); break;
+        case 10: stage<T, DIR, 5, 2>(a, b, L, Ns, lg, es, tw); break;
+        case 12: stage<T, DIR, 3, 4>(a, b, L, Ns, lg, es, tw); break;
+        case 14: stage<T, DIR, 7, 2>(a, b, L, Ns, lg, es, tw); break;
+        case 15: stage<T, DIR, 5, 3>(a, b, L, Ns, lg, es, tw); break;
+        default: stage<T, DIR, 4, 4>(a, b, L, Ns, lg, es, tw); break;   // 16
+    }
+}
+
 // Full transform of the lines in `a` (`b`: scratch of the same size, tw: the
 // length-L twiddles in shared memory); returns the buffer holding the result.
+// Stage radices 2..8 directly; on the FP32 path also the composites of
+// fft_plan (apm_internal.cuh), computed in registers as R1 x R2.
 template <typename T, int DIR>
 __device__ C<T>* fft_lines(C<T>* a, C<T>* b, const FftPlan1D& pl, int lg, int es, const C<T>* tw) {
     const int L = pl.L;
     int Ns = 1;
     for (int st = 0; st < pl.nst; ++st) {
-        int R = pl.radix[st];
+        const int R = pl.radix[st];
         switch (R) {
-            case 8: stage<T, DIR, 8>(a, b, L, Ns, lg, es, tw); break;
-            case 4: stage<T, DIR, 4>(a, b, L, Ns, lg, es, tw); break;
-            case 2: stage<T, DIR, 2>(a, b, L, Ns, lg, es, tw); break;
-            case 3: stage<T, DIR, 3>(a, b, L, Ns, lg, es, tw); break;
-            case 5: stage<T, DIR, 5>(a, b, L, Ns, lg, es, tw); break;
-            default: stage<T, DIR, 7>(a, b, L, Ns, lg, es, tw); break;
+            case 2: stage<T, DIR, 2, 1>(a, b, L, Ns, lg, es, tw); break;
+            case 3: stage<T, DIR, 3, 1>(a, b, L, Ns, lg, es, tw); break;
+            case 4: stage<T, DIR, 4, 1>(a, b, L, Ns, lg, es, tw); break;
+            case 5: stage<T, DIR, 5, 1>(a, b, L, Ns, lg, es, tw); break;
+            case 7: stage<T, DIR, 7, 1>(a, b, L, Ns, lg, es, tw); break;
+            case 8: stage<T, DIR, 8, 1>(a, b, L, Ns, lg, es, tw); break;
+            default:
+                if constexpr (sizeof(T) == 4) stage_composite<T, DIR>(R, a, b, L, Ns, lg, es, tw);
+                break;
         }
         C<T>* t = a;
         a = b;
@@ -226,7 +301,7 @@ template <> __device__ __forceinline__ float fixed_to_real<float>(long long q, i
 // ---- xf: GMF rows -> half spectra along x ----------------------------------
 // smem: A, B (M0 x (np+1) each, element-major, padded), twiddles (M0)
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_xf(const GridDev* __restrict__ grids,
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xf(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
                                                     const int64_t* const* __restrict__ gmf,
                                                     const C<T>* __restrict__ tw_arena,
@@ -289,7 +364,7 @@ __global__ void __launch_bounds__(kFftThreads) k_xf(const GridDev* __restrict__ 
 //   yi (AX 1, MODE 2): in A[zw][ky][kx],         out B[zw][yw][kx]
 // smem: A, B (L x tx each, element-major), twiddles (L)
 template <typename T, int AX, int MODE>
-__global__ void __launch_bounds__(kFftThreads) k_col(const GridDev* __restrict__ grids,
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const GridDev* __restrict__ grids,
                                                      const Chunk* __restrict__ chunks,
                                                      const C<T>* __restrict__ tw_arena,
                                                      const T* __restrict__ tab,
@@ -385,7 +460,7 @@ __global__ void __launch_bounds__(kFftThreads) k_col(const GridDev* __restrict__
 // ---- xi: half spectra -> real rows of the window -------------------------------
 // smem: A, B (M0 x (np+1) each), twiddles (M0)
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_xi(const GridDev* __restrict__ grids,
+__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xi(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
                                                     const C<T>* __restrict__ tw_arena,
                                                     const C<T>* __restrict__ wsB,
