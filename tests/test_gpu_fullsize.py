@@ -1,0 +1,156 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times
+(every grid of a level batched in one launch sequence, FP32 path).
+
+* periodic 128^3 root + three 64^3 levels, 2^20 Plummer particles: the whole
+  solve against the oracle, element by element;
+* 512 batched subgrids of one level with gas: every grid on the GPU, a sample
+  of grids (GMF bit-exact, potential, accelerations) against the oracle;
+* periodic 512^3 root + 2 x 64 subgrids of 128^3, 16.8M particles: root GMF
+  bit-exact against the oracle's full deposit; the root potential mode by mode
+  (DFT of the GPU output at sampled modes against T(kappa) DFT(mass)(kappa) with
+  the oracle's Green's function); two 128^3 subgrids solved fully by the oracle;
+  FD, parent carry and particle interpolation on samples.
+"""
+import numpy as np
+import pytest
+
+import apm_inputs as W
+from gpu_helpers import TOL, compare, rel_l2, run_gpu, run_oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def test_plummer_periodic_three_levels_full():
+    w = W.config_plummer()
+    ref = run_oracle(w.grids, w.particles, w.half_dt, periodic=True)
+    gpu = run_gpu(w.grids, w.particles, w.half_dt, periodic=True, precision="fp32")
+    compare(gpu, ref, "fp32")
+
+
+def test_batched_level_sampled_grids():
+    import oracle
+    w = W.config_batched_level()
+    gpu = run_gpu(w.grids, w.particles, w.half_dt, gas=w.gas, precision="fp32",
+                  mass_frac_bits=w.mass_frac_bits, levels=w.solve_levels)
+    cfg = oracle.Config(periodic=False, mass_frac_bits=w.mass_frac_bits)
+    grids = [oracle.Grid(*g) for g in w.grids]
+    rng = np.random.default_rng(40)
+    sample = sorted(rng.choice(np.arange(1, len(grids)), size=6, replace=False).tolist())
+    for gi in sample:
+        gmf, st = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt, gas=w.gas[gi])
+        assert np.array_equal(gpu["gmf"][gi], gmf), gi
+        phis = oracle.solve(cfg, grids, gi, gmf)
+        assert rel_l2(gpu["phis"][gi], phis) <= TOL["fp32"]["phis"], gi
+        phi, acc = oracle.accel(cfg, grids, gi, phis)
+        assert rel_l2(gpu["phi"][gi], phi) <= TOL["fp32"]["phi"], gi
+        assert rel_l2(gpu["acc"][gi], acc) <= TOL["fp32"]["acc"], gi
+
+
+@pytest.fixture(scope="module")
+def cosmo():
+    """The 512^3 workload solved once on the GPU (FP32), with the arrays the
+    checks below read."""
+    import torch
+
+    from paper_1410_0010_gb300.solver import Particles, Solver
+    w = W.config_cosmo512()
+    dev = torch.device("cuda", 0)
+    s = Solver(w.grids, periodic=True, precision="fp32", mass_frac_bits=w.mass_frac_bits, device=0)
+    P = Particles({k: torch.as_tensor(v, device=dev) for k, v in w.particles.items()})
+    bufs = s.alloc_all()
+    pacc = torch.zeros((3, w.n_particles), dtype=torch.float32, device=dev)
+    s.step(P, w.half_dt, bufs, pacc)
+    s.sync_status()
+    l1 = s.level_grids[1][:2]
+    out = dict(w=w, solver=s, root_gmf=bufs[0]["gmf"][0].cpu().numpy(),
+               root_phis=bufs[0]["phis"][0].cpu().numpy(),
+               root_phi=bufs[0]["phi"][0].cpu().numpy(), root_acc=bufs[0]["acc"][0].cpu().numpy(),
+               l1_ids=l1, l1={k: {key: bufs[1][key][s.info[gi]["level_index"]].cpu().numpy()
+                                  for key in ("gmf", "phis", "phi", "acc")} for k, gi in enumerate(l1)},
+               pacc=pacc.cpu().numpy())
+    del bufs, P
+    torch.cuda.empty_cache()
+    return out
+
+
+def test_cosmo_root_mass_field_bit_exact(cosmo):
+    import oracle
+    w = cosmo["w"]
+    cfg = oracle.Config(periodic=True, mass_frac_bits=w.mass_frac_bits)
+    gmf, st = oracle.deposit(cfg, [oracle.Grid(*g) for g in w.grids], 0, w.particles, w.half_dt)
+    assert st == 0
+    assert np.array_equal(cosmo["root_gmf"], gmf)
+
+
+def test_cosmo_root_potential_mode_by_mode(cosmo):
+    """Phi = IDFT(T DFT(m)) on the periodic 512^3 root: at sampled modes the DFT of
+    the GPU potential equals T(kappa) times the DFT of the cell masses."""
+    import oracle
+    w = cosmo["w"]
+    n = w.grids[0].dims[0]
+    d = 1.0 / n
+    m = np.ldexp(cosmo["root_gmf"].astype(np.float64), -w.mass_frac_bits)
+    phi = cosmo["root_phis"][2:-2, 2:-2, 2:-2].astype(np.float64)   # cells [0, n)
+    ar = np.arange(n)
+    rng = np.random.default_rng(41)
+    modes = [(1, 0, 0), (0, 3, 1), (5, 7, 2), (40, 11, 90), (n // 2 - 1, 3, 200)] + \
+        [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(4)]
+    # FP32 round-off of the output field, seen in one Fourier mode
+    floor = 2e-6 * float(np.sqrt(np.mean(phi * phi))) * n ** 1.5
+
+    def dft(f, kap):
+        ex, ey, ez = [np.exp(-2j * np.pi * kap[j] * ar / n) for j in range(3)]
+        zy = f @ ex.real + 1j * (f @ ex.imag)            # sum over x -> [z, y]
+        z = zy @ ey                                      # sum over y -> [z]
+        return z @ ez
+
+    for kap in modes:
+        dm = dft(m, kap)
+        dp = dft(phi, kap)
+        fk = [min(k, n - k) for k in kap]
+        T = oracle.green_opt(fk, (n, n, n), d, 3.4 * d, 0.0, 0) / d ** 3
+        expect = T * dm
+        assert abs(dp - expect) <= 2e-5 * abs(expect) + floor, kap
+
+
+def test_cosmo_subgrids_full_oracle_solve(cosmo):
+    import oracle
+    w = cosmo["w"]
+    cfg = oracle.Config(periodic=True, mass_frac_bits=w.mass_frac_bits)
+    grids = [oracle.Grid(*g) for g in w.grids]
+    for k, gi in enumerate(cosmo["l1_ids"]):
+        gmf, st = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt)
+        assert np.array_equal(cosmo["l1"][k]["gmf"], gmf)
+        phis = oracle.solve(cfg, grids, gi, gmf)
+        assert rel_l2(cosmo["l1"][k]["phis"], phis) <= TOL["fp32"]["phis"]
+
+
+def test_cosmo_fd_carry_and_interpolation(cosmo):
+    """The root accelerations are the FD of its potential; a level-1 grid's fields
+    are its FD plus the trilinear carry of the root fields; particle accelerations
+    are the TSC interpolation of the owning grid's field (oracle routines applied
+    to the GPU's own inputs)."""
+    import oracle
+    w = cosmo["w"]
+    cfg = oracle.Config(periodic=True, mass_frac_bits=w.mass_frac_bits)
+    grids = [oracle.Grid(*g) for g in w.grids]
+    phi0, acc0 = oracle.accel(cfg, grids, 0, cosmo["root_phis"])
+    assert rel_l2(cosmo["root_phi"], phi0) <= TOL["fp32"]["phi"]
+    assert rel_l2(cosmo["root_acc"], acc0) <= TOL["fp32"]["acc"]
+    gi = cosmo["l1_ids"][0]
+    phi1, acc1 = oracle.accel(cfg, grids, gi, cosmo["l1"][0]["phis"], cosmo["root_phi"],
+                              cosmo["root_acc"])
+    assert rel_l2(cosmo["l1"][0]["phi"], phi1) <= TOL["fp32"]["phi"]
+    assert rel_l2(cosmo["l1"][0]["acc"], acc1) <= TOL["fp32"]["acc"]
+    # particles: a sample owned by the root and by the first level-1 grid
+    rng = np.random.default_rng(42)
+    sub = np.sort(rng.choice(w.n_particles, size=200000, replace=False))
+    parts = {k: v[sub] for k, v in w.particles.items()}
+    own = oracle.owners(cfg, grids, parts, w.half_dt)
+    out = np.zeros((3, len(sub)))
+    oracle.interp(cfg, grids, 0, cosmo["root_acc"].astype(np.float64), parts, w.half_dt, own, out)
+    oracle.interp(cfg, grids, gi, cosmo["l1"][0]["acc"].astype(np.float64), parts, w.half_dt, own, out)
+    sel = (own == 0) | (own == gi)
+    assert sel.sum() > 1000
+    got = cosmo["pacc"][:, sub][:, sel]
+    assert rel_l2(got, out[:, sel]) <= TOL["fp32"]["pacc"]
