@@ -35,8 +35,10 @@
  *   R10 Parent carry: potential and acceleration, trilinear interpolation from
  *       parent cell centres in FP64 (Sec. 2.2, last paragraph).
  *   R11 TSC weights in fixed point (the paper fixes the TSC assignment of
- *       Sec. 2, not its arithmetic): the drifted coordinate in root cells is
- *       rounded once to X = rint(x/delta0 2^31), the same for every level; on
+ *       Sec. 2, not its arithmetic): the drifted coordinate x + v dt/2 (FP64,
+ *       two rounded operations) in root cells is rounded once to
+ *       X = rint(x/delta0 2^31), the same for every level, and on a periodic
+ *       domain taken modulo the box (N0 2^31); on
  *       level l (2^l cells per root cell) the cell is i = floor(X / 2^(31-l))
  *       and t = (X mod 2^(31-l)) / 2^(31-l) the offset from its lower face;
  *       the three weights of the cells i-1, i, i+1 are (1-t)^2/2,
@@ -340,13 +342,20 @@ double orc_drift(double x, double v, double half_dt, double box, int periodic) {
  * high and low bits of X with 31 - l fraction bits. */
 #define ORC_POS_BITS 31
 int64_t orc_position_fixed(double x, double delta0) {
-    return (int64_t)rint(ldexp(x / delta0, ORC_POS_BITS));
+    /* a coordinate 2^31 root cells or more from the origin (or NaN) saturates
+     * at -+2^62: far outside every box */
+    double t = ldexp(x / delta0, ORC_POS_BITS);
+    double lim = ldexp(1.0, 62);
+    if (t >= lim) return (int64_t)1 << 62;
+    if (!(t > -lim)) return -((int64_t)1 << 62);
+    return (int64_t)rint(t);
 }
 
-/* The fixed-point position of a drifted coordinate xd, made canonical: on a
- * periodic domain X is taken modulo the box (N0 2^31); on an isolated domain a
- * coordinate inside [0, box) that rounds onto the upper face stays in the last
- * root cell. */
+/* The fixed-point position of a drifted coordinate xd = x + v half_dt, made
+ * canonical: on a periodic domain X is taken modulo the box (N0 2^31), i.e. the
+ * periodic wrap of Sec. 3.4 is applied to the fixed-point position; on an
+ * isolated domain a coordinate inside [0, box) that rounds onto the upper face
+ * stays in the last root cell. */
 static int64_t pos_fixed(double xd, double delta0, double box, int periodic) {
     int64_t X = orc_position_fixed(xd, delta0);
     int64_t span = (int64_t)llround(box / delta0) << ORC_POS_BITS;
@@ -423,7 +432,7 @@ int orc_deposit(int64_t n, const double* px, const double* py, const double* pz,
         int64_t ic[3];
         int outside = 0;
         for (int j = 0; j < 3; ++j) {
-            double xd = orc_drift(pos[j], vel[j], half_dt, box, periodic);
+            double xd = orc_drift(pos[j], vel[j], half_dt, box, 0);
             if (!(xd >= 0.0 && xd < box)) outside = 1;
             ic[j] = orc_tsc_fixed(pos_fixed(xd, delta0, box, periodic), level, w[j]);
         }
@@ -630,7 +639,7 @@ void orc_interp(int64_t n, const double* px, const double* py, const double* pz,
         uint64_t w[3][3];
         int64_t ic[3];
         for (int j = 0; j < 3; ++j) {
-            double xd = orc_drift(pos[j], vel[j], half_dt, box, periodic);
+            double xd = orc_drift(pos[j], vel[j], half_dt, box, 0);
             ic[j] = orc_tsc_fixed(pos_fixed(xd, delta0, box, periodic), level, w[j]) - start[j];
         }
         /* the 27 weights of the deposit: the centre takes 2^63 minus the other 26,
@@ -674,7 +683,7 @@ void orc_cells(int64_t n, const double* px, const double* py, const double* pz,
         double pos[3] = {px[p], py[p], pz[p]};
         double vel[3] = {pvx[p], pvy[p], pvz[p]};
         for (int j = 0; j < 3; ++j) {
-            double xd = orc_drift(pos[j], vel[j], half_dt, box, periodic);
+            double xd = orc_drift(pos[j], vel[j], half_dt, box, 0);
             uint64_t w[3];
             cells[j * n + p] = orc_tsc_fixed(pos_fixed(xd, delta0, box, periodic), level, w);
         }

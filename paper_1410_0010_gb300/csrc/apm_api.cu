@@ -613,12 +613,15 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
         D.g = L.d_grids;
         D.delta = L.hg[0].delta;
         D.inv_delta = 1.0 / D.delta;
-        D.cull_fp32 = (cfg.box * D.inv_delta) < 4194304.0 ? 1 : 0;
         D.delta0 = cfg.box / N0;
         D.inv_delta0 = 1.0 / D.delta0;
         {
             int ex = 0;
-            D.delta0_pow2 = std::frexp(D.delta0, &ex) == 0.5 ? 1 : 0;
+            // delta0 = 2^(ex-1): X = rint(x 2^pos_exp) from the bits of x (the
+            // exponent bound keeps subnormal coordinates below half a unit)
+            const bool pow2 = std::frexp(D.delta0, &ex) == 0.5;
+            D.pos_exp = kPosBits - (ex - 1);
+            D.delta0_pow2 = (pow2 && D.pos_exp < 1000) ? 1 : 0;
         }
         D.frac_bits = kPosBits - L.level;
         D.span = (long long)N0 << kPosBits;
@@ -642,7 +645,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             }
             long long ext = 0;
             for (int j = 0; j < 3; ++j) ext = std::max(ext, hi[j] - lo[j]);
-            int shift = 2;   // tiles of at least 4 cells (the FP32 culling below relies on it)
+            int shift = 2;   // tiles of at least 4 cells
             while ((ext >> shift) > 64) ++shift;
             int nt[3];
             for (int j = 0; j < 3; ++j) nt[j] = (int)(((hi[j] - lo[j]) + (1LL << shift) - 1) >> shift);

@@ -161,7 +161,6 @@ struct LevelDev {
     TileMap map;
     double delta;
     double inv_delta;      // 1/delta
-    int cull_fp32;         // level narrower than 2^22 cells: FP32 tile estimates are safe
     double delta0;         // root cell: fixed-point positions count 2^-31 root cells
     double inv_delta0;
     int delta0_pow2;       // delta0 is a power of two: x/delta0 == x*inv_delta0 exactly
@@ -169,6 +168,7 @@ struct LevelDev {
     long long span;        // N0 2^31: the box in fixed-point units
     double box;
     int periodic;
+    int pos_exp;           // delta0 = 2^(31 - pos_exp) when delta0_pow2: X = rint(x 2^pos_exp)
 };
 
 // Fixed-point TSC (shared by the deposit and the interpolation).  A drifted
@@ -178,13 +178,60 @@ struct LevelDev {
 constexpr int kPosBits = 31;
 constexpr unsigned long long kOne63 = 1ULL << 63;
 
-// canonical: modulo the box on a periodic domain; on an isolated domain a
-// coordinate inside [0, box) that rounds onto the upper face stays in the last cell
+// rint(x 2^K), ties to even, of a finite double with |x 2^K| < 2^62, from its
+// exponent and significand with integer operations (no FP64 pipe); ok is
+// cleared for larger or non-finite values.
+__device__ __forceinline__ long long scaled_rint(double x, int K, bool& ok) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    ok = true;
+    if (e == 0x7FF) {
+        ok = false;
+        return 0;
+    }
+    if (e == 0) return 0;   // zero or subnormal: far below one unit here
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL;
+    const int sh = e - 1075 + K;   // |x 2^K| = m 2^sh
+    unsigned long long r;
+    if (sh >= 0) {
+        if (sh >= 10) {            // m 2^sh >= 2^62
+            ok = false;
+            return 0;
+        }
+        r = m << sh;
+    } else if (sh < -54) {
+        r = 0;
+    } else {
+        const int t = -sh;
+        r = m >> t;
+        const unsigned long long rem = m & ((1ULL << t) - 1);
+        const unsigned long long half = 1ULL << (t - 1);
+        if (rem > half || (rem == half && (r & 1))) ++r;
+    }
+    return (b >> 63) ? -(long long)r : (long long)r;
+}
+
+// x' = x + v half_dt in FP64 (two rounded operations; x itself when half_dt = 0)
+__device__ __forceinline__ double drift_raw(double x, double v, double half_dt) {
+    return half_dt == 0.0 ? x : __dadd_rn(x, __dmul_rn(v, half_dt));
+}
+
+// X = rint(x'/delta0 2^31), canonical: modulo the box on a periodic domain; on
+// an isolated domain a coordinate inside [0, box) that rounds onto the upper
+// face stays in the last cell
 __device__ __forceinline__ long long fixed_position(double xd, const LevelDev& L) {
-    double u0 = L.delta0_pow2 ? __dmul_rn(xd, L.inv_delta0) : __ddiv_rn(xd, L.delta0);
-    // rint(u0 2^31) for |u0 2^31| < 2^51: adding 1.5 2^52 leaves the integer in the low bits
-    double v = __dadd_rn(__dmul_rn(u0, 2147483648.0), 6755399441055744.0);
-    long long X = __double_as_longlong(v) - 0x4338000000000000LL;
+    // a coordinate 2^31 root cells or more from the origin (or NaN) saturates at
+    // -+2^62: far outside every box
+    long long X;
+    bool ok;
+    if (L.delta0_pow2) {
+        X = scaled_rint(xd, L.pos_exp, ok);
+    } else {
+        const double t = __dmul_rn(__ddiv_rn(xd, L.delta0), 2147483648.0);
+        ok = fabs(t) < 4611686018427387904.0;   // 2^62
+        X = ok ? __double2ll_rn(t) : 0;
+    }
+    if (!ok) X = xd > 0.0 ? (1LL << 62) : -(1LL << 62);
     if (L.periodic) {
         if (X < 0 || X >= L.span) {
             X %= L.span;

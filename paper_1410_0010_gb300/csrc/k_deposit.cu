@@ -63,15 +63,6 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
     }
 }
 
-// x' = x + v half_dt; on a periodic domain x' - box floor(x'/box), which is x'
-// itself (bit for bit) when x' is already inside [0, box)
-__device__ __forceinline__ double drift(double x, double v, double half_dt, double box,
-                                        int periodic) {
-    double xd = __dadd_rn(x, __dmul_rn(v, half_dt));
-    if (periodic && !(xd >= 0.0 && xd < box))
-        xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
-    return xd;
-}
 
 // GMF-local index of one cloud cell per axis under the grid's edge rule
 // (mode 0 drop: -1 when outside, 1 fold, 2 wrap)
@@ -94,36 +85,17 @@ __global__ void __launch_bounds__(256, 2) k_deposit(LevelDev L, Particles P, dou
                                                  unsigned* __restrict__ status) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P.n) return;
-    const double x = P.x[p], y = P.y[p], z = P.z[p];
-    const double vx = P.vx[p], vy = P.vy[p], vz = P.vz[p];
-    if (!L.is_root && L.cull_fp32) {
-        // FP32 estimate of the particle's tile (error far below the 4-cell tile):
-        // particles with no occupied tile nearby touch no GMF box of this level
-        const TileMap& m = L.map;
-        const float hf = (float)half_dt, inv = (float)L.inv_delta;
-        const float px[3] = {((float)x + (float)vx * hf) * inv, ((float)y + (float)vy * hf) * inv,
-                             ((float)z + (float)vz * hf) * inv};
-        long long t[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float rel = floorf(px[j]) - (float)m.lo[j];
-            if (!(rel > -4.0f)) return;
-            t[j] = rel < 0.0f ? 0 : ((long long)rel >> m.shift);
-            if (t[j] >= m.nt[j]) {
-                if (t[j] > m.nt[j]) return;
-                t[j] = m.nt[j] - 1;
-            }
-        }
-        if (!m.occ[t[0] + (long long)m.nt[0] * (t[1] + (long long)m.nt[1] * t[2])]) return;
-    }
     // fixed-point position and weights (the same for every level)
+    const double xd[3] = {drift_raw(P.x[p], P.vx[p], half_dt), drift_raw(P.y[p], P.vy[p], half_dt),
+                          drift_raw(P.z[p], P.vz[p], half_dt)};
     long long ic[3];
-    unsigned long long w[3][3];
     const int PB = L.frac_bits;
-    const double xd[3] = {drift(x, vx, half_dt, box, periodic), drift(y, vy, half_dt, box, periodic),
-                          drift(z, vz, half_dt, box, periodic)};
+    long long X[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) ic[j] = tsc_fixed(fixed_position(xd[j], L), PB, w[j]);
+    for (int j = 0; j < 3; ++j) {
+        X[j] = fixed_position(xd[j], L);
+        ic[j] = X[j] >> PB;
+    }
 
     // candidate grids
     int e0 = 0, e1 = 1;
@@ -142,13 +114,16 @@ __global__ void __launch_bounds__(256, 2) k_deposit(LevelDev L, Particles P, dou
         e1 = m.dep_off[tile + 1];
         if (e0 == e1) return;
     }
+    unsigned long long w[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) tsc_fixed(X[j], PB, w[j]);
 
-    const double mq = __dmul_rn(P.m[p], ldexp(1.0, F));
-    if (!(fabs(mq) < 4611686018427387904.0)) {   // 2^62
+    bool ok;
+    const long long M = scaled_rint(P.m[p], F, ok);   // rint(m 2^F)
+    if (!ok) {                                         // |m 2^F| >= 2^62
         atomicOr(status, kStOverflow);
         return;
     }
-    const long long M = __double2ll_rn(mq);
     const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
     // charges ((|M| wx) wy) wz of the 26 outer cells, every product rounded half
     // up on the scale 2^63; the centre takes M minus the others

@@ -112,15 +112,6 @@ __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __rest
     }
 }
 
-// x' = x + v half_dt; on a periodic domain x' - box floor(x'/box), which is x'
-// itself when x' is already inside [0, box)
-__device__ __forceinline__ double drift(double x, double v, double half_dt, double box,
-                                        int periodic) {
-    double xd = __dadd_rn(x, __dmul_rn(v, half_dt));
-    if (periodic && !(xd >= 0.0 && xd < box))
-        xd = __dsub_rn(xd, __dmul_rn(box, floor(__ddiv_rn(xd, box))));
-    return xd;
-}
 
 // index of the grid of level L whose interior holds level cell ic, or -1
 __device__ int find_owner(const LevelDev& L, const long long ic[3]) {
@@ -169,9 +160,9 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P.n) return;
     long long X[3];
-    X[0] = fixed_position(drift(P.x[p], P.vx[p], half_dt, box, periodic), L);
-    X[1] = fixed_position(drift(P.y[p], P.vy[p], half_dt, box, periodic), L);
-    X[2] = fixed_position(drift(P.z[p], P.vz[p], half_dt, box, periodic), L);
+    X[0] = fixed_position(drift_raw(P.x[p], P.vx[p], half_dt), L);
+    X[1] = fixed_position(drift_raw(P.y[p], P.vy[p], half_dt), L);
+    X[2] = fixed_position(drift_raw(P.z[p], P.vz[p], half_dt), L);
     long long ic[3];
     for (int j = 0; j < 3; ++j) ic[j] = X[j] >> L.frac_bits;
     int gi = find_owner(L, ic);
