@@ -170,6 +170,44 @@ def dist_env():
     return world, rank, local
 
 
+class Ranks:
+    """The process group around the timed region: a barrier, and the maximum or
+    sum of a number over ranks (NCCL for GPU ranks; any backend whose tensors
+    live on `device`).  With one rank every call is the identity."""
+
+    def __init__(self, world, device):
+        self.world = world
+        self.device = device
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.SUM)
+
+
+def job_rate(ranks, units, ms):
+    """Whole-job throughput in millions of units per second: the units all ranks
+    processed over the slowest rank's time (ms, the max over ranks)."""
+    return ranks.sum(units) / (ms / 1e3) / 1e6
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -225,19 +263,10 @@ def run_apm(args):
     n = w.n_particles
     cells = w.interior_cells(levels)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world > 1:
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+    ranks = Ranks(world, dev)
 
     def timed(fn, steps):
-        barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -246,8 +275,8 @@ def run_apm(args):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / steps)
+        ranks.barrier()
+        return ranks.max(e0.elapsed_time(e1) / steps)
 
     # ---------------- FP32 (the product configuration)
     s32, b32 = make("fp32")
@@ -322,7 +351,7 @@ def run_apm(args):
                        torch.linalg.vector_norm(pacc64[:, own]))
         e_phi = float(max(torch.linalg.vector_norm(a.double() - b) / torch.linalg.vector_norm(b)
                           for a, b in zip(phi32, b64[-1]["phi"])))
-        fp64 = {"value": cells / (ms64 / 1e3) / 1e6 * world, "ms_per_step": ms64,
+        fp64 = {"value": job_rate(ranks, cells, ms64), "ms_per_step": ms64,
                 "fp32_speedup": ms64 / ms, "fp32_rel_l2_vs_fp64": {"phi_finest": e_phi, "pacc": e_pacc}}
         s64.close()
 
@@ -355,7 +384,7 @@ def run_apm(args):
         cpu = {"value": c / dt / 1e6, "unit": "Mcells/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": desc, "seconds": dt}
 
-    value = cells / (ms / 1e3) / 1e6 * world
+    value = job_rate(ranks, cells, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -364,11 +393,11 @@ def run_apm(args):
                    "interior_cells": cells, "particles": n, "periodic": w.periodic,
                    "l2": "inputs larger than L2 (no flush)", "cuda_graph": used_graph,
                    "parallelism": f"replicas x{world}"},
-        "particles_per_s": n / (ms / 1e3) * world,
+        "particles_per_s": job_rate(ranks, n, ms) * 1e6,
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,
-        "e2e": {"value": cells / (e2e_ms / 1e3) / 1e6 * world, "unit": "Mcells/s",
+        "e2e": {"value": job_rate(ranks, cells, e2e_ms), "unit": "Mcells/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "fp64": fp64,
