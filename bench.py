@@ -129,6 +129,20 @@ def algorithmic_bytes(solver, w, levels, csz, rsz):
     return out
 
 
+def kernel_source_hash():
+    """sha256 over the CUDA sources of the library (file names and contents, in
+    name order): identifies the kernels a DRAM-traffic capture was taken on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1410_0010_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
 # ----------------------------------------------------------------------------
 # oracle sample (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------
@@ -373,7 +387,10 @@ def run_apm(args):
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            traffic = json.load(f).get(f"{w.name}:{top}")
+            tj = json.load(f)
+        # counters taken on other kernel sources do not describe these kernels
+        if tj.get("source_sha256") == kernel_source_hash():
+            traffic = tj.get("per_launch_bytes", {}).get(f"{w.name}:{top}")
     roofline = {"bound": "hbm", "kernel": top, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_source": peak_src, "traffic": traffic}
 
