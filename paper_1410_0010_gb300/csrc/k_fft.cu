@@ -4,7 +4,8 @@
 // the window of cells [-2, N+2) of the result is written.
 //
 // Five passes, each one CTA per batch of lines, each line transformed entirely
-// in shared memory by mixed-radix (2, 3, 4, 5, 7, 8) Stockham stages (ping-pong
+// in shared memory by mixed-radix Stockham stages (radices 2-8, and on the FP32
+// path the composites 6, 9, 10, 12, 14, 15, 16 done in registers; ping-pong
 // between two shared-memory buffers, twiddles staged in shared memory).  A CTA
 // holds a power-of-two number of lines, laid out element-major (line index
 // fastest), so consecutive threads take consecutive lines and no integer
@@ -19,6 +20,8 @@
 //        scaled by 1/(M0 M1 M2)                        -> phi_short[zw][yw][xw]
 // Zero-padded inputs are never read and outputs outside the window never
 // written.  Lines of the y/z passes are tiles of consecutive kx (coalesced).
+#include <utility>
+
 #include "apm_internal.cuh"
 
 namespace apm {
@@ -51,12 +54,82 @@ template <typename T, int DIR> __device__ __forceinline__ C<T> twid(const C<T>* 
     return w;
 }
 
+// ---- roots of unity as compile-time constants --------------------------------
+// cos and sin of a reduced angle |x| <= pi/4 by their Taylor series (terms to
+// x^27: the truncation error is below 1e-30), evaluated by the compiler.
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double ct_sin(double x) {
+    double term = x, sum = x;
+    for (int n = 1; n <= 13; ++n) {
+        term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double ct_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n <= 13; ++n) {
+        term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+        sum += term;
+    }
+    return sum;
+}
+// cos / sin of 2 pi m / R: the quadrant q = floor(4m/R) and the remainder
+// r = 4m - qR (in units of pi/(2R)) are integers, so multiples of pi/2 are exact
+// and the series only sees angles up to pi/4.
+constexpr double ct_cs(int m, int R, bool want_sin) {
+    const int u = ((m % R) + R) % R;
+    const int q = (4 * u) / R, r = 4 * u - q * R;
+    double c = 1.0, s = 0.0;                 // of phi = r pi / (2R), 0 <= phi < pi/2
+    if (r != 0) {
+        if (2 * r <= R) {
+            c = ct_cos(r * kPi / (2.0 * R));
+            s = ct_sin(r * kPi / (2.0 * R));
+        } else {
+            c = ct_sin((R - r) * kPi / (2.0 * R));
+            s = ct_cos((R - r) * kPi / (2.0 * R));
+        }
+    }
+    double cc = c, ss = s;                   // rotate by q quarter turns
+    if (q == 1) { cc = -s; ss = c; }
+    if (q == 2) { cc = -c; ss = -s; }
+    if (q == 3) { cc = s; ss = -c; }
+    return want_sin ? ss : cc;
+}
+// v times exp(DIR 2 pi i m / R); quarter turns are exact rotations
+template <typename T, int DIR, int M, int R> __device__ __forceinline__ C<T> mul_root(C<T> v) {
+    constexpr int u = ((M % R) + R) % R;
+    constexpr int quarter = (4 * u) % R == 0 ? (4 * u) / R : -1;
+    if constexpr (quarter == 0) {
+        return v;
+    } else if constexpr (quarter == 2) {
+        return mk<T>(-v.x, -v.y);
+    } else if constexpr (quarter == 1 || quarter == 3) {
+        // (DIR i)^quarter: i when DIR quarter = 1 mod 4, -i when 3 mod 4
+        constexpr int turn = (((DIR * quarter) % 4) + 4) % 4;
+        if constexpr (turn == 1) return mk<T>(-v.y, v.x);
+        else return mk<T>(v.y, -v.x);
+    } else {
+        constexpr T re = (T)ct_cs(M, R, false);
+        constexpr T im = (T)(DIR * ct_cs(M, R, true));
+        return mk<T>(v.x * re - v.y * im, v.x * im + v.y * re);
+    }
+}
+
+// compile-time loop: f(std::integral_constant<int, 0>) ... f(<N-1>)
+template <typename F, int... I>
+__device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F> __device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 // In-register DFT of size R: X_q = sum_r v_r exp(DIR 2 pi i q r / R).
-// `root` holds exp(DIR 2 pi i t / R), t < R (used by the odd radices).
 template <typename T, int DIR, int R> struct Dft;
 
 template <typename T, int DIR> struct Dft<T, DIR, 2> {
-    __device__ static void run(C<T>* v, const C<T>*) {
+    __device__ static void run(C<T>* v) {
         C<T> a = v[0], b = v[1];
         v[0] = add<T>(a, b);
         v[1] = sub<T>(a, b);
@@ -64,7 +137,7 @@ template <typename T, int DIR> struct Dft<T, DIR, 2> {
 };
 
 template <typename T, int DIR> struct Dft<T, DIR, 4> {
-    __device__ static void run(C<T>* v, const C<T>*) {
+    __device__ static void run(C<T>* v) {
         C<T> t0 = add<T>(v[0], v[2]), t1 = sub<T>(v[0], v[2]);
         C<T> t2 = add<T>(v[1], v[3]), t3 = rot90<T, DIR>(sub<T>(v[1], v[3]));
         v[0] = add<T>(t0, t2);
@@ -75,11 +148,11 @@ template <typename T, int DIR> struct Dft<T, DIR, 4> {
 };
 
 template <typename T, int DIR> struct Dft<T, DIR, 8> {
-    __device__ static void run(C<T>* v, const C<T>*) {
+    __device__ static void run(C<T>* v) {
         C<T> e[4] = {v[0], v[2], v[4], v[6]};
         C<T> o[4] = {v[1], v[3], v[5], v[7]};
-        Dft<T, DIR, 4>::run(e, nullptr);
-        Dft<T, DIR, 4>::run(o, nullptr);
+        Dft<T, DIR, 4>::run(e);
+        Dft<T, DIR, 4>::run(o);
         const T h = (T)0.70710678118654752440084436210484903928;
         // o_q * exp(DIR 2 pi i q / 8)
         C<T> o1 = mk<T>(h * (o[1].x - DIR * o[1].y), h * (o[1].y + DIR * o[1].x));
@@ -96,60 +169,71 @@ template <typename T, int DIR> struct Dft<T, DIR, 8> {
     }
 };
 
-// odd radices: direct sum with the roots of unity
+// odd prime R (3, 5, 7): with a_k = v_k + v_{R-k}, b_k = v_k - v_{R-k}
+// (k = 1 .. (R-1)/2),
+//   X_0     = v_0 + sum_k a_k
+//   X_q     = v_0 + sum_k cos(2 pi qk/R) a_k + DIR i sum_k sin(2 pi qk/R) b_k
+//   X_{R-q} = the same with -DIR i,
+// every cosine and sine a compile-time constant.
 template <typename T, int DIR, int R> struct Dft {
-    __device__ static void run(C<T>* v, const C<T>* root) {
-        C<T> out[R];
+    __device__ static void run(C<T>* v) {
+        constexpr int H = (R - 1) / 2;
+        C<T> a[H], b[H];
+        const C<T> x0 = v[0];
+        C<T> s0 = x0;
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            C<T> acc = v[0];
-#pragma unroll
-            for (int r = 1; r < R; ++r) acc = add<T>(acc, mul<T>(v[r], root[(q * r) % R]));
-            out[q] = acc;
+        for (int k = 1; k <= H; ++k) {
+            a[k - 1] = add<T>(v[k], v[R - k]);
+            b[k - 1] = sub<T>(v[k], v[R - k]);
+            s0 = add<T>(s0, a[k - 1]);
         }
-#pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = out[q];
+        sfor<H>([&](auto qi) {
+            constexpr int q = decltype(qi)::value + 1;
+            C<T> re = x0, im = mk<T>(0, 0);
+            sfor<H>([&](auto ki) {
+                constexpr int k = decltype(ki)::value + 1;
+                constexpr T c = (T)ct_cs(q * k, R, false);
+                constexpr T sn = (T)ct_cs(q * k, R, true);
+                re.x += c * a[k - 1].x;
+                re.y += c * a[k - 1].y;
+                im.x += sn * b[k - 1].x;
+                im.y += sn * b[k - 1].y;
+            });
+            // DIR i im
+            const C<T> r = DIR > 0 ? mk<T>(-im.y, im.x) : mk<T>(im.y, -im.x);
+            v[q] = add<T>(re, r);
+            v[R - q] = sub<T>(re, r);
+        });
+        v[0] = s0;
     }
 };
 
 // Composite radix R = R1 R2 in registers (Cooley-Tukey inside the butterfly):
 // with n = R2 n1 + n2 and k = k1 + R1 k2,
 //   X[k1 + R1 k2] = sum_n2 w_R2^(n2 k2) w_R^(n2 k1) sum_n1 v[R2 n1 + n2] w_R1^(n1 k1),
-// w_m = exp(DIR 2 pi i / m); powers of w_R come from the length-L twiddles
-// (w_R^t = tw[t L/R]).
+// w_m = exp(DIR 2 pi i / m); every w_R^(n2 k1) is a compile-time constant.
 template <typename T, int DIR, int R1, int R2>
 struct DftC {
-    __device__ static void run(C<T>* v, const C<T>* __restrict__ tw, int sR) {
+    __device__ static void run(C<T>* v) {
         constexpr int R = R1 * R2;
-        C<T> r1[R1], r2[R2];
-        if (R1 & 1) {
-#pragma unroll
-            for (int t = 0; t < R1; ++t) r1[t] = twid<T, DIR>(tw, ((t * R2) % R) * sR);
-        }
-        if (R2 & 1) {
-#pragma unroll
-            for (int t = 0; t < R2; ++t) r2[t] = twid<T, DIR>(tw, ((t * R1) % R) * sR);
-        }
-#pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) {
+        sfor<R2>([&](auto n2i) {
+            constexpr int n2 = decltype(n2i)::value;
             C<T> t[R1];
 #pragma unroll
             for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[R2 * n1 + n2];
-            Dft<T, DIR, R1>::run(t, r1);
-#pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) {
-                C<T> y = t[k1];
-                if (k1 > 0 && n2 > 0) y = mul<T>(y, twid<T, DIR>(tw, ((n2 * k1) % R) * sR));
-                v[R2 * k1 + n2] = y;
-            }
-        }
+            Dft<T, DIR, R1>::run(t);
+            sfor<R1>([&](auto k1i) {
+                constexpr int k1 = decltype(k1i)::value;
+                v[R2 * k1 + n2] = mul_root<T, DIR, n2 * k1, R>(t[k1]);
+            });
+        });
         C<T> out[R];
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) {
             C<T> t[R2];
 #pragma unroll
             for (int n2 = 0; n2 < R2; ++n2) t[n2] = v[R2 * k1 + n2];
-            Dft<T, DIR, R2>::run(t, r2);
+            Dft<T, DIR, R2>::run(t);
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) out[k1 + R1 * k2] = t[k2];
         }
@@ -177,11 +261,6 @@ __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int 
         const int step = L / (Ns * R);
         int jm = j % Ns, k = j / Ns;
         const int djm = jstep % Ns, dk = jstep / Ns;
-        C<T> root[R2 == 1 ? R : 1];
-        if (R2 == 1 && (R & 1)) {
-#pragma unroll
-            for (int t = 0; t < R; ++t) root[t] = twid<T, DIR>(tw, t * nb);
-        }
         for (; j < nb; j += jstep) {
             C<T> v[R];
 #pragma unroll
@@ -190,8 +269,8 @@ __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int 
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[r] = mul<T>(v[r], twid<T, DIR>(tw, jm * r * step));
             }
-            if (R2 == 1) Dft<T, DIR, R1>::run(v, root);
-            else DftC<T, DIR, R1, R2>::run(v, tw, nb);
+            if constexpr (R2 == 1) Dft<T, DIR, R1>::run(v);
+            else DftC<T, DIR, R1, R2>::run(v);
             const int idx = k * Ns * R + jm;
 #pragma unroll
             for (int r = 0; r < R; ++r) dst[(idx + r * Ns) * es + line] = v[r];
