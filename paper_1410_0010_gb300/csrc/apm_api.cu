@@ -517,7 +517,14 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             g.cells_gmf = (long long)g.G[0] * g.G[1] * g.G[2];
             g.inv2d = 0.5 / delta;
             g.rows_gas = std::max(1, kChunkCells / g.G[0]);
-            g.rows_acc = std::max(1, kChunkCells / (g.N[0] + 2));
+            // 2x2x2 output blocks pair level cells (2k+1, 2k+2), the two children
+            // between the same parent centres
+            for (int j = 0; j < 3; ++j) {
+                const long long ic0 = g.start[j] - 1;       // output cell 0 (cell -1)
+                g.acc_sh[j] = (ic0 & 1) ? 0 : 1;
+                g.acc_nb[j] = (g.N[j] + 2 + g.acc_sh[j] + 1) / 2;
+            }
+            g.rows_acc = std::max(1, (kChunkCells / 4) / g.acc_nb[0]);
             g.np_x = fft_row_pairs(g.M[0], f64);
             g.tx_y = fft_col_lines(g.M[1], f64);
             g.tx_z = fft_col_lines(g.M[2], f64);
@@ -585,8 +592,8 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             for (long long t = 0; t < (pairs_o + g.np_x - 1) / g.np_x; ++t) xi.push_back({k, (int)t});
             const long long grows = (long long)g.G[1] * g.G[2];
             for (long long t = 0; t < (grows + g.rows_gas - 1) / g.rows_gas; ++t) gas.push_back({k, (int)t});
-            const long long erows = (long long)(g.N[1] + 2) * (g.N[2] + 2);
-            for (long long t = 0; t < (erows + g.rows_acc - 1) / g.rows_acc; ++t) acc.push_back({k, (int)t});
+            const long long brows = (long long)g.acc_nb[1] * g.acc_nb[2];
+            for (long long t = 0; t < (brows + g.rows_acc - 1) / g.rows_acc; ++t) acc.push_back({k, (int)t});
             sxf = std::max(sxf, fft_row_smem(g.M[0], g.np_x, csz));
             syf = std::max(syf, fft_col_smem(g.M[1], g.tx_y, csz));
             sz = std::max(sz, fft_col_smem(g.M[2], g.tx_z, csz));

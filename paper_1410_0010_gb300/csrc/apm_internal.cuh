@@ -108,7 +108,9 @@ struct GridDev {
     int np_x;            // row pairs per CTA of the x passes
     int tx_y, tx_z;      // kx lines per CTA of the y / z passes
     int rows_gas;        // GMF rows per CTA of the baryon initialisation
-    int rows_acc;        // output rows per CTA of the acceleration kernel
+    int rows_acc;        // rows of 2x2x2 output blocks per CTA of the acceleration kernel
+    int acc_sh[3];       // 1 when output cell 0 is the second cell of its block, else 0
+    int acc_nb[3];       // output blocks per axis
     double inv2d;        // 1 / (2 delta)
 };
 

@@ -5,40 +5,55 @@
 namespace apm {
 namespace {
 
-// Trilinear weights of child cell ic from the parent cell centres, R = 2: in
-// parent units the child centre is at (ic + 1/2)/2, i.e. 3/4 (even ic) or 1/4
-// (odd ic) of a cell above the centre of parent cell i0 = floor((ic - 1) / 2),
-// so i0 weighs 1/4 for even ic and 3/4 for odd ic (i0 + 1 the rest).
-__device__ __forceinline__ void carry_axis(long long ic, long long pstart, int& i0, float& w_lo) {
-    long long a = (ic - 1) >> 1;          // floor((ic - 1) / 2)
-    i0 = (int)(a - pstart) + 1;           // +1: parent ghost offset
-    w_lo = (ic & 1) ? 0.75f : 0.25f;
-}
-
-// trilinear interpolation of one parent field, separably (x, then y, then z);
-// the weights 1/4, 3/4 are exact in either precision
+// acc_j(c) = -(phis(c+e_j) - phis(c-e_j)) / (2 delta) + I(parent acc_j)(c)
+// phi(c)   = phis(c) + I(parent phi)(c),    c in [-1, N]^3
+// I is the trilinear interpolation from the parent cell centres (Sec. 2.2), for
+// R = 2: level cells 2k+1 and 2k+2 lie 1/4 and 3/4 of a parent cell above the
+// centre of parent cell k, so they weigh parent cells (k, k+1) with (3/4, 1/4)
+// and (1/4, 3/4).  Each thread computes one 2x2x2 block of such cells: the 8
+// parent values of a field serve all 8 cells, interpolated separably (x, then
+// y, then z), and the 32 values of phis around the block serve the 8 centred
+// differences.  Everything is evaluated in T; the weights are exact.
+// A block may straddle the edge of [-1, N]: its outside cells are not written
+// and the loads they would need are clamped into the window.
 template <typename T>
-__device__ __forceinline__ T trilinear(const T* __restrict__ f, unsigned base, int P0, unsigned P01,
-                                       T wx, T wy, T wz) {
-    T c[2][2];
+__device__ __forceinline__ void lerp_block(const T q[2][2][2], T out[2][2][2]) {
+    const T a = (T)0.75, b = (T)0.25;
+    T x[2][2][2], y[2][2][2];
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
-            const T* r = f + base + dy * P0 + dz * P01;
-            c[dz][dy] = wx * r[0] + ((T)1 - wx) * r[1];
+            x[dz][dy][0] = a * q[dz][dy][0] + b * q[dz][dy][1];
+            x[dz][dy][1] = b * q[dz][dy][0] + a * q[dz][dy][1];
         }
-    T e0 = wy * c[0][0] + ((T)1 - wy) * c[0][1];
-    T e1 = wy * c[1][0] + ((T)1 - wy) * c[1][1];
-    return wz * e0 + ((T)1 - wz) * e1;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+            y[dz][0][cx] = a * x[dz][0][cx] + b * x[dz][1][cx];
+            y[dz][1][cx] = b * x[dz][0][cx] + a * x[dz][1][cx];
+        }
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+            out[0][cy][cx] = a * y[0][cy][cx] + b * y[1][cy][cx];
+            out[1][cy][cx] = b * y[0][cy][cx] + a * y[1][cy][cx];
+        }
 }
 
-// acc_j(c) = -(phis(c+e_j) - phis(c-e_j)) / (2 delta) + I(parent acc_j)(c)
-// phi(c)   = phis(c) + I(parent phi)(c),    c in [-1, N]^3
-// I is the trilinear interpolation from the parent cell centres.  Everything is
-// evaluated in T: the FP64 path in FP64, the FP32 path in FP32 (the weights are
-// exact; the interpolated FP32 fields carry no more digits than FP32 anyway).
-// One CTA per batch of `rows_per_cta` output rows (x fastest over threads).
+template <typename T>
+__device__ __forceinline__ void load_parent(const T* __restrict__ f, unsigned base, int P0, unsigned P01,
+                                            T q[2][2][2]) {
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) q[dz][dy][dx] = f[base + dx + dy * P0 + dz * P01];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __restrict__ pgrids,
                                                const void* const* __restrict__ phis_p,
@@ -46,13 +61,14 @@ __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __rest
                                                const void* const* __restrict__ pacc_p,
                                                void* const* __restrict__ phi_p,
                                                void* const* __restrict__ acc_p,
-                                               const Chunk* __restrict__ chunks, int rows_per_cta) {
+                                               const Chunk* __restrict__ chunks) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = L.g[ch.grid];
     const int E0 = g.N[0] + 2, E1 = g.N[1] + 2, E2 = g.N[2] + 2;
     const unsigned ncell = (unsigned)E0 * E1 * E2;
-    const int nrows = E1 * E2;
-    const int W0 = g.W[0], W1 = g.W[1];
+    const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
+    const int nbx = g.acc_nb[0], nby = g.acc_nb[1];
+    const int nbrows = nby * g.acc_nb[2];
     const T* __restrict__ phis = reinterpret_cast<const T*>(phis_p[ch.grid]);
     T* __restrict__ phi = reinterpret_cast<T*>(phi_p[ch.grid]);
     T* __restrict__ acc = reinterpret_cast<T*>(acc_p[ch.grid]);
@@ -61,54 +77,149 @@ __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __rest
     const T* __restrict__ pacc = carry ? reinterpret_cast<const T*>(pacc_p[g.parent]) : nullptr;
     int P0 = 0;
     unsigned P01 = 0, pn = 0;
-    long long ps0 = 0, ps1 = 0, ps2 = 0;
+    long long ps[3] = {0, 0, 0};
     if (carry) {
         const GridDev& p = pgrids[g.parent];
         P0 = p.N[0] + 2;
         P01 = (unsigned)P0 * (p.N[1] + 2);
         pn = P01 * (p.N[2] + 2);
-        ps0 = p.start[0]; ps1 = p.start[1]; ps2 = p.start[2];
+        ps[0] = p.start[0]; ps[1] = p.start[1]; ps[2] = p.start[2];
     }
     const T inv2d = (T)g.inv2d;
     const unsigned sy = W0, sz = (unsigned)W0 * W1;
     const int r0 = ch.tile * g.rows_acc;
-    const int r1 = min(nrows, r0 + g.rows_acc);
-    int last = -1, iy = 0, iz = 0;
-    float wyf = 0.f, wzf = 0.f;
-    unsigned prow = 0, orow = 0;
-    for (RowWalk it(r0, E0); it.r < r1; it.next()) {
-        const int r = it.r, ex = it.x;
-        if (r != last) {
-            last = r;
-            const int ey = r % E1, ez = r / E1;
-            if (carry) {
-                carry_axis(g.start[1] + (long long)ey - 1, ps1, iy, wyf);
-                carry_axis(g.start[2] + (long long)ez - 1, ps2, iz, wzf);
+    const int r1 = min(nbrows, r0 + g.rows_acc);
+    int last = -1;
+    int ey0 = 0, ez0 = 0;
+    unsigned ybase[4] = {0, 0, 0, 0}, zbase[4] = {0, 0, 0, 0};   // phis offsets of rows -1, 0, 1, 2 of the block
+    unsigned prow = 0;
+    for (RowWalk it(r0, nbx); it.r < r1; it.next()) {
+        if (it.r != last) {
+            last = it.r;
+            const int by = it.r % nby, bz = it.r / nby;
+            ey0 = 2 * by - g.acc_sh[1];
+            ez0 = 2 * bz - g.acc_sh[2];
+            // output cell e has phis index e + 1 on each axis; clamp into [0, W)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ybase[k] = sy * (unsigned)min(max(ey0 + k, 0), W1 - 1);
+                zbase[k] = sz * (unsigned)min(max(ez0 + k, 0), W2 - 1);
             }
-            prow = 1 + sy * (ey + 1) + sz * (ez + 1);   // phis index of x = -1
-            orow = (unsigned)r * E0;
+            if (carry) {
+                // the odd level cell of the block's pair (2k+1) gives parent cell k
+                const long long ky = ((g.start[1] + ey0 - 1) - 1) >> 1;
+                const long long kz = ((g.start[2] + ez0 - 1) - 1) >> 1;
+                prow = (unsigned)(ky - ps[1] + 1) * (unsigned)P0 + (unsigned)(kz - ps[2] + 1) * P01;
+            }
         }
-        const unsigned ps = prow + ex;
-        T p0 = phis[ps];
-        T a0 = -(phis[ps + 1] - phis[ps - 1]) * inv2d;
-        T a1 = -(phis[ps + sy] - phis[ps - sy]) * inv2d;
-        T a2 = -(phis[ps + sz] - phis[ps - sz]) * inv2d;
+        const int ex0 = 2 * it.x - g.acc_sh[0];
+        int xi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xi[k] = min(max(ex0 + k, 0), W0 - 1);
+        // centre values (phis index e + 1 = ex0 + 1 + a, i.e. xi[1 + a], rows 1 + b, 1 + c)
+        T pc[2][2][2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) pc[c][b][a] = phis[zbase[1 + c] + ybase[1 + b] + xi[1 + a]];
+        T out[2][2][2], q[2][2][2];
+        unsigned pbase = 0;
         if (carry) {
-            int ix;
-            float wxf;
-            carry_axis(g.start[0] + (long long)ex - 1, ps0, ix, wxf);
-            const unsigned base = ix + P0 * iy + P01 * iz;
-            const T wx = (T)wxf, wy = (T)wyf, wz = (T)wzf;
-            p0 += trilinear<T>(pphi, base, P0, P01, wx, wy, wz);
-            a0 += trilinear<T>(pacc, base, P0, P01, wx, wy, wz);
-            a1 += trilinear<T>(pacc + pn, base, P0, P01, wx, wy, wz);
-            a2 += trilinear<T>(pacc + 2 * pn, base, P0, P01, wx, wy, wz);
+            const long long kx = ((g.start[0] + ex0 - 1) - 1) >> 1;
+            pbase = prow + (unsigned)(kx - ps[0] + 1);
         }
-        const unsigned o = orow + ex;
-        phi[o] = p0;
-        acc[o] = a0;
-        acc[ncell + o] = a1;
-        acc[2 * ncell + o] = a2;
+        bool wr[2][2][2];
+        unsigned o[2][2][2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int ex = ex0 + a, ey = ey0 + b, ez = ez0 + c;
+                    wr[c][b][a] = ex >= 0 && ex < E0 && ey >= 0 && ey < E1 && ez >= 0 && ez < E2;
+                    o[c][b][a] = (unsigned)ex + (unsigned)E0 * ((unsigned)ey + (unsigned)E1 * (unsigned)ez);
+                }
+        // phi
+        if (carry) {
+            load_parent<T>(pphi, pbase, P0, P01, q);
+            lerp_block<T>(q, out);
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+                    if (wr[c][b][a]) phi[o[c][b][a]] = carry ? pc[c][b][a] + out[c][b][a] : pc[c][b][a];
+        // acc_x: neighbours at phis x indices xi[0] and xi[3]
+        {
+            if (carry) {
+                load_parent<T>(pacc, pbase, P0, P01, q);
+                lerp_block<T>(q, out);
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const unsigned row = zbase[1 + c] + ybase[1 + b];
+                    const T lo = phis[row + xi[0]], hi = phis[row + xi[3]];
+                    T g0 = -(pc[c][b][1] - lo) * inv2d;
+                    T g1 = -(hi - pc[c][b][0]) * inv2d;
+                    if (carry) {
+                        g0 += out[c][b][0];
+                        g1 += out[c][b][1];
+                    }
+                    if (wr[c][b][0]) acc[o[c][b][0]] = g0;
+                    if (wr[c][b][1]) acc[o[c][b][1]] = g1;
+                }
+        }
+        // acc_y: rows ybase[0] and ybase[3]
+        {
+            if (carry) {
+                load_parent<T>(pacc + pn, pbase, P0, P01, q);
+                lerp_block<T>(q, out);
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const T lo = phis[zbase[1 + c] + ybase[0] + xi[1 + a]];
+                    const T hi = phis[zbase[1 + c] + ybase[3] + xi[1 + a]];
+                    T g0 = -(pc[c][1][a] - lo) * inv2d;
+                    T g1 = -(hi - pc[c][0][a]) * inv2d;
+                    if (carry) {
+                        g0 += out[c][0][a];
+                        g1 += out[c][1][a];
+                    }
+                    if (wr[c][0][a]) acc[ncell + o[c][0][a]] = g0;
+                    if (wr[c][1][a]) acc[ncell + o[c][1][a]] = g1;
+                }
+        }
+        // acc_z: planes zbase[0] and zbase[3]
+        {
+            if (carry) {
+                load_parent<T>(pacc + 2 * pn, pbase, P0, P01, q);
+                lerp_block<T>(q, out);
+            }
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const T lo = phis[zbase[0] + ybase[1 + b] + xi[1 + a]];
+                    const T hi = phis[zbase[3] + ybase[1 + b] + xi[1 + a]];
+                    T g0 = -(pc[1][b][a] - lo) * inv2d;
+                    T g1 = -(hi - pc[0][b][a]) * inv2d;
+                    if (carry) {
+                        g0 += out[0][b][a];
+                        g1 += out[1][b][a];
+                    }
+                    if (wr[0][b][a]) acc[2 * ncell + o[0][b][a]] = g0;
+                    if (wr[1][b][a]) acc[2 * ncell + o[1][b][a]] = g1;
+                }
+        }
     }
 }
 
@@ -232,8 +343,8 @@ cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const v
                          void* const* acc, const Chunk* chunks, int n_chunks, int rows_per_cta,
                          cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    k_accel<T><<<n_chunks, 256, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks,
-                                        rows_per_cta);
+    (void)rows_per_cta;
+    k_accel<T><<<n_chunks, 256, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks);
     return cudaGetLastError();
 }
 

@@ -76,6 +76,25 @@ def test_odd_and_mixed_fft_lengths(precision):
     compare(gpu, ref, precision)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_odd_starts_odd_root_and_grandchild(precision):
+    """Odd interior starts and sizes on every axis: the parent carry pairs level
+    cells (2k+1, 2k+2) between the same parent centres, so odd starts put the
+    first and last cell of a row in half-filled pairs; the isolated root has an
+    odd N (21, M = 42)."""
+    grids = [GridDesc(0, -1, (0, 0, 0), (21, 21, 21)),
+             GridDesc(1, 0, (9, 11, 13), (15, 12, 9)),
+             GridDesc(1, 0, (27, 7, 25), (9, 17, 11)),
+             GridDesc(2, 1, (25, 27, 31), (11, 9, 7))]
+    rng = np.random.default_rng(13)
+    parts = W.concat_particles(_random_particles(rng, 500, 0.05, 0.95, vscale=0.2),
+                               _random_particles(rng, 300, 0.3, 0.42, vscale=0.2))
+    gas = [None, rng.random((9, 12, 15)) + 0.2, None, rng.random((7, 9, 11)) + 0.2]
+    ref = run_oracle(grids, parts, 1e-3, gas=gas)
+    gpu = run_gpu(grids, parts, 1e-3, gas=gas, precision=precision)
+    compare(gpu, ref, precision)
+
+
 def test_edge_particles_faces_corners_border_and_outside():
     grids = [GridDesc(0, -1, (0, 0, 0), (16, 16, 16)), GridDesc(1, 0, (10, 10, 10), (8, 8, 8))]
     d0, d1 = 1 / 16, 1 / 32
