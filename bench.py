@@ -299,6 +299,8 @@ def run_apm(args):
     def step32():
         s32.step(P, w.half_dt, b32, pacc, gas=gas, levels=levels)
 
+    # FFT pass launch shapes from the library's autotuner (one tuned solve per level)
+    shapes32 = s32.autotune(P, w.half_dt, b32, gas=gas, levels=levels) if not args.no_tune else None
     for _ in range(args.warmup):
         step32()
     s32.sync_status()
@@ -356,6 +358,8 @@ def run_apm(args):
         def step64():
             s64.step(P, w.half_dt, b64, pacc64, gas=gas, levels=levels)
 
+        if not args.no_tune:
+            s64.autotune(P, w.half_dt, b64, gas=gas, levels=levels)
         for _ in range(max(1, args.warmup // 2)):
             step64()
         s64.sync_status()
@@ -409,7 +413,8 @@ def run_apm(args):
         "config": {"workload": w.name, "levels": levels, "grids": len(w.grids),
                    "interior_cells": cells, "particles": n, "periodic": w.periodic,
                    "l2": "inputs larger than L2 (no flush)", "cuda_graph": used_graph,
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "fft_shapes": shapes32},
         "particles_per_s": job_rate(ranks, n, ms) * 1e6,
         "roofline": roofline,
         "kernels": kernels,
@@ -437,6 +442,7 @@ def main():
     ap.add_argument("--workload", choices=["c3", "c4", "c5", "c5s"], default="c5")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -181,7 +181,9 @@ apm_status apm_deposit(apm_ctx* ctx, int32_t level, const apm_particles* particl
  * the window of cells [-2, dims+2) is written:
  *  phi_short: HOST array (grids of the level) of device pointers to
  *             (dims+4)^3 floats/doubles (apm_grid_info.phi_short)
- * The FFTs are hand-written mixed-radix (2,3,4,5,7,8) Stockham passes. */
+ * The FFTs are hand-written mixed-radix Stockham passes (radices 2-8; the
+ * FP32 path also 6, 9, 10, 12, 14, 15, 16 in registers), five launches: x
+ * forward, y forward, z forward + table + z inverse, y inverse, x inverse. */
 apm_status apm_solve_level(apm_ctx* ctx, int32_t level, const int64_t* const* gmf,
                            void* const* phi_short, void* stream);
 
@@ -198,6 +200,37 @@ apm_status apm_solve_level(apm_ctx* ctx, int32_t level, const int64_t* const* gm
 apm_status apm_accel(apm_ctx* ctx, int32_t level, const void* const* phi_short,
                      const void* const* parent_phi, const void* const* parent_acc,
                      void* const* phi, void* const* acc, void* stream);
+
+/* Launch shapes of the five FFT passes of one level (x forward, y forward, z
+ * with the table, y inverse, x inverse), in that order.  budget[p] is the
+ * number of complex elements one shared-memory buffer of a pass CTA aims at:
+ * each grid batches pow2_floor(budget / M) lines per CTA (1..32 row pairs for
+ * the x passes, 4..32 kx columns for the y/z passes, 2..32 in FP64), halved
+ * while the CTA needs more than 200 KB of shared memory.  threads[p] is the
+ * CTA size, 128 or 256.  The defaults are budget 2048
+ * (FP32) / 1024 (FP64) and 256 threads.  A shape only regroups whole lines, so
+ * it never changes a result, bit for bit.  The paper has no counterpart: this
+ * is a property of the GPU launch, not of the method. */
+typedef struct {
+    int32_t budget[5];
+    int32_t threads[5];
+} apm_fft_shapes;
+
+/* Autotuner: solves `level` like apm_solve_level (same arguments and outputs)
+ * while timing every candidate shape of each FFT pass in turn (budgets
+ * 512..8192 (FP32) or 256..4096 (FP64) by powers of two, 128 or 256 threads;
+ * the mean of two launches after a warm one, CUDA events on `stream`), and
+ * keeps the fastest shape per pass for the context's later calls.  phi_short
+ * holds the level's potential on return.  Synchronises `stream` and the
+ * device several times: APM_E_STATE while `stream` is being captured. */
+apm_status apm_autotune_level(apm_ctx* ctx, int32_t level, const int64_t* const* gmf,
+                              void* const* phi_short, void* stream);
+
+/* The shapes in use for `level`, and setting them (for instance from a cache
+ * of earlier autotuner results).  apm_set_fft_shapes synchronises the device;
+ * APM_E_INVALID for a budget < 1 or a thread count outside the rule above. */
+apm_status apm_get_fft_shapes(const apm_ctx* ctx, int32_t level, apm_fft_shapes* out);
+apm_status apm_set_fft_shapes(apm_ctx* ctx, int32_t level, const apm_fft_shapes* shapes);
 
 /* TSC interpolation of the cell accelerations to the particles (Sec. 2, the
  * same 27 weights as the deposit, at the same drifted position).  Only

@@ -36,6 +36,10 @@ class ApmGridInfo(ctypes.Structure):
                 ("delta", c_dbl)]
 
 
+class ApmFftShapes(ctypes.Structure):
+    _fields_ = [("budget", c_i32 * 5), ("threads", c_i32 * 5)]
+
+
 # name -> (restype, argtypes); every function declared in include/apm.h
 SIGNATURES = {
     "apm_config_default": (None, [ctypes.POINTER(ApmConfig)]),
@@ -54,6 +58,10 @@ SIGNATURES = {
                           ctypes.POINTER(c_void_p), c_void_p]),
     "apm_interp": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p), ctypes.POINTER(ApmParticles),
                            c_dbl, c_void_p, c_void_p]),
+    "apm_autotune_level": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p),
+                                   ctypes.POINTER(c_void_p), c_void_p]),
+    "apm_get_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
+    "apm_set_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
     "apm_sync_status": (c_i32, [c_void_p, c_void_p]),
     "apm_profile_enable": (c_i32, [c_void_p, c_i32, c_i32]),
     "apm_profile_read": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]),

@@ -34,18 +34,25 @@ struct Profiler {
     double ms[K_COUNT] = {};
 };
 
+// Launch shape of one FFT pass over a level: the buffer budget that sets each
+// grid's lines per CTA, the threads per CTA, and the resulting work list.
+struct PassPlan {
+    int budget = 0;
+    int threads = 0;
+    Chunk* d = nullptr;
+    int n = 0;
+    size_t smem = 0;
+    std::vector<int> lines;          // per grid of the level
+};
+
 struct Level {
     int level = 0;
     std::vector<int> grids;          // hierarchy indices, in order
     std::vector<GridDev> hg;         // host copies of the descriptors
     GridDev* d_grids = nullptr;
     LevelDev dev{};
-    // CTA work lists
-    Chunk* d_xf = nullptr; int n_xf = 0; size_t smem_xf = 0;
-    Chunk* d_yf = nullptr; int n_yf = 0; size_t smem_yf = 0;
-    Chunk* d_z = nullptr;  int n_z = 0;  size_t smem_z = 0;
-    Chunk* d_yi = nullptr; int n_yi = 0; size_t smem_yi = 0;
-    Chunk* d_xi = nullptr; int n_xi = 0; size_t smem_xi = 0;
+    // CTA work lists: the FFT passes (launch shape per pass), baryons, accelerations
+    PassPlan pass[kFftPasses];
     Chunk* d_gas = nullptr; int n_gas = 0;
     Chunk* d_acc = nullptr; int n_acc = 0;
     // pointer tables (device) + pinned mirrors + last uploaded values
@@ -106,6 +113,13 @@ apm_status upload(apm_ctx* c, V** dst, const std::vector<V>& src) {
         cudaMemcpy(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess)
         return APM_E_CUDA;
     return APM_OK;
+}
+
+void dfree(apm_ctx* c, void* p) {
+    if (!p) return;
+    cudaFree(p);
+    auto it = std::find(c->dev_allocs.begin(), c->dev_allocs.end(), p);
+    if (it != c->dev_allocs.end()) c->dev_allocs.erase(it);
 }
 
 void free_hierarchy(apm_ctx* c) {
@@ -235,6 +249,71 @@ void build_csr(const std::vector<std::pair<std::array<long long, 3>, std::array<
 }
 
 apm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APM_OK : APM_E_CUDA; }
+
+// Work list of FFT pass q over the grids of a level for a buffer budget and a
+// CTA size: each grid's lines per CTA (halved until the CTA fits its shared
+// memory), one chunk per CTA.  The lines batch whole lines, so the shape never
+// changes a result.
+apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads, bool f64, PassPlan& P) {
+    const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
+    std::vector<Chunk> list;
+    P.lines.assign(L.hg.size(), 0);
+    P.smem = 0;
+    for (int k = 0; k < (int)L.hg.size(); ++k) {
+        const GridDev& g = L.hg[k];
+        const int len = (q == kPassXf || q == kPassXi) ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
+        int lines = fft_pass_lines(q, len, budget, f64);
+        while (lines > 1 && fft_pass_smem(q, len, lines, csz) > (size_t)kFftSmemLimit) lines /= 2;
+        P.lines[k] = lines;
+        P.smem = std::max(P.smem, fft_pass_smem(q, len, lines, csz));
+        const long long kt = (g.Hx + lines - 1) / lines;     // kx tiles of the y / z passes
+        long long n = 0;
+        switch (q) {
+            case kPassXf: n = (((long long)g.G[1] * g.G[2] + 1) / 2 + lines - 1) / lines; break;
+            case kPassXi: n = (((long long)g.W[1] * g.W[2] + 1) / 2 + lines - 1) / lines; break;
+            case kPassYf: n = kt * g.G[2]; break;
+            case kPassZ: n = kt * g.M[1]; break;
+            default: n = kt * g.W[2]; break;
+        }
+        for (long long t = 0; t < n; ++t) list.push_back({k, (int)t});
+    }
+    P.budget = budget;
+    P.threads = threads;
+    P.n = (int)list.size();
+    P.d = nullptr;
+    return upload(c, &P.d, list);
+}
+
+// copies pass q's lines per CTA into the host descriptors of the level
+void apply_pass(Level& L, int q) {
+    for (size_t k = 0; k < L.hg.size(); ++k) L.hg[k].lines[q] = L.pass[q].lines[k];
+}
+
+// launches FFT pass q of a level with plan P
+cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void** d_gmf, void** d_phis,
+                     cudaStream_t s) {
+    const bool f64 = c->cfg.precision == APM_FP64;
+    FftArgs a;
+    a.g = L.d_grids;
+    a.tw = f64 ? (const void*)c->tw64 : (const void*)c->tw32;
+    a.tab = f64 ? (const void*)c->tab64 : (const void*)c->tab32;
+    a.wsA = c->wsA;
+    a.wsB = c->wsB;
+    a.F = c->cfg.mass_frac_bits;
+    a.chunks = P.d;
+    a.n_chunks = P.n;
+    a.smem = P.smem;
+    a.threads = P.threads;
+    switch (q) {
+        case kPassXf:
+            return f64 ? launch_fft_xf<double>(a, (const int64_t* const*)d_gmf, s)
+                       : launch_fft_xf<float>(a, (const int64_t* const*)d_gmf, s);
+        case kPassYf: return f64 ? launch_fft_yf<double>(a, s) : launch_fft_yf<float>(a, s);
+        case kPassZ: return f64 ? launch_fft_z<double>(a, s) : launch_fft_z<float>(a, s);
+        case kPassYi: return f64 ? launch_fft_yi<double>(a, s) : launch_fft_yi<float>(a, s);
+        default: return f64 ? launch_fft_xi<double>(a, d_phis, s) : launch_fft_xi<float>(a, d_phis, s);
+    }
+}
 
 // Uploads the device pointers of one role if they changed since the last call.
 apm_status set_ptrs(apm_ctx* c, Level& L, int role, const void* const* host, int count,
@@ -525,9 +604,6 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
                 g.acc_nb[j] = (g.N[j] + 2 + g.acc_sh[j] + 1) / 2;
             }
             g.rows_acc = std::max(1, (kChunkCells / 4) / g.acc_nb[0]);
-            g.np_x = fft_row_pairs(g.M[0], f64);
-            g.tx_y = fft_col_lines(g.M[1], f64);
-            g.tx_z = fft_col_lines(g.M[2], f64);
             // green table (cached per shape and level parameters)
             TabKey key{g.kind, g.M[0], g.M[1], g.M[2], delta, a_lev, a_par};
             auto it = tab_off.find(key);
@@ -578,38 +654,24 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
     for (Level& L : c->levels) {
         const int ng = (int)L.grids.size();
         if ((st = upload(c, &L.d_grids, L.hg)) != APM_OK) return st;
-        std::vector<Chunk> xf, yf, zc, yi, xi, gas, acc;
-        size_t sxf = 0, syf = 0, sz = 0;
+        std::vector<Chunk> gas, acc;
         for (int k = 0; k < ng; ++k) {
             const GridDev& g = L.hg[k];
-            long long pairs = ((long long)g.G[1] * g.G[2] + 1) / 2;
-            for (long long t = 0; t < (pairs + g.np_x - 1) / g.np_x; ++t) xf.push_back({k, (int)t});
-            int nky = (g.Hx + g.tx_y - 1) / g.tx_y, nkz = (g.Hx + g.tx_z - 1) / g.tx_z;
-            for (int t = 0; t < nky * g.G[2]; ++t) yf.push_back({k, t});
-            for (int t = 0; t < nkz * g.M[1]; ++t) zc.push_back({k, t});
-            for (int t = 0; t < nky * g.W[2]; ++t) yi.push_back({k, t});
-            long long pairs_o = ((long long)g.W[1] * g.W[2] + 1) / 2;
-            for (long long t = 0; t < (pairs_o + g.np_x - 1) / g.np_x; ++t) xi.push_back({k, (int)t});
             const long long grows = (long long)g.G[1] * g.G[2];
             for (long long t = 0; t < (grows + g.rows_gas - 1) / g.rows_gas; ++t) gas.push_back({k, (int)t});
             const long long brows = (long long)g.acc_nb[1] * g.acc_nb[2];
             for (long long t = 0; t < (brows + g.rows_acc - 1) / g.rows_acc; ++t) acc.push_back({k, (int)t});
-            sxf = std::max(sxf, fft_row_smem(g.M[0], g.np_x, csz));
-            syf = std::max(syf, fft_col_smem(g.M[1], g.tx_y, csz));
-            sz = std::max(sz, fft_col_smem(g.M[2], g.tx_z, csz));
         }
-        L.smem_xf = L.smem_xi = sxf;
-        L.smem_yf = L.smem_yi = syf;
-        L.smem_z = sz;
-        if ((st = upload(c, &L.d_xf, xf)) != APM_OK) return st;
-        if ((st = upload(c, &L.d_yf, yf)) != APM_OK) return st;
-        if ((st = upload(c, &L.d_z, zc)) != APM_OK) return st;
-        if ((st = upload(c, &L.d_yi, yi)) != APM_OK) return st;
-        if ((st = upload(c, &L.d_xi, xi)) != APM_OK) return st;
+        for (int q = 0; q < kFftPasses; ++q) {
+            if ((st = build_pass(c, L, q, f64 ? kFftBudgetF64 : kFftBudgetF32, kFftThreads, f64, L.pass[q])) != APM_OK)
+                return st;
+            apply_pass(L, q);
+        }
+        if (cudaMemcpy(L.d_grids, L.hg.data(), L.hg.size() * sizeof(GridDev), cudaMemcpyHostToDevice) != cudaSuccess)
+            return APM_E_CUDA;
         if ((st = upload(c, &L.d_gas, gas)) != APM_OK) return st;
         if ((st = upload(c, &L.d_acc, acc)) != APM_OK) return st;
-        L.n_xf = (int)xf.size(); L.n_yf = (int)yf.size(); L.n_z = (int)zc.size();
-        L.n_yi = (int)yi.size(); L.n_xi = (int)xi.size(); L.n_gas = (int)gas.size(); L.n_acc = (int)acc.size();
+        L.n_gas = (int)gas.size(); L.n_acc = (int)acc.size();
         // tile map
         LevelDev& D = L.dev;
         std::memset(&D, 0, sizeof(D));
@@ -760,32 +822,128 @@ apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
     apm_status st;
     if ((st = set_ptrs(c, L, R_GMF_IN, (const void* const*)gmf, ng, &d_gmf, s)) != APM_OK) return st;
     if ((st = set_ptrs(c, L, R_PHIS, (const void* const*)phi_short, ng, &d_phis, s)) != APM_OK) return st;
+    const Kern kind[kFftPasses] = {K_XF, K_YF, K_Z, K_YI, K_XI};
+    for (int q = 0; q < kFftPasses; ++q) {
+        Trace t(c, kind[q], s);
+        if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) return APM_E_CUDA;
+    }
+    return APM_OK;
+}
+
+apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
+                              void* const* phi_short, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size() || !gmf || !phi_short) return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return APM_E_STATE;
+    Level& L = c->levels[level];
+    const int ng = (int)L.grids.size();
+    for (int i = 0; i < ng; ++i)
+        if (!gmf[i] || !phi_short[i]) return APM_E_INVALID;
+    void **d_gmf, **d_phis;
+    apm_status st;
+    if ((st = set_ptrs(c, L, R_GMF_IN, (const void* const*)gmf, ng, &d_gmf, s)) != APM_OK) return st;
+    if ((st = set_ptrs(c, L, R_PHIS, (const void* const*)phi_short, ng, &d_phis, s)) != APM_OK) return st;
     const bool f64 = c->cfg.precision == APM_FP64;
-    FftArgs a;
-    a.g = L.d_grids;
-    a.tw = f64 ? (const void*)c->tw64 : (const void*)c->tw32;
-    a.tab = f64 ? (const void*)c->tab64 : (const void*)c->tab32;
-    a.wsA = c->wsA;
-    a.wsB = c->wsB;
-    a.F = c->cfg.mass_frac_bits;
-    cudaError_t e;
-    a.chunks = L.d_xf; a.n_chunks = L.n_xf; a.smem = L.smem_xf;
-    { Trace t(c, K_XF, s);
-    e = f64 ? launch_fft_xf<double>(a, (const int64_t* const*)d_gmf, s)
-            : launch_fft_xf<float>(a, (const int64_t* const*)d_gmf, s); }
-    if (e != cudaSuccess) return APM_E_CUDA;
-    a.chunks = L.d_yf; a.n_chunks = L.n_yf; a.smem = L.smem_yf;
-    { Trace t(c, K_YF, s); e = f64 ? launch_fft_yf<double>(a, s) : launch_fft_yf<float>(a, s); }
-    if (e != cudaSuccess) return APM_E_CUDA;
-    a.chunks = L.d_z; a.n_chunks = L.n_z; a.smem = L.smem_z;
-    { Trace t(c, K_Z, s); e = f64 ? launch_fft_z<double>(a, s) : launch_fft_z<float>(a, s); }
-    if (e != cudaSuccess) return APM_E_CUDA;
-    a.chunks = L.d_yi; a.n_chunks = L.n_yi; a.smem = L.smem_yi;
-    { Trace t(c, K_YI, s); e = f64 ? launch_fft_yi<double>(a, s) : launch_fft_yi<float>(a, s); }
-    if (e != cudaSuccess) return APM_E_CUDA;
-    a.chunks = L.d_xi; a.n_chunks = L.n_xi; a.smem = L.smem_xi;
-    { Trace t(c, K_XI, s); e = f64 ? launch_fft_xi<double>(a, d_phis, s) : launch_fft_xi<float>(a, d_phis, s); }
-    return cuda_status(e);
+    const std::vector<int> budgets = f64 ? std::vector<int>{256, 512, 1024, 2048, 4096}
+                                         : std::vector<int>{512, 1024, 2048, 4096, 8192};
+    const int threads[] = {128, 256};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return APM_E_CUDA;
+    }
+    auto upload_grids = [&]() -> apm_status {
+        if (cudaStreamSynchronize(s) != cudaSuccess ||
+            cudaMemcpy(L.d_grids, L.hg.data(), L.hg.size() * sizeof(GridDev), cudaMemcpyHostToDevice) != cudaSuccess)
+            return APM_E_CUDA;
+        return APM_OK;
+    };
+    // mean of two launches after a warm one.  The passes are tuned in order, so
+    // each candidate reads the previous pass's output and rewrites the same
+    // result (the shape never changes a value).
+    auto time_pass = [&](int q, const PassPlan& P, float* ms) -> apm_status {
+        for (size_t k = 0; k < L.hg.size(); ++k) L.hg[k].lines[q] = P.lines[k];
+        apm_status r = upload_grids();
+        if (r != APM_OK) return r;
+        if (run_pass(c, L, q, P, d_gmf, d_phis, s) != cudaSuccess) return APM_E_CUDA;
+        if (cudaEventRecord(e0, s) != cudaSuccess) return APM_E_CUDA;
+        for (int k = 0; k < 2; ++k)
+            if (run_pass(c, L, q, P, d_gmf, d_phis, s) != cudaSuccess) return APM_E_CUDA;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+            return APM_E_CUDA;
+        *ms *= 0.5f;
+        return APM_OK;
+    };
+    for (int q = 0; q < kFftPasses && st == APM_OK; ++q) {
+        float best_ms = 0;
+        st = time_pass(q, L.pass[q], &best_ms);
+        for (size_t bi = 0; bi < budgets.size() && st == APM_OK; ++bi) {
+            for (int t : threads) {
+                PassPlan cand;
+                if ((st = build_pass(c, L, q, budgets[bi], t, f64, cand)) != APM_OK) break;
+                float ms = 0;
+                const bool same = cand.lines == L.pass[q].lines && cand.threads == L.pass[q].threads;
+                if (!same && (st = time_pass(q, cand, &ms)) == APM_OK && ms < best_ms) {
+                    best_ms = ms;
+                    dfree(c, L.pass[q].d);
+                    L.pass[q] = cand;
+                } else {
+                    dfree(c, cand.d);
+                }
+                if (st != APM_OK) break;
+            }
+        }
+        apply_pass(L, q);
+        if (st == APM_OK) st = upload_grids();
+        // the chosen shape leaves this pass's output in place for the next pass
+        if (st == APM_OK && run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) st = APM_E_CUDA;
+    }
+    if (st != APM_OK) {   // keep the descriptors consistent with the plans in use
+        for (int q = 0; q < kFftPasses; ++q) apply_pass(L, q);
+        cudaStreamSynchronize(s);
+        cudaMemcpy(L.d_grids, L.hg.data(), L.hg.size() * sizeof(GridDev), cudaMemcpyHostToDevice);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+apm_status apm_get_fft_shapes(const apm_ctx* c, int32_t level, apm_fft_shapes* out) {
+    if (!c || !out) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size()) return APM_E_INVALID;
+    for (int q = 0; q < kFftPasses; ++q) {
+        out->budget[q] = c->levels[level].pass[q].budget;
+        out->threads[q] = c->levels[level].pass[q].threads;
+    }
+    return APM_OK;
+}
+
+apm_status apm_set_fft_shapes(apm_ctx* c, int32_t level, const apm_fft_shapes* shapes) {
+    if (!c || !shapes) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size()) return APM_E_INVALID;
+    for (int q = 0; q < kFftPasses; ++q) {
+        const int t = shapes->threads[q];
+        if (shapes->budget[q] < 1 || (t != 128 && t != 256)) return APM_E_INVALID;
+    }
+    Level& L = c->levels[level];
+    const bool f64 = c->cfg.precision == APM_FP64;
+    if (cudaDeviceSynchronize() != cudaSuccess) return APM_E_CUDA;
+    for (int q = 0; q < kFftPasses; ++q) {
+        PassPlan P;
+        apm_status st = build_pass(c, L, q, shapes->budget[q], shapes->threads[q], f64, P);
+        if (st != APM_OK) return st;
+        dfree(c, L.pass[q].d);
+        L.pass[q] = P;
+        apply_pass(L, q);
+    }
+    return cudaMemcpy(L.d_grids, L.hg.data(), L.hg.size() * sizeof(GridDev), cudaMemcpyHostToDevice) == cudaSuccess
+               ? APM_OK : APM_E_CUDA;
 }
 
 apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,

@@ -15,30 +15,35 @@ namespace apm {
 // compile-time sizes
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 12;      // radix stages of one 1-D transform
-constexpr int kFftThreads = 256;    // threads of every FFT pass CTA
-// complex elements one buffer of a pass CTA aims at (lines per CTA x length)
+constexpr int kFftThreads = 256;    // most threads of an FFT pass CTA (launch bound)
+// complex elements one buffer of a pass CTA aims at by default (lines x length)
 constexpr int kFftBudgetF32 = 2048;
 constexpr int kFftBudgetF64 = 1024;
+constexpr int kFftSmemLimit = 200 * 1024;   // dynamic shared memory a pass CTA may take
+
+// the five FFT passes of a level solve
+enum { kPassXf = 0, kPassYf = 1, kPassZ = 2, kPassYi = 3, kPassXi = 4, kFftPasses = 5 };
 
 inline int pow2_floor_i(int v) {
     int p = 1;
     while (p * 2 <= v) p *= 2;
     return p;
 }
-// lines (kx columns) per CTA of a y/z pass: a power of two, at least 32 bytes
-// of contiguous row per line group, at most 32
-inline int fft_col_lines(int L, bool f64) {
-    int v = pow2_floor_i(std::max(1, (f64 ? kFftBudgetF64 : kFftBudgetF32) / L));
+// lines per CTA of a pass for a transform of length L and a buffer budget (in
+// complex elements): a power of two; row pairs 1..32 for the x passes, kx
+// columns 4..32 (FP64 2..32) for the y/z passes (at least 32 contiguous bytes
+// of each row a line group reads)
+inline int fft_pass_lines(int pass, int L, int budget, bool f64) {
+    const int v = pow2_floor_i(std::max(1, budget / L));
+    if (pass == kPassXf || pass == kPassXi) return std::min(32, v);
     return std::min(32, std::max(f64 ? 2 : 4, v));
 }
-// complex lines (row pairs) per CTA of an x pass: a power of two, 1..32
-inline int fft_row_pairs(int M0, bool f64) {
-    int v = pow2_floor_i(std::max(1, (f64 ? kFftBudgetF64 : kFftBudgetF32) / M0));
-    return std::min(32, v);
+// dynamic shared memory of a pass CTA: two buffers plus the twiddles (the x
+// passes pad each element row to lines + 1)
+inline size_t fft_pass_smem(int pass, int L, int lines, size_t csz) {
+    if (pass == kPassXf || pass == kPassXi) return (size_t)(2 * L * (lines + 1) + L) * csz;
+    return (size_t)(2 * L * lines + L) * csz;
 }
-// dynamic shared memory of the passes: two buffers plus the twiddles
-inline size_t fft_row_smem(int M0, int np, size_t csz) { return (size_t)(2 * M0 * (np + 1) + M0) * csz; }
-inline size_t fft_col_smem(int L, int tx, size_t csz) { return (size_t)(2 * L * tx + L) * csz; }
 constexpr int kMaxFft = 1024;       // longest supported transform
 
 // device status bits (latched with atomicOr, read by apm_sync_status)
@@ -105,8 +110,7 @@ struct GridDev {
     long long tab_off;   // octant table offset (elements) in the table arenas
     long long wsA, wsB;  // workspace offsets (complex elements)
     long long cells_gmf; // G0 G1 G2
-    int np_x;            // row pairs per CTA of the x passes
-    int tx_y, tx_z;      // kx lines per CTA of the y / z passes
+    int lines[kFftPasses];   // lines per CTA of each pass (row pairs for xf / xi)
     int rows_gas;        // GMF rows per CTA of the baryon initialisation
     int rows_acc;        // rows of 2x2x2 output blocks per CTA of the acceleration kernel
     int acc_sh[3];       // 1 when output cell 0 is the second cell of its block, else 0
@@ -303,6 +307,7 @@ struct FftArgs {
     void* wsB;
     int F;
     size_t smem;
+    int threads;           // threads per CTA: 128 or 256
 };
 cudaError_t fft_configure();
 template <typename T>

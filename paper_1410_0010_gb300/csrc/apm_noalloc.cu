@@ -93,8 +93,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     g.delta = delta;
     g.parent = -1;
     g.cells_gmf = (long long)n * n * n;
-    g.np_x = fft_row_pairs(n, false);
-    g.tx_y = g.tx_z = fft_col_lines(n, false);
+    for (int q = 0; q < kFftPasses; ++q) g.lines[q] = fft_pass_lines(q, n, kFftBudgetF32, false);
     const long long Hx = g.Hx;
     const long long szA = (long long)(n + 4) * n * Hx;         // max(G1 G2, W2 M1) Hx
     const long long szB = (long long)(n + 4) * (n + 4) * Hx;   // max(G2 M1, W2 W1) Hx
@@ -125,14 +124,14 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     g.wsB = 0;
 
     // CTAs of each pass (one grid)
-    const int nky = (int)((Hx + g.tx_y - 1) / g.tx_y);
+    const int nky = (int)((Hx + g.lines[kPassYf] - 1) / g.lines[kPassYf]);   // the same for yi and z
     const long long pairs_in = ((long long)n * n + 1) / 2;
     const long long pairs_out = ((long long)(n + 4) * (n + 4) + 1) / 2;
-    const int n_xf = (int)((pairs_in + g.np_x - 1) / g.np_x);
+    const int n_xf = (int)((pairs_in + g.lines[kPassXf] - 1) / g.lines[kPassXf]);
     const int n_yf = nky * n;
     const int n_z = nky * n;
     const int n_yi = nky * (n + 4);
-    const int n_xi = (int)((pairs_out + g.np_x - 1) / g.np_x);
+    const int n_xi = (int)((pairs_out + g.lines[kPassXi] - 1) / g.lines[kPassXi]);
     const int n_max = std::max(std::max(n_xf, n_yf), std::max(std::max(n_z, n_yi), n_xi));
     if (n_max > kMaxChunks - 2) return APM_E_INVALID;
     // the per-grid pointer tables of the passes sit in the last two chunk slots
@@ -157,8 +156,9 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     a.wsA = wsA;
     a.wsB = wsB;
     a.F = mass_frac_bits;
-    const size_t smem_rows = fft_row_smem(n, g.np_x, sizeof(float2));
-    const size_t smem_cols = fft_col_smem(n, g.tx_y, sizeof(float2));
+    a.threads = kFftThreads;
+    const size_t smem_rows = fft_pass_smem(kPassXf, n, g.lines[kPassXf], sizeof(float2));
+    const size_t smem_cols = fft_pass_smem(kPassYf, n, g.lines[kPassYf], sizeof(float2));
     a.n_chunks = n_xf;
     a.smem = smem_rows;
     if (launch_fft_xf<float>(a, d_in, s) != cudaSuccess) return APM_E_CUDA;

@@ -249,13 +249,13 @@ struct DftC {
 // (j / Ns) Ns R + (j mod Ns) + r Ns: natural order after the last stage.
 // Thread t owns line t mod nl and butterflies j = t / nl + m (threads / nl);
 // j / Ns and j mod Ns are stepped incrementally.
-template <typename T, int DIR, int R1, int R2>
+template <typename T, int DIR, int R1, int R2, int NT>
 __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int L, int Ns, int lg,
                       int es, const C<T>* __restrict__ tw) {
     constexpr int R = R1 * R2;
     const int nb = L / R;
     const int line = threadIdx.x & ((1 << lg) - 1);
-    const int jstep = kFftThreads >> lg;
+    const int jstep = NT >> lg;
     int j = threadIdx.x >> lg;
     if (j < nb) {
         const int step = L / (Ns * R);
@@ -286,17 +286,17 @@ __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int 
 }
 
 // composite stage radices (FP32 plans only)
-template <typename T, int DIR>
+template <typename T, int DIR, int NT>
 __device__ __forceinline__ void stage_composite(int R, const C<T>* a, C<T>* b, int L, int Ns, int lg,
                                                 int es, const C<T>* tw) {
     switch (R) {
-        case 6: stage<T, DIR, 3, 2>(a, b, L, Ns, lg, es, tw); break;
-        case 9: stage<T, DIR, 3, 3>(a, b, L, Ns, lg, es, tw); break;
-        case 10: stage<T, DIR, 5, 2>(a, b, L, Ns, lg, es, tw); break;
-        case 12: stage<T, DIR, 3, 4>(a, b, L, Ns, lg, es, tw); break;
-        case 14: stage<T, DIR, 7, 2>(a, b, L, Ns, lg, es, tw); break;
-        case 15: stage<T, DIR, 5, 3>(a, b, L, Ns, lg, es, tw); break;
-        default: stage<T, DIR, 4, 4>(a, b, L, Ns, lg, es, tw); break;   // 16
+        case 6: stage<T, DIR, 3, 2, NT>(a, b, L, Ns, lg, es, tw); break;
+        case 9: stage<T, DIR, 3, 3, NT>(a, b, L, Ns, lg, es, tw); break;
+        case 10: stage<T, DIR, 5, 2, NT>(a, b, L, Ns, lg, es, tw); break;
+        case 12: stage<T, DIR, 3, 4, NT>(a, b, L, Ns, lg, es, tw); break;
+        case 14: stage<T, DIR, 7, 2, NT>(a, b, L, Ns, lg, es, tw); break;
+        case 15: stage<T, DIR, 5, 3, NT>(a, b, L, Ns, lg, es, tw); break;
+        default: stage<T, DIR, 4, 4, NT>(a, b, L, Ns, lg, es, tw); break;   // 16
     }
 }
 
@@ -304,21 +304,21 @@ __device__ __forceinline__ void stage_composite(int R, const C<T>* a, C<T>* b, i
 // length-L twiddles in shared memory); returns the buffer holding the result.
 // Stage radices 2..8 directly; on the FP32 path also the composites of
 // fft_plan (apm_internal.cuh), computed in registers as R1 x R2.
-template <typename T, int DIR>
+template <typename T, int DIR, int NT>
 __device__ C<T>* fft_lines(C<T>* a, C<T>* b, const FftPlan1D& pl, int lg, int es, const C<T>* tw) {
     const int L = pl.L;
     int Ns = 1;
     for (int st = 0; st < pl.nst; ++st) {
         const int R = pl.radix[st];
         switch (R) {
-            case 2: stage<T, DIR, 2, 1>(a, b, L, Ns, lg, es, tw); break;
-            case 3: stage<T, DIR, 3, 1>(a, b, L, Ns, lg, es, tw); break;
-            case 4: stage<T, DIR, 4, 1>(a, b, L, Ns, lg, es, tw); break;
-            case 5: stage<T, DIR, 5, 1>(a, b, L, Ns, lg, es, tw); break;
-            case 7: stage<T, DIR, 7, 1>(a, b, L, Ns, lg, es, tw); break;
-            case 8: stage<T, DIR, 8, 1>(a, b, L, Ns, lg, es, tw); break;
+            case 2: stage<T, DIR, 2, 1, NT>(a, b, L, Ns, lg, es, tw); break;
+            case 3: stage<T, DIR, 3, 1, NT>(a, b, L, Ns, lg, es, tw); break;
+            case 4: stage<T, DIR, 4, 1, NT>(a, b, L, Ns, lg, es, tw); break;
+            case 5: stage<T, DIR, 5, 1, NT>(a, b, L, Ns, lg, es, tw); break;
+            case 7: stage<T, DIR, 7, 1, NT>(a, b, L, Ns, lg, es, tw); break;
+            case 8: stage<T, DIR, 8, 1, NT>(a, b, L, Ns, lg, es, tw); break;
             default:
-                if constexpr (sizeof(T) == 4) stage_composite<T, DIR>(R, a, b, L, Ns, lg, es, tw);
+                if constexpr (sizeof(T) == 4) stage_composite<T, DIR, NT>(R, a, b, L, Ns, lg, es, tw);
                 break;
         }
         C<T>* t = a;
@@ -337,9 +337,9 @@ template <typename T> __device__ __forceinline__ C<T>* smem_c() {
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
 // copies the twiddles exp(-2 pi i t / L), t < L, into shared memory
-template <typename T>
+template <typename T, int NT>
 __device__ __forceinline__ void load_twiddles(C<T>* dst, const C<T>* __restrict__ src, int L) {
-    for (int t = threadIdx.x; t < L; t += kFftThreads) dst[t] = src[t];
+    for (int t = threadIdx.x; t < L; t += NT) dst[t] = src[t];
 }
 
 // Correctly rounded conversion of a fixed-point cell mass q * 2^-F to T without
@@ -379,27 +379,27 @@ template <> __device__ __forceinline__ float fixed_to_real<float>(long long q, i
 
 // ---- xf: GMF rows -> half spectra along x ----------------------------------
 // smem: A, B (M0 x (np+1) each, element-major, padded), twiddles (M0)
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xf(const GridDev* __restrict__ grids,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_xf(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
                                                     const int64_t* const* __restrict__ gmf,
                                                     const C<T>* __restrict__ tw_arena,
                                                     C<T>* __restrict__ wsA, int F) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
-    const int M0 = g.M[0], G0 = g.G[0], Hx = g.Hx, np = g.np_x, lg = ilog2(np), es = np + 1;
+    const int M0 = g.M[0], G0 = g.G[0], Hx = g.Hx, np = g.lines[kPassXf], lg = ilog2(np), es = np + 1;
     C<T>* s = smem_c<T>();
     C<T>* s2 = s + M0 * es;
     C<T>* tw = s2 + M0 * es;
     const long long nrows = (long long)g.G[1] * g.G[2];
     const long long r_first = 2LL * ch.tile * np;
     const int64_t* __restrict__ in = gmf[ch.grid];
-    load_twiddles<T>(tw, tw_arena + g.fx.tw_off, M0);
+    load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
     // rows r0 = 2p, r1 = 2p + 1 packed as one complex line p; x fastest over threads
     {
         int p = 0, x = threadIdx.x;
         while (x >= M0) { x -= M0; ++p; }
-        const int dp = kFftThreads / M0, dx = kFftThreads % M0;
+        const int dp = NT / M0, dx = NT % M0;
         for (; p < np; ) {
             long long r0 = r_first + 2 * p, r1 = r0 + 1;
             T a = 0, b = 0;
@@ -414,13 +414,13 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xf(const Gri
         }
     }
     __syncthreads();
-    s = fft_lines<T, -1>(s, s2, g.fx, lg, es, tw);
+    s = fft_lines<T, -1, NT>(s, s2, g.fx, lg, es, tw);
     // separate the two real rows: A_k = (Z_k + conj Z_{M-k}) / 2, B_k = (Z_k - conj Z_{M-k}) / 2i
     C<T>* out = wsA + g.wsA;
     {
         int p = 0, k = threadIdx.x;
         while (k >= Hx) { k -= Hx; ++p; }
-        const int dp = kFftThreads / Hx, dk = kFftThreads % Hx;
+        const int dp = NT / Hx, dk = NT % Hx;
         for (; p < np; ) {
             long long r0 = r_first + 2 * p, r1 = r0 + 1;
             if (r0 < nrows) {
@@ -442,8 +442,8 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xf(const Gri
 //   z  (AX 2, MODE 1): in B[z][ky][kx] (z < G2), out A[zw][ky][kx]
 //   yi (AX 1, MODE 2): in A[zw][ky][kx],         out B[zw][yw][kx]
 // smem: A, B (L x tx each, element-major), twiddles (L)
-template <typename T, int AX, int MODE>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const GridDev* __restrict__ grids,
+template <typename T, int AX, int MODE, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_col(const GridDev* __restrict__ grids,
                                                      const Chunk* __restrict__ chunks,
                                                      const C<T>* __restrict__ tw_arena,
                                                      const T* __restrict__ tab,
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const Gr
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
     const int Hx = g.Hx;
-    const int tx = AX == 1 ? g.tx_y : g.tx_z;
+    const int tx = g.lines[AX == 2 ? kPassZ : (MODE == 0 ? kPassYf : kPassYi)];
     const int lg = ilog2(tx);
     const int nkt = (Hx + tx - 1) >> lg;
     const int other = ch.tile / nkt;    // z (yf), ky (z), zw (yi)
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const Gr
     C<T>* s = smem_c<T>();
     C<T>* s2 = s + L * tx;
     C<T>* tw = s2 + L * tx;
-    load_twiddles<T>(tw, tw_arena + pl.tw_off, L);
+    load_twiddles<T, NT>(tw, tw_arena + pl.tw_off, L);
 
     const C<T>* in;
     long long in_base, in_stride;
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const Gr
         in_base = (long long)other * M1 * Hx; in_stride = Hx;
     }
     const int line = threadIdx.x & (tx - 1);
-    const int istep = kFftThreads >> lg;
+    const int istep = NT >> lg;
     const int kx = kx0 + line;
     const bool live = kx < Hx;
     for (int i = threadIdx.x >> lg; i < L; i += istep) {
@@ -488,9 +488,9 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const Gr
     }
     __syncthreads();
     if (MODE == 2) {
-        s = fft_lines<T, 1>(s, s2, pl, lg, tx, tw);
+        s = fft_lines<T, 1, NT>(s, s2, pl, lg, tx, tw);
     } else {
-        s = fft_lines<T, -1>(s, s2, pl, lg, tx, tw);
+        s = fft_lines<T, -1, NT>(s, s2, pl, lg, tx, tw);
     }
     if (MODE == 1) {
         // phi-hat = T(kappa) rho-hat; the table is even in every component
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const Gr
             }
         }
         __syncthreads();
-        s = fft_lines<T, 1>(s, s2, pl, lg, tx, tw);
+        s = fft_lines<T, 1, NT>(s, s2, pl, lg, tx, tw);
     }
     // store
     C<T>* out;
@@ -538,27 +538,27 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_col(const Gr
 
 // ---- xi: half spectra -> real rows of the window -------------------------------
 // smem: A, B (M0 x (np+1) each), twiddles (M0)
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xi(const GridDev* __restrict__ grids,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_xi(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
                                                     const C<T>* __restrict__ tw_arena,
                                                     const C<T>* __restrict__ wsB,
                                                     void* const* __restrict__ phis) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
-    const int M0 = g.M[0], Hx = g.Hx, np = g.np_x, W0 = g.W[0], lg = ilog2(np), es = np + 1;
+    const int M0 = g.M[0], Hx = g.Hx, np = g.lines[kPassXi], W0 = g.W[0], lg = ilog2(np), es = np + 1;
     C<T>* s = smem_c<T>();
     C<T>* s2 = s + M0 * es;
     C<T>* tw = s2 + M0 * es;
     const long long nrows = (long long)g.W[1] * g.W[2];
     const long long r_first = 2LL * ch.tile * np;
     const C<T>* __restrict__ in = wsB + g.wsB;
-    load_twiddles<T>(tw, tw_arena + g.fx.tw_off, M0);
+    load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
     // Z_k = A_k + i B_k with A, B extended by Hermitian symmetry
     {
         int p = 0, k = threadIdx.x;
         while (k >= M0) { k -= M0; ++p; }
-        const int dp = kFftThreads / M0, dk = kFftThreads % M0;
+        const int dp = NT / M0, dk = NT % M0;
         for (; p < np; ) {
             long long r0 = r_first + 2 * p, r1 = r0 + 1;
             int kk = k < Hx ? k : M0 - k;
@@ -573,13 +573,13 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xi(const Gri
         }
     }
     __syncthreads();
-    s = fft_lines<T, 1>(s, s2, g.fx, lg, es, tw);
+    s = fft_lines<T, 1, NT>(s, s2, g.fx, lg, es, tw);
     const T norm = (T)(1.0 / ((double)g.M[0] * (double)g.M[1] * (double)g.M[2]));
     T* out = reinterpret_cast<T*>(phis[ch.grid]);
     {
         int p = 0, xw = threadIdx.x;
         while (xw >= W0) { xw -= W0; ++p; }
-        const int dp = kFftThreads / W0, dx = kFftThreads % W0;
+        const int dp = NT / W0, dx = NT % W0;
         for (; p < np; ) {
             long long r0 = r_first + 2 * p, r1 = r0 + 1;
             if (r0 < nrows) {
@@ -600,12 +600,14 @@ __global__ void __launch_bounds__(kFftThreads, MinCtas<T>::value) k_xi(const Gri
 // Allows every pass kernel up to 200 KB of dynamic shared memory (above the
 // 48 KB default).
 cudaError_t fft_configure() {
-    const int lim = 200 * 1024;
-    const void* fns[] = {(const void*)k_xf<float>, (const void*)k_col<float, 1, 0>,
-                         (const void*)k_col<float, 2, 1>, (const void*)k_col<float, 1, 2>,
-                         (const void*)k_xi<float>, (const void*)k_xf<double>,
-                         (const void*)k_col<double, 1, 0>, (const void*)k_col<double, 2, 1>,
-                         (const void*)k_col<double, 1, 2>, (const void*)k_xi<double>};
+    const int lim = kFftSmemLimit;
+    const void* fns[] = {
+#define APM_FNS(T, NT)                                                                          \
+    (const void*)k_xf<T, NT>, (const void*)k_col<T, 1, 0, NT>, (const void*)k_col<T, 2, 1, NT>, \
+        (const void*)k_col<T, 1, 2, NT>, (const void*)k_xi<T, NT>,
+        APM_FNS(float, 128) APM_FNS(float, 256) APM_FNS(double, 128) APM_FNS(double, 256)
+#undef APM_FNS
+    };
     for (const void* f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (e != cudaSuccess) return e;
@@ -613,43 +615,43 @@ cudaError_t fft_configure() {
     return cudaSuccess;
 }
 
+// The CTA size is a template parameter of the pass kernels (128 or 256 threads).
 template <typename T>
 cudaError_t launch_fft_xf(const FftArgs& a, const int64_t* const* gmf, cudaStream_t s) {
     if (a.n_chunks <= 0) return cudaSuccess;
-    k_xf<T><<<a.n_chunks, kFftThreads, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw,
-                                                    (C<T>*)a.wsA, a.F);
+    if (a.threads == 128)
+        k_xf<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F);
+    else
+        k_xf<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F);
+    return cudaGetLastError();
+}
+
+template <typename T, int AX, int MODE>
+cudaError_t launch_col(const FftArgs& a, cudaStream_t s) {
+    if (a.n_chunks <= 0) return cudaSuccess;
+    if (a.threads == 128)
+        k_col<T, AX, MODE, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
+                                                               (const T*)a.tab, (C<T>*)a.wsA, (C<T>*)a.wsB);
+    else
+        k_col<T, AX, MODE, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
+                                                               (const T*)a.tab, (C<T>*)a.wsA, (C<T>*)a.wsB);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_fft_yf(const FftArgs& a, cudaStream_t s) {
-    if (a.n_chunks <= 0) return cudaSuccess;
-    k_col<T, 1, 0><<<a.n_chunks, kFftThreads, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
-                                                           (const T*)a.tab, (C<T>*)a.wsA, (C<T>*)a.wsB);
-    return cudaGetLastError();
-}
-
+cudaError_t launch_fft_yf(const FftArgs& a, cudaStream_t s) { return launch_col<T, 1, 0>(a, s); }
 template <typename T>
-cudaError_t launch_fft_z(const FftArgs& a, cudaStream_t s) {
-    if (a.n_chunks <= 0) return cudaSuccess;
-    k_col<T, 2, 1><<<a.n_chunks, kFftThreads, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
-                                                           (const T*)a.tab, (C<T>*)a.wsA, (C<T>*)a.wsB);
-    return cudaGetLastError();
-}
-
+cudaError_t launch_fft_z(const FftArgs& a, cudaStream_t s) { return launch_col<T, 2, 1>(a, s); }
 template <typename T>
-cudaError_t launch_fft_yi(const FftArgs& a, cudaStream_t s) {
-    if (a.n_chunks <= 0) return cudaSuccess;
-    k_col<T, 1, 2><<<a.n_chunks, kFftThreads, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
-                                                           (const T*)a.tab, (C<T>*)a.wsA, (C<T>*)a.wsB);
-    return cudaGetLastError();
-}
+cudaError_t launch_fft_yi(const FftArgs& a, cudaStream_t s) { return launch_col<T, 1, 2>(a, s); }
 
 template <typename T>
 cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s) {
     if (a.n_chunks <= 0) return cudaSuccess;
-    k_xi<T><<<a.n_chunks, kFftThreads, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
-                                                    (const C<T>*)a.wsB, phis);
+    if (a.threads == 128)
+        k_xi<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis);
+    else
+        k_xi<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis);
     return cudaGetLastError();
 }
 

@@ -3,11 +3,13 @@ memory and torch streams.  Every step of the solve runs in the library's CUDA
 kernels; this module only marshals pointers and allocates output buffers.
 """
 import ctypes
+import json
+import os
 
 import torch
 
 from . import _lib
-from ._lib import ApmConfig, ApmGrid, ApmGridInfo, ApmParticles, check, lib, ptr_array
+from ._lib import ApmConfig, ApmFftShapes, ApmGrid, ApmGridInfo, ApmParticles, check, lib, ptr_array
 
 PARTICLE_KEYS = ("x", "y", "z", "vx", "vy", "vz", "m")
 
@@ -130,6 +132,56 @@ class Solver:
                                     ptr_array([_ptr(t) for t in phis]), _stream_handle(stream)),
               "apm_solve_level")
 
+    def autotune_level(self, level, gmf, phis, stream=None):
+        """apm_solve_level that also picks the fastest launch shape of each FFT pass."""
+        check(lib().apm_autotune_level(self._ctx, level, ptr_array([_ptr(t) for t in gmf]),
+                                       ptr_array([_ptr(t) for t in phis]), _stream_handle(stream)),
+              "apm_autotune_level")
+
+    def fft_shapes(self, level):
+        sh = ApmFftShapes()
+        check(lib().apm_get_fft_shapes(self._ctx, level, ctypes.byref(sh)), "apm_get_fft_shapes")
+        return {"budget": list(sh.budget), "threads": list(sh.threads)}
+
+    def set_fft_shapes(self, level, shapes):
+        sh = ApmFftShapes()
+        for i in range(5):
+            sh.budget[i] = int(shapes["budget"][i])
+            sh.threads[i] = int(shapes["threads"][i])
+        check(lib().apm_set_fft_shapes(self._ctx, level, ctypes.byref(sh)), "apm_set_fft_shapes")
+
+    def shape_key(self, level):
+        """Autotuner cache key of a level: GPU name, precision and every grid's
+        FFT lengths, GMF box and window (what the pass shapes depend on)."""
+        grids = sorted((tuple(self.info[i]["fft"]), tuple(self.info[i]["gmf"]),
+                        tuple(self.info[i]["phi_short"])) for i in self.level_grids[level])
+        return json.dumps([torch.cuda.get_device_name(self.device), self.precision, grids])
+
+    def autotune(self, particles, half_dt, bufs, gas=None, levels=None, cache=None, stream=None):
+        """Picks the FFT pass shapes of every level: from the JSON file `cache`
+        when it holds this GPU, precision and level shape; otherwise by one step
+        whose solves run the library's autotuner (apm_autotune_level), after
+        which the file is updated.  Returns {level: shapes}."""
+        levs = list(range(self.n_levels) if levels is None else levels)
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        keys = {lev: self.shape_key(lev) for lev in levs}
+        if all(k in table for k in keys.values()):
+            for lev in levs:
+                self.set_fft_shapes(lev, table[keys[lev]])
+        else:
+            self.step(particles, half_dt, bufs, None, gas=gas, levels=levels, stream=stream, tune=True)
+            for lev in levs:
+                table[keys[lev]] = self.fft_shapes(lev)
+            if cache:
+                tmp = cache + ".tmp"
+                with open(tmp, "w") as f:
+                    json.dump(table, f, indent=1)
+                os.replace(tmp, cache)
+        return {lev: self.fft_shapes(lev) for lev in levs}
+
     def accel(self, level, phis, phi, acc, parent_phi=None, parent_acc=None, stream=None):
         pp = None if parent_phi is None else ptr_array([_ptr(t) for t in parent_phi])
         pa = None if parent_acc is None else ptr_array([_ptr(t) for t in parent_acc])
@@ -162,11 +214,13 @@ class Solver:
         check(lib().apm_sync_status(self._ctx, _stream_handle(stream)), "apm_sync_status")
 
     # ------------------------------------------------------------------ one solve
-    def step(self, particles, half_dt, bufs, pacc, gas=None, levels=None, stream=None):
+    def step(self, particles, half_dt, bufs, pacc, gas=None, levels=None, stream=None, tune=False):
         """One APM solve over the hierarchy (Sec. 2, 2.2), levels top-down:
         deposit -> solve -> accel per level, then interpolation on every level.
-        bufs: from alloc_all(); pacc: (3, n) tensor of the context precision;
-        gas: None or a list with one device density tensor (or None) per grid."""
+        bufs: from alloc_all(); pacc: (3, n) tensor of the context precision, or
+        None to stop after the cell accelerations; gas: None or a list with one
+        device density tensor (or None) per grid; tune: solve through the
+        autotuner."""
         P = particles if isinstance(particles, Particles) else Particles(particles)
         levs = range(self.n_levels) if levels is None else levels
         for lev in levs:
@@ -181,11 +235,16 @@ class Solver:
             if g is not None and all(t is None for t in g):
                 g = None
             self.deposit(lev, P, half_dt, b["gmf"], g, pg, stream)
-            self.solve_level(lev, b["gmf"], b["phis"], stream)
+            if tune:
+                self.autotune_level(lev, b["gmf"], b["phis"], stream)
+            else:
+                self.solve_level(lev, b["gmf"], b["phis"], stream)
             if lev > 0 and (levels is None or (lev - 1) in levs):
                 self.accel(lev, b["phis"], b["phi"], b["acc"], bufs[lev - 1]["phi"],
                            bufs[lev - 1]["acc"], stream)
             else:
                 self.accel(lev, b["phis"], b["phi"], b["acc"], stream=stream)
+        if pacc is None:
+            return
         for lev in levs:
             self.interp(lev, bufs[lev]["acc"], P, half_dt, pacc, stream)

@@ -1,0 +1,107 @@
+"""The FFT pass autotuner (apm_autotune_level) and the launch shapes it picks
+(apm_get_fft_shapes / apm_set_fft_shapes).  A shape regroups whole lines per
+CTA and sets the CTA size; it must never change a result, bit for bit, and the
+tuned solve must leave the same potential as the plain one."""
+import json
+
+import numpy as np
+import pytest
+
+import apm_inputs as W
+from apm_inputs import GridDesc
+
+pytestmark = pytest.mark.gpu
+
+# uneven grids in one level: several FFT lengths per pass
+GRIDS = [GridDesc(0, -1, (0, 0, 0), (48, 48, 48)),
+         GridDesc(1, 0, (10, 12, 14), (25, 29, 43)),
+         GridDesc(1, 0, (10, 44, 62), (55, 26, 16)),
+         GridDesc(1, 0, (66, 10, 10), (24, 24, 24))]
+
+
+def _setup(precision):
+    import torch
+
+    from paper_1410_0010_gb300.solver import Particles, Solver
+    rng = np.random.default_rng(31)
+    n = 3000
+    pos = 0.1 + 0.8 * rng.random((3, n))
+    v = rng.normal(scale=0.1, size=(3, n))
+    dev = torch.device("cuda", 0)
+    parts = dict(x=pos[0], y=pos[1], z=pos[2], vx=v[0], vy=v[1], vz=v[2], m=0.5 + rng.random(n))
+    P = Particles({k: torch.as_tensor(np.ascontiguousarray(a), device=dev) for k, a in parts.items()})
+    s = Solver(GRIDS, periodic=False, precision=precision, device=0)
+    return s, P
+
+
+def _fields(bufs):
+    return [[t.clone() for t in b["phis"]] + [t.clone() for t in b["acc"]] for b in bufs]
+
+
+def _same(a, b):
+    import torch
+    return all(torch.equal(x, y) for la, lb in zip(a, b) for x, y in zip(la, lb))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_tuned_and_forced_shapes_give_identical_bits(precision):
+    import torch
+    s, P = _setup(precision)
+    bufs = s.alloc_all()
+    pacc = torch.zeros((3, P.n), dtype=s.dtype, device="cuda")
+    s.step(P, 1e-3, bufs, pacc)
+    ref = _fields(bufs)
+    ref_pacc = pacc.clone()
+    default = s.fft_shapes(1)
+    assert default["threads"] == [256] * 5
+    # the tuned solve
+    for b in bufs:
+        for t in b["phis"]:
+            t.fill_(float("nan"))
+    s.step(P, 1e-3, bufs, None, tune=True)
+    assert _same(_fields(bufs), ref)
+    tuned = [s.fft_shapes(lev) for lev in range(s.n_levels)]
+    for sh in tuned:
+        assert all(t in (128, 256) for t in sh["threads"])
+    # forced extreme shapes: one line per CTA batch and the largest budget
+    for budget, threads in ((1, 128), (8192, 128), (100000, 256)):
+        for lev in range(s.n_levels):
+            s.set_fft_shapes(lev, {"budget": [budget] * 5, "threads": [threads] * 5})
+        s.step(P, 1e-3, bufs, pacc)
+        assert _same(_fields(bufs), ref), (budget, threads)
+        assert torch.equal(pacc, ref_pacc)
+    s.close()
+
+
+def test_shape_validation_and_roundtrip():
+    from paper_1410_0010_gb300._lib import ApmError
+    s, _ = _setup("fp32")
+    sh = {"budget": [512, 1024, 2048, 4096, 8192], "threads": [128, 256, 128, 256, 128]}
+    s.set_fft_shapes(1, sh)
+    assert s.fft_shapes(1) == sh
+    for bad in ({"budget": [0] * 5, "threads": [256] * 5},
+                {"budget": [2048] * 5, "threads": [48] * 5},
+                {"budget": [2048] * 5, "threads": [512] * 5},
+                {"budget": [2048] * 5, "threads": [64] * 5}):
+        with pytest.raises(ApmError):
+            s.set_fft_shapes(1, bad)
+    assert s.fft_shapes(1) == sh
+    s.close()
+
+
+def test_cache_file_roundtrip(tmp_path):
+    s, P = _setup("fp32")
+    bufs = s.alloc_all()
+    cache = str(tmp_path / "shapes.json")
+    first = s.autotune(P, 1e-3, bufs, cache=cache)
+    table = json.load(open(cache))
+    assert len(table) == s.n_levels
+    s.close()
+    # a second context on the same shapes reads them back without tuning
+    s2, P2 = _setup("fp32")
+    bufs2 = s2.alloc_all()
+    for lev in range(s2.n_levels):
+        s2.set_fft_shapes(lev, {"budget": [2048] * 5, "threads": [256] * 5})
+    again = s2.autotune(P2, 1e-3, bufs2, cache=cache)
+    assert again == first
+    s2.close()
