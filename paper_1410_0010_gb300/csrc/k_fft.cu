@@ -342,39 +342,23 @@ __device__ __forceinline__ void load_twiddles(C<T>* dst, const C<T>* __restrict_
     for (int t = threadIdx.x; t < L; t += NT) dst[t] = src[t];
 }
 
-// Correctly rounded conversion of a fixed-point cell mass q * 2^-F to T without
-// the FP64 pipe for T = float: the leading 24 significant bits are rounded to
-// nearest-even with integer operations, then scaled by 2^-F (exact).  Same value
-// as the FP64 conversion (double)q * 2^-F rounded to float whenever |q| < 2^53.
-template <typename T> __device__ __forceinline__ T fixed_to_real(long long q, int F);
-template <> __device__ __forceinline__ double fixed_to_real<double>(long long q, int F) {
-    return ldexp((double)q, -F);
+// Correctly rounded conversion of a fixed-point cell mass q * 2^-F to T:
+// q rounded to nearest-even in T (the hardware int64 conversion), then scaled
+// by scale = 2^-F, which is exact.  For T = float this equals the FP64
+// conversion (double)q * 2^-F rounded to float whenever |q| < 2^53.
+template <typename T> __device__ __forceinline__ T fixed_to_real(long long q, T scale);
+template <> __device__ __forceinline__ double fixed_to_real<double>(long long q, double scale) {
+    return __ll2double_rn(q) * scale;
 }
-template <> __device__ __forceinline__ float fixed_to_real<float>(long long q, int F) {
-    if (q == 0) return 0.0f;
-    const bool neg = q < 0;
-    unsigned long long a = neg ? (unsigned long long)(-q) : (unsigned long long)q;
-    const int msb = 63 - __clzll((long long)a);     // position of the leading bit
-    int e = msb;                                     // value = a * 2^-F, a in [2^msb, 2^(msb+1))
-    unsigned m;                                      // 24-bit significand
-    if (msb <= 23) {
-        m = (unsigned)(a << (23 - msb));
-    } else {
-        const int sh = msb - 23;
-        unsigned long long keep = a >> sh;
-        unsigned long long rem = a & ((1ULL << sh) - 1);
-        unsigned long long half = 1ULL << (sh - 1);
-        if (rem > half || (rem == half && (keep & 1))) ++keep;
-        if (keep >> 24) {   // rounding carried into a new bit
-            keep >>= 1;
-            ++e;
-        }
-        m = (unsigned)keep;
-    }
-    // float with significand m / 2^23 and exponent e, then times 2^-F
-    float f = __int_as_float(((e + 127) << 23) | (m & 0x7FFFFF));
-    f = ldexpf(f, -F);
-    return neg ? -f : f;
+template <> __device__ __forceinline__ float fixed_to_real<float>(long long q, float scale) {
+    return __ll2float_rn(q) * scale;
+}
+
+// 2^-F in T, 1 <= F <= 62
+template <typename T> __device__ __forceinline__ T pow2_neg(int F);
+template <> __device__ __forceinline__ float pow2_neg<float>(int F) { return __int_as_float((127 - F) << 23); }
+template <> __device__ __forceinline__ double pow2_neg<double>(int F) {
+    return __longlong_as_double((long long)(1023 - F) << 52);
 }
 
 // ---- xf: GMF rows -> half spectra along x ----------------------------------
@@ -395,6 +379,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     const long long r_first = 2LL * ch.tile * np;
     const int64_t* __restrict__ in = gmf[ch.grid];
     load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
+    const T scale = pow2_neg<T>(F);
     // rows r0 = 2p, r1 = 2p + 1 packed as one complex line p; x fastest over threads
     {
         int p = 0, x = threadIdx.x;
@@ -404,8 +389,8 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
             long long r0 = r_first + 2 * p, r1 = r0 + 1;
             T a = 0, b = 0;
             if (x < G0) {
-                if (r0 < nrows) a = fixed_to_real<T>(in[r0 * G0 + x], F);
-                if (r1 < nrows) b = fixed_to_real<T>(in[r1 * G0 + x], F);
+                if (r0 < nrows) a = fixed_to_real<T>(in[r0 * G0 + x], scale);
+                if (r1 < nrows) b = fixed_to_real<T>(in[r1 * G0 + x], scale);
             }
             s[x * es + p] = mk<T>(a, b);
             x += dx;
