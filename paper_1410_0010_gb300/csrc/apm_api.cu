@@ -266,16 +266,17 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
         while (lines > 1 && fft_pass_smem(q, len, lines, csz) > (size_t)kFftSmemLimit) lines /= 2;
         P.lines[k] = lines;
         P.smem = std::max(P.smem, fft_pass_smem(q, len, lines, csz));
-        const long long kt = (g.Hx + lines - 1) / lines;     // kx tiles of the y / z passes
-        long long n = 0;
-        switch (q) {
-            case kPassXf: n = (((long long)g.G[1] * g.G[2] + 1) / 2 + lines - 1) / lines; break;
-            case kPassXi: n = (((long long)g.W[1] * g.W[2] + 1) / 2 + lines - 1) / lines; break;
-            case kPassYf: n = kt * g.G[2]; break;
-            case kPassZ: n = kt * g.M[1]; break;
-            default: n = kt * g.W[2]; break;
+        if (q == kPassXf || q == kPassXi) {
+            const long long rows = q == kPassXf ? (long long)g.G[1] * g.G[2] : (long long)g.W[1] * g.W[2];
+            const long long n = ((rows + 1) / 2 + lines - 1) / lines;
+            for (long long t = 0; t < n; ++t) list.push_back({k, (int)t});
+        } else {
+            // (kx tile, z | ky | zw) pairs, encoded as (kt << kColOtherBits) | other
+            const int nkt = (g.Hx + lines - 1) / lines;
+            const int n_other = q == kPassYf ? g.G[2] : (q == kPassZ ? g.M[1] : g.W[2]);
+            for (int o = 0; o < n_other; ++o)
+                for (int kt = 0; kt < nkt; ++kt) list.push_back({k, (kt << kColOtherBits) | o});
         }
-        for (long long t = 0; t < n; ++t) list.push_back({k, (int)t});
     }
     P.budget = budget;
     P.threads = threads;

@@ -61,6 +61,12 @@ struct FftPlan1D {
     int nst;
     int tw_off;                       // offset of exp(-2 pi i t/L), t < L, in the twiddle arenas
     unsigned char radix[kMaxStages];
+    // per stage: Ns (product of the radices before it), the twiddle stride
+    // L / (Ns R), and ceil(2^32 / Ns) for exact division of small integers
+    // (n < 2^21) by Ns as __umulhi(n, magic) (Ns = 1: magic 0, q = n)
+    unsigned short ns[kMaxStages];
+    unsigned short step[kMaxStages];
+    unsigned magic[kMaxStages];
 };
 
 // Stage radices of a length-L transform: greedily the largest allowed radix
@@ -86,8 +92,19 @@ inline bool fft_plan(int L, int max_radix, FftPlan1D* pl) {
         pl->radix[pl->nst++] = (unsigned char)pick;
         n /= pick;
     }
+    int Ns = 1;
+    for (int st = 0; st < pl->nst; ++st) {
+        pl->ns[st] = (unsigned short)Ns;
+        pl->step[st] = (unsigned short)(L / (Ns * pl->radix[st]));
+        pl->magic[st] = Ns == 1 ? 0u : (unsigned)((0x100000000ULL + Ns - 1) / Ns);
+        Ns *= pl->radix[st];
+    }
     return true;
 }
+
+// Column-pass chunks carry (kx tile, line index of the other axis) as
+// (kt << 20) | other: other < 2^20, kt < 2^11.
+constexpr int kColOtherBits = 20;
 
 // Everything a kernel needs to know about one grid.
 struct GridDev {

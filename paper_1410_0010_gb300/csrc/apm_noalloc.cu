@@ -31,15 +31,21 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 // writes the descriptor, the pointer tables of the passes and a chunk list
 // {grid 0, tile i} into the scratch
-__global__ void k_noalloc_setup(GridDev g, GridDev* dst, Chunk* chunks, int n, const int64_t** in_tab,
-                                const int64_t* in, void** out_tab, void* out) {
+// row chunks {0, i}; column chunks {0, (kt << kColOtherBits) | other} for
+// i = other * nkt + kt
+__global__ void k_noalloc_setup(GridDev g, GridDev* dst, Chunk* chunks, Chunk* cchunks, int n, int nkt,
+                                const int64_t** in_tab, const int64_t* in, void** out_tab, void* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *dst = g;
         *in_tab = in;
         *out_tab = out;
     }
-    if (i < n) chunks[i] = Chunk{0, i};
+    if (i < n) {
+        chunks[i] = Chunk{0, i};
+        const int other = i / nkt, kt = i - other * nkt;
+        cchunks[i] = Chunk{0, (kt << kColOtherBits) | other};
+    }
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -105,6 +111,8 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     off = align256(off + sizeof(GridDev));
     Chunk* d_chunks = reinterpret_cast<Chunk*>(base + off);
     off = align256(off + kMaxChunks * sizeof(Chunk));
+    Chunk* d_cchunks = reinterpret_cast<Chunk*>(base + off);
+    off = align256(off + kMaxChunks * sizeof(Chunk));
     double2* tw64 = reinterpret_cast<double2*>(base + off);
     off = align256(off + n * sizeof(double2));
     float2* tw32 = reinterpret_cast<float2*>(base + off);
@@ -139,8 +147,8 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     void** d_out = reinterpret_cast<void**>(d_chunks + (kMaxChunks - 1));
 
     // every call rebuilds what it reads: nothing depends on the previous call
-    k_noalloc_setup<<<(n_max + 255) / 256, 256, 0, s>>>(g, d_g, d_chunks, n_max, d_in, gmf, d_out,
-                                                        phi_short);
+    k_noalloc_setup<<<(n_max + 255) / 256, 256, 0, s>>>(g, d_g, d_chunks, d_cchunks, n_max, nky, d_in, gmf,
+                                                        d_out, phi_short);
     if (cudaGetLastError() != cudaSuccess) return APM_E_CUDA;
     if (launch_twiddles(tw64, tw32, n, s) != cudaSuccess) return APM_E_CUDA;
     const int M[3] = {n, n, n};
@@ -162,6 +170,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     a.n_chunks = n_xf;
     a.smem = smem_rows;
     if (launch_fft_xf<float>(a, d_in, s) != cudaSuccess) return APM_E_CUDA;
+    a.chunks = d_cchunks;
     a.n_chunks = n_yf;
     a.smem = smem_cols;
     if (launch_fft_yf<float>(a, s) != cudaSuccess) return APM_E_CUDA;
@@ -169,6 +178,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     if (launch_fft_z<float>(a, s) != cudaSuccess) return APM_E_CUDA;
     a.n_chunks = n_yi;
     if (launch_fft_yi<float>(a, s) != cudaSuccess) return APM_E_CUDA;
+    a.chunks = d_chunks;
     a.n_chunks = n_xi;
     a.smem = smem_rows;
     if (launch_fft_xi<float>(a, d_out, s) != cudaSuccess) return APM_E_CUDA;

@@ -248,19 +248,23 @@ struct DftC {
 // exp(DIR 2 pi i (j mod Ns) r / (Ns R)), and writes elements
 // (j / Ns) Ns R + (j mod Ns) + r Ns: natural order after the last stage.
 // Thread t owns line t mod nl and butterflies j = t / nl + m (threads / nl);
-// j / Ns and j mod Ns are stepped incrementally.
+// j / Ns and j mod Ns are stepped incrementally (the first ones by a
+// multiply-high with magic = ceil(2^32 / Ns), exact for j < 2^21).
+__device__ __forceinline__ int div_small(int n, int d, unsigned magic) {
+    return d == 1 ? n : (int)__umulhi((unsigned)n, magic);
+}
+
 template <typename T, int DIR, int R1, int R2, int NT>
-__device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int L, int Ns, int lg,
-                      int es, const C<T>* __restrict__ tw) {
+__device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int L, int Ns, int step,
+                      unsigned magic, int lg, int es, const C<T>* __restrict__ tw) {
     constexpr int R = R1 * R2;
     const int nb = L / R;
     const int line = threadIdx.x & ((1 << lg) - 1);
     const int jstep = NT >> lg;
     int j = threadIdx.x >> lg;
     if (j < nb) {
-        const int step = L / (Ns * R);
-        int jm = j % Ns, k = j / Ns;
-        const int djm = jstep % Ns, dk = jstep / Ns;
+        int k = div_small(j, Ns, magic), jm = j - k * Ns;
+        const int dk = div_small(jstep, Ns, magic), djm = jstep - dk * Ns;
         for (; j < nb; j += jstep) {
             C<T> v[R];
 #pragma unroll
@@ -287,16 +291,16 @@ __device__ void stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst, int 
 
 // composite stage radices (FP32 plans only)
 template <typename T, int DIR, int NT>
-__device__ __forceinline__ void stage_composite(int R, const C<T>* a, C<T>* b, int L, int Ns, int lg,
-                                                int es, const C<T>* tw) {
+__device__ __forceinline__ void stage_composite(int R, const C<T>* a, C<T>* b, int L, int Ns, int step,
+                                                unsigned magic, int lg, int es, const C<T>* tw) {
     switch (R) {
-        case 6: stage<T, DIR, 3, 2, NT>(a, b, L, Ns, lg, es, tw); break;
-        case 9: stage<T, DIR, 3, 3, NT>(a, b, L, Ns, lg, es, tw); break;
-        case 10: stage<T, DIR, 5, 2, NT>(a, b, L, Ns, lg, es, tw); break;
-        case 12: stage<T, DIR, 3, 4, NT>(a, b, L, Ns, lg, es, tw); break;
-        case 14: stage<T, DIR, 7, 2, NT>(a, b, L, Ns, lg, es, tw); break;
-        case 15: stage<T, DIR, 5, 3, NT>(a, b, L, Ns, lg, es, tw); break;
-        default: stage<T, DIR, 4, 4, NT>(a, b, L, Ns, lg, es, tw); break;   // 16
+        case 6: stage<T, DIR, 3, 2, NT>(a, b, L, Ns, step, magic, lg, es, tw); break;
+        case 9: stage<T, DIR, 3, 3, NT>(a, b, L, Ns, step, magic, lg, es, tw); break;
+        case 10: stage<T, DIR, 5, 2, NT>(a, b, L, Ns, step, magic, lg, es, tw); break;
+        case 12: stage<T, DIR, 3, 4, NT>(a, b, L, Ns, step, magic, lg, es, tw); break;
+        case 14: stage<T, DIR, 7, 2, NT>(a, b, L, Ns, step, magic, lg, es, tw); break;
+        case 15: stage<T, DIR, 5, 3, NT>(a, b, L, Ns, step, magic, lg, es, tw); break;
+        default: stage<T, DIR, 4, 4, NT>(a, b, L, Ns, step, magic, lg, es, tw); break;   // 16
     }
 }
 
@@ -307,24 +311,23 @@ __device__ __forceinline__ void stage_composite(int R, const C<T>* a, C<T>* b, i
 template <typename T, int DIR, int NT>
 __device__ C<T>* fft_lines(C<T>* a, C<T>* b, const FftPlan1D& pl, int lg, int es, const C<T>* tw) {
     const int L = pl.L;
-    int Ns = 1;
     for (int st = 0; st < pl.nst; ++st) {
-        const int R = pl.radix[st];
+        const int R = pl.radix[st], Ns = pl.ns[st], step = pl.step[st];
+        const unsigned mg = pl.magic[st];
         switch (R) {
-            case 2: stage<T, DIR, 2, 1, NT>(a, b, L, Ns, lg, es, tw); break;
-            case 3: stage<T, DIR, 3, 1, NT>(a, b, L, Ns, lg, es, tw); break;
-            case 4: stage<T, DIR, 4, 1, NT>(a, b, L, Ns, lg, es, tw); break;
-            case 5: stage<T, DIR, 5, 1, NT>(a, b, L, Ns, lg, es, tw); break;
-            case 7: stage<T, DIR, 7, 1, NT>(a, b, L, Ns, lg, es, tw); break;
-            case 8: stage<T, DIR, 8, 1, NT>(a, b, L, Ns, lg, es, tw); break;
+            case 2: stage<T, DIR, 2, 1, NT>(a, b, L, Ns, step, mg, lg, es, tw); break;
+            case 3: stage<T, DIR, 3, 1, NT>(a, b, L, Ns, step, mg, lg, es, tw); break;
+            case 4: stage<T, DIR, 4, 1, NT>(a, b, L, Ns, step, mg, lg, es, tw); break;
+            case 5: stage<T, DIR, 5, 1, NT>(a, b, L, Ns, step, mg, lg, es, tw); break;
+            case 7: stage<T, DIR, 7, 1, NT>(a, b, L, Ns, step, mg, lg, es, tw); break;
+            case 8: stage<T, DIR, 8, 1, NT>(a, b, L, Ns, step, mg, lg, es, tw); break;
             default:
-                if constexpr (sizeof(T) == 4) stage_composite<T, DIR, NT>(R, a, b, L, Ns, lg, es, tw);
+                if constexpr (sizeof(T) == 4) stage_composite<T, DIR, NT>(R, a, b, L, Ns, step, mg, lg, es, tw);
                 break;
         }
         C<T>* t = a;
         a = b;
         b = t;
-        Ns *= R;
     }
     return a;
 }
@@ -438,9 +441,8 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     const int Hx = g.Hx;
     const int tx = g.lines[AX == 2 ? kPassZ : (MODE == 0 ? kPassYf : kPassYi)];
     const int lg = ilog2(tx);
-    const int nkt = (Hx + tx - 1) >> lg;
-    const int other = ch.tile / nkt;    // z (yf), ky (z), zw (yi)
-    const int kx0 = (ch.tile - other * nkt) << lg;
+    const int other = ch.tile & ((1 << kColOtherBits) - 1);    // z (yf), ky (z), zw (yi)
+    const int kx0 = (ch.tile >> kColOtherBits) << lg;
     const FftPlan1D& pl = AX == 1 ? g.fy : g.fz;
     const int L = pl.L;
     const int M1 = g.M[1];
@@ -466,10 +468,18 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     const int istep = NT >> lg;
     const int kx = kx0 + line;
     const bool live = kx < Hx;
-    for (int i = threadIdx.x >> lg; i < L; i += istep) {
-        C<T> v = mk<T>(0, 0);
-        if (i < n_in && live) v = in[in_base + i * in_stride + kx];
-        s[i * tx + line] = v;
+    {
+        // element i of this thread's line from in[in_base + i in_stride + kx];
+        // elements [n_in, L) are the zero padding
+        int i = threadIdx.x >> lg;
+        C<T>* sp = s + i * tx + line;
+        const int sstep = istep * tx;
+        if (live) {
+            const C<T>* __restrict__ ip = in + (in_base + (long long)i * in_stride + kx);
+            const long long istride = (long long)istep * in_stride;
+            for (; i < n_in; i += istep, ip += istride, sp += sstep) *sp = *ip;
+        }
+        for (; i < L; i += istep, sp += sstep) *sp = mk<T>(0, 0);
     }
     __syncthreads();
     if (MODE == 2) {
@@ -482,12 +492,12 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
         s2 = (s == smem_c<T>()) ? s + L * tx : smem_c<T>();
         const int ky = other;
         const int fy = ky <= M1 / 2 ? ky : M1 - ky;
-        const T* tb = tab + g.tab_off + (long long)fy * Hx;
-        const long long zst = (long long)g.Hy2 * Hx;
+        const T* __restrict__ tb = tab + (g.tab_off + (long long)fy * Hx + kx);
+        const int zst = g.Hy2 * Hx;     // the octant table holds < 2^31 entries
         if (live) {
             for (int kz = threadIdx.x >> lg; kz < L; kz += istep) {
-                int fz = kz <= L / 2 ? kz : L - kz;
-                T t = tb[fz * zst + kx];
+                const int fz = kz <= L / 2 ? kz : L - kz;
+                const T t = tb[fz * zst];
                 C<T> v = s[kz * tx + line];
                 s[kz * tx + line] = mk<T>(v.x * t, v.y * t);
             }
@@ -511,10 +521,13 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     }
     if (live) {
         int o = threadIdx.x >> lg;
-        int i = (s0 + o) % L;
-        const int di = istep % L;
-        for (; o < n_out; o += istep) {
-            out[out_base + o * out_stride + kx] = s[i * tx + line];
+        int i = s0 + o, di = istep;     // (s0 + o) mod L and istep mod L
+        while (i >= L) i -= L;
+        while (di >= L) di -= L;
+        C<T>* __restrict__ op = out + (out_base + (long long)o * out_stride + kx);
+        const long long ostride = (long long)istep * out_stride;
+        for (; o < n_out; o += istep, op += ostride) {
+            *op = s[i * tx + line];
             i += di;
             if (i >= L) i -= L;
         }
@@ -565,17 +578,27 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
         int p = 0, xw = threadIdx.x;
         while (xw >= W0) { xw -= W0; ++p; }
         const int dp = NT / W0, dx = NT % W0;
+        int x = g.s0[0] + xw;             // (s0 + xw) mod M0, stepped with xw
+        while (x >= M0) x -= M0;
+        int dxm = dx;
+        while (dxm >= M0) dxm -= M0;
         for (; p < np; ) {
             long long r0 = r_first + 2 * p, r1 = r0 + 1;
             if (r0 < nrows) {
-                int x = (g.s0[0] + xw) % M0;
                 C<T> z = s[x * es + p];
                 out[r0 * W0 + xw] = z.x * norm;
                 if (r1 < nrows) out[r1 * W0 + xw] = z.y * norm;
             }
             xw += dx;
             p += dp;
-            if (xw >= W0) { xw -= W0; ++p; }
+            x += dxm;
+            if (x >= M0) x -= M0;
+            if (xw >= W0) {
+                xw -= W0;
+                ++p;
+                x -= W0 % M0;
+                if (x < 0) x += M0;
+            }
         }
     }
 }
