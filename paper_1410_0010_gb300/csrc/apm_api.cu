@@ -596,6 +596,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             g.Hz2 = g.M[2] / 2 + 1;
             g.cells_gmf = (long long)g.G[0] * g.G[1] * g.G[2];
             g.inv2d = 0.5 / delta;
+            g.inv_m3 = 1.0 / ((double)g.M[0] * (double)g.M[1] * (double)g.M[2]);
             g.rows_gas = std::max(1, kChunkCells / g.G[0]);
             // 2x2x2 output blocks pair level cells (2k+1, 2k+2), the two children
             // between the same parent centres

@@ -133,6 +133,7 @@ struct GridDev {
     int acc_sh[3];       // 1 when output cell 0 is the second cell of its block, else 0
     int acc_nb[3];       // output blocks per axis
     double inv2d;        // 1 / (2 delta)
+    double inv_m3;       // 1 / (M0 M1 M2), the inverse transform's normalisation
 };
 
 // Threads of a CTA walking a batch of rows [r0, r1) of length n in row-major

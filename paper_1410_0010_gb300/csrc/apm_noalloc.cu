@@ -99,6 +99,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     g.delta = delta;
     g.parent = -1;
     g.cells_gmf = (long long)n * n * n;
+    g.inv_m3 = 1.0 / ((double)n * (double)n * (double)n);
     for (int q = 0; q < kFftPasses; ++q) g.lines[q] = fft_pass_lines(q, n, kFftBudgetF32, false);
     const long long Hx = g.Hx;
     const long long szA = (long long)(n + 4) * n * Hx;         // max(G1 G2, W2 M1) Hx

@@ -378,9 +378,10 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     C<T>* s = smem_c<T>();
     C<T>* s2 = s + M0 * es;
     C<T>* tw = s2 + M0 * es;
-    const long long nrows = (long long)g.G[1] * g.G[2];
+    // this CTA's rows: r_first + [0, nr), nr <= 2 np; 32-bit offsets from there
     const long long r_first = 2LL * ch.tile * np;
-    const int64_t* __restrict__ in = gmf[ch.grid];
+    const int nr = (int)min(2LL * np, (long long)g.G[1] * g.G[2] - r_first);
+    const int64_t* __restrict__ in = gmf[ch.grid] + r_first * G0;
     load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
     const T scale = pow2_neg<T>(F);
     // rows r0 = 2p, r1 = 2p + 1 packed as one complex line p; x fastest over threads
@@ -389,11 +390,11 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
         while (x >= M0) { x -= M0; ++p; }
         const int dp = NT / M0, dx = NT % M0;
         for (; p < np; ) {
-            long long r0 = r_first + 2 * p, r1 = r0 + 1;
+            const int q0 = 2 * p;
             T a = 0, b = 0;
             if (x < G0) {
-                if (r0 < nrows) a = fixed_to_real<T>(in[r0 * G0 + x], scale);
-                if (r1 < nrows) b = fixed_to_real<T>(in[r1 * G0 + x], scale);
+                if (q0 < nr) a = fixed_to_real<T>(in[q0 * G0 + x], scale);
+                if (q0 + 1 < nr) b = fixed_to_real<T>(in[(q0 + 1) * G0 + x], scale);
             }
             s[x * es + p] = mk<T>(a, b);
             x += dx;
@@ -404,18 +405,18 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     __syncthreads();
     s = fft_lines<T, -1, NT>(s, s2, g.fx, lg, es, tw);
     // separate the two real rows: A_k = (Z_k + conj Z_{M-k}) / 2, B_k = (Z_k - conj Z_{M-k}) / 2i
-    C<T>* out = wsA + g.wsA;
+    C<T>* out = wsA + (g.wsA + r_first * Hx);
     {
         int p = 0, k = threadIdx.x;
         while (k >= Hx) { k -= Hx; ++p; }
         const int dp = NT / Hx, dk = NT % Hx;
         for (; p < np; ) {
-            long long r0 = r_first + 2 * p, r1 = r0 + 1;
-            if (r0 < nrows) {
+            const int q0 = 2 * p;
+            if (q0 < nr) {
                 C<T> z = s[k * es + p];
                 C<T> zm = s[(k == 0 ? 0 : M0 - k) * es + p];
-                out[r0 * Hx + k] = mk<T>((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
-                if (r1 < nrows) out[r1 * Hx + k] = mk<T>((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
+                out[q0 * Hx + k] = mk<T>((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
+                if (q0 + 1 < nr) out[(q0 + 1) * Hx + k] = mk<T>((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
             }
             k += dk;
             p += dp;
@@ -548,9 +549,9 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     C<T>* s = smem_c<T>();
     C<T>* s2 = s + M0 * es;
     C<T>* tw = s2 + M0 * es;
-    const long long nrows = (long long)g.W[1] * g.W[2];
     const long long r_first = 2LL * ch.tile * np;
-    const C<T>* __restrict__ in = wsB + g.wsB;
+    const int nr = (int)min(2LL * np, (long long)g.W[1] * g.W[2] - r_first);
+    const C<T>* __restrict__ in = wsB + (g.wsB + r_first * Hx);
     load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
     // Z_k = A_k + i B_k with A, B extended by Hermitian symmetry
     {
@@ -558,11 +559,11 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
         while (k >= M0) { k -= M0; ++p; }
         const int dp = NT / M0, dk = NT % M0;
         for (; p < np; ) {
-            long long r0 = r_first + 2 * p, r1 = r0 + 1;
+            const int q0 = 2 * p;
             int kk = k < Hx ? k : M0 - k;
             C<T> a = mk<T>(0, 0), b = mk<T>(0, 0);
-            if (r0 < nrows) a = in[r0 * Hx + kk];
-            if (r1 < nrows) b = in[r1 * Hx + kk];
+            if (q0 < nr) a = in[q0 * Hx + kk];
+            if (q0 + 1 < nr) b = in[(q0 + 1) * Hx + kk];
             if (k >= Hx) { a.y = -a.y; b.y = -b.y; }
             s[k * es + p] = mk<T>(a.x - b.y, a.y + b.x);
             k += dk;
@@ -572,8 +573,8 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     }
     __syncthreads();
     s = fft_lines<T, 1, NT>(s, s2, g.fx, lg, es, tw);
-    const T norm = (T)(1.0 / ((double)g.M[0] * (double)g.M[1] * (double)g.M[2]));
-    T* out = reinterpret_cast<T*>(phis[ch.grid]);
+    const T norm = (T)g.inv_m3;
+    T* out = reinterpret_cast<T*>(phis[ch.grid]) + r_first * W0;
     {
         int p = 0, xw = threadIdx.x;
         while (xw >= W0) { xw -= W0; ++p; }
@@ -583,11 +584,11 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
         int dxm = dx;
         while (dxm >= M0) dxm -= M0;
         for (; p < np; ) {
-            long long r0 = r_first + 2 * p, r1 = r0 + 1;
-            if (r0 < nrows) {
+            const int q0 = 2 * p;
+            if (q0 < nr) {
                 C<T> z = s[x * es + p];
-                out[r0 * W0 + xw] = z.x * norm;
-                if (r1 < nrows) out[r1 * W0 + xw] = z.y * norm;
+                out[q0 * W0 + xw] = z.x * norm;
+                if (q0 + 1 < nr) out[(q0 + 1) * W0 + xw] = z.y * norm;
             }
             xw += dx;
             p += dp;
