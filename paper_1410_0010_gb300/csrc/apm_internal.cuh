@@ -288,6 +288,16 @@ __device__ __forceinline__ unsigned long long wmul63(unsigned long long a, unsig
     return (hi << 1) | (lo2 >> 63);
 }
 
+// wmul63 for a < 2^32: with b = bh 2^32 + bl, (a b + 2^62) >> 63 equals
+// (a bh + ((a bl) >> 32) + 2^30) >> 31 (the low 32 bits of a bl cannot carry
+// into the result); two 32 x 32 -> 64 products
+__device__ __forceinline__ unsigned long long wmul63_small(unsigned long long a, unsigned long long b) {
+    const unsigned a32 = (unsigned)a;
+    const unsigned long long hi = (unsigned long long)a32 * (unsigned)(b >> 32);
+    const unsigned long long lo = (unsigned long long)a32 * (unsigned)b;
+    return (hi + (lo >> 32) + (1ULL << 30)) >> 31;
+}
+
 struct Particles {
     long long n;
     const double *x, *y, *z, *vx, *vy, *vz, *m;

@@ -10,17 +10,12 @@
 namespace apm {
 namespace {
 
-__device__ __forceinline__ long long floor_div(long long a, long long b) {
-    long long q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-    return q;
-}
 
 // One CTA per batch of `rows` GMF rows (a row: G0 cells along x at fixed y, z).
 __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __restrict__ pgrids,
                            const double* const* __restrict__ gas,
                            const double* const* __restrict__ pgas, int64_t* const* __restrict__ gmf,
-                           const Chunk* __restrict__ chunks, int rows_per_cta, int F, int refine) {
+                           const Chunk* __restrict__ chunks, int rows_per_cta, int F) {
     const Chunk c = chunks[blockIdx.x];
     const GridDev& g = L.g[c.grid];
     const int G0 = g.G[0], G1 = g.G[1];
@@ -54,9 +49,10 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
         if (yz_in && cx >= 0 && cx < g.N[0]) {
             if (own) rho = own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)];
         } else if (par) {
-            long long px = floor_div(g.start[0] + cx, refine) - p->start[0];
-            long long py = floor_div(g.start[1] + cy, refine) - p->start[1];
-            long long pz = floor_div(g.start[2] + cz, refine) - p->start[2];
+            // parent cell floor(c / 2): the refinement factor is 2 (checked on the host)
+            long long px = ((g.start[0] + cx) >> 1) - p->start[0];
+            long long py = ((g.start[1] + cy) >> 1) - p->start[1];
+            long long pz = ((g.start[2] + cz) >> 1) - p->start[2];
             rho = par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
         }
         row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
@@ -66,12 +62,10 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
 
 // GMF-local index of one cloud cell per axis under the grid's edge rule
 // (mode 0 drop: -1 when outside, 1 fold, 2 wrap)
+// (on the periodic root the centre cell is in [0, G), so v is in [-1, G])
 __device__ __forceinline__ int edge_rule(long long v, int G, int mode) {
     if (mode == 1) return v < 0 ? 0 : (v >= G ? G - 1 : (int)v);
-    if (mode == 2) {
-        v %= G;
-        return (int)(v < 0 ? v + G : v);
-    }
+    if (mode == 2) return (int)(v < 0 ? v + G : (v >= G ? v - G : v));
     return (v < 0 || v >= G) ? -1 : (int)v;
 }
 
@@ -79,7 +73,71 @@ __device__ __forceinline__ void add_charge(int64_t* __restrict__ out, unsigned i
     if (q != 0) atomicAdd(reinterpret_cast<unsigned long long*>(out + idx), (unsigned long long)q);
 }
 
-__global__ void __launch_bounds__(256, 2) k_deposit(LevelDev L, Particles P, double half_dt,
+// CTA size and minimum resident CTAs per SM of the particle deposit
+#ifndef APM_DEP_THREADS
+#define APM_DEP_THREADS 128
+#endif
+#ifndef APM_DEP_MIN_CTAS
+#define APM_DEP_MIN_CTAS 5
+#endif
+constexpr int kDepThreads = APM_DEP_THREADS;
+
+template <bool SMALL>
+__device__ __forceinline__ unsigned long long mul63(unsigned long long a, unsigned long long b) {
+    return SMALL ? wmul63_small(a, b) : wmul63(a, b);
+}
+
+// The 27 charges of one particle into every candidate grid [e0, e1) of the
+// level: ((|M| wx) wy) wz for the 26 outer cells, every product rounded half up
+// on the scale 2^63, the centre cell M minus the others.  SMALL: |M| < 2^32.
+template <bool SMALL>
+__device__ __forceinline__ void scatter_charges(const LevelDev& L, int64_t* const* __restrict__ gmf,
+                                                unsigned* __restrict__ status, long long M,
+                                                unsigned long long aM, const unsigned long long w[3][3],
+                                                const long long ic[3], int e0, int e1, bool outside) {
+    unsigned long long mx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mx[a] = mul63<SMALL>(aM, w[0][a]);
+    for (int e = e0; e < e1; ++e) {
+        const int gi = L.is_root ? 0 : L.map.dep_list[e];
+        const GridDev& g = L.g[gi];
+        if (g.mode == 1 && outside) atomicOr(status, kStOutOfBox);
+        int64_t* __restrict__ out = gmf[gi];
+        // GMF boxes hold fewer than 2^31 cells (checked on the host)
+        int cx[3], cy[3], cz[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            cx[k] = edge_rule(ic[0] + k - 1 - g.lo[0], g.G[0], g.mode);
+            cy[k] = edge_rule(ic[1] + k - 1 - g.lo[1], g.G[1], g.mode);
+            cz[k] = edge_rule(ic[2] + k - 1 - g.lo[2], g.G[2], g.mode);
+        }
+        const unsigned G0 = g.G[0], G01 = (unsigned)g.G[0] * g.G[1];
+        long long others = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            unsigned long long mxy[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) mxy[a] = mul63<SMALL>(mx[a], w[1][b]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const bool ok = cy[b] >= 0 && cz[c] >= 0;
+                const unsigned row = G0 * (unsigned)cy[b] + G01 * (unsigned)cz[c];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (a == 1 && b == 1 && c == 1) continue;
+                    long long v = (long long)mul63<SMALL>(mxy[a], w[2][c]);
+                    v = M < 0 ? -v : v;
+                    others += v;
+                    if (ok && cx[a] >= 0) add_charge(out, row + (unsigned)cx[a], v);
+                }
+            }
+        }
+        if (cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0)
+            add_charge(out, (unsigned)cx[1] + G0 * (unsigned)cy[1] + G01 * (unsigned)cz[1], M - others);
+    }
+}
+
+__global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(LevelDev L, Particles P, double half_dt,
                                                  double box, int periodic, int F,
                                                  int64_t* const* __restrict__ gmf,
                                                  unsigned* __restrict__ status) {
@@ -125,51 +183,14 @@ __global__ void __launch_bounds__(256, 2) k_deposit(LevelDev L, Particles P, dou
         return;
     }
     const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
-    // charges ((|M| wx) wy) wz of the 26 outer cells, every product rounded half
-    // up on the scale 2^63; the centre takes M minus the others
-    unsigned long long mxy[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const unsigned long long mx = wmul63(aM, w[0][a]);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) mxy[b][a] = wmul63(mx, w[1][b]);
-    }
-    for (int e = e0; e < e1; ++e) {
-        const int gi = L.is_root ? 0 : L.map.dep_list[e];
-        const GridDev& g = L.g[gi];
-        if (g.mode == 1) {
-            for (int j = 0; j < 3; ++j)
-                if (!(xd[j] >= 0.0 && xd[j] < box)) atomicOr(status, kStOutOfBox);
-        }
-        int64_t* __restrict__ out = gmf[gi];
-        // GMF boxes hold fewer than 2^31 cells (checked on the host)
-        int cx[3], cy[3], cz[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            cx[k] = edge_rule(ic[0] + k - 1 - g.lo[0], g.G[0], g.mode);
-            cy[k] = edge_rule(ic[1] + k - 1 - g.lo[1], g.G[1], g.mode);
-            cz[k] = edge_rule(ic[2] + k - 1 - g.lo[2], g.G[2], g.mode);
-        }
-        const unsigned G0 = g.G[0], G01 = (unsigned)g.G[0] * g.G[1];
-        long long others = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const bool ok = cy[b] >= 0 && cz[c] >= 0;
-                const unsigned row = G0 * (unsigned)cy[b] + G01 * (unsigned)cz[c];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (a == 1 && b == 1 && c == 1) continue;
-                    long long v = (long long)wmul63(mxy[b][a], w[2][c]);
-                    v = M < 0 ? -v : v;
-                    others += v;
-                    if (ok && cx[a] >= 0) add_charge(out, row + (unsigned)cx[a], v);
-                }
-            }
-        if (cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0)
-            add_charge(out, (unsigned)cx[1] + G0 * (unsigned)cy[1] + G01 * (unsigned)cz[1], M - others);
-    }
+    // isolated root only: a drifted particle outside [0, box) is flagged (its cloud folds)
+    const bool outside = L.is_root && L.g[0].mode == 1 &&
+                         !(xd[0] >= 0.0 && xd[0] < box && xd[1] >= 0.0 && xd[1] < box && xd[2] >= 0.0 &&
+                           xd[2] < box);
+    if (aM < (1ULL << 32))   // every product has a 32-bit factor: |M|, then (|M| wx), then (|M| wx) wy
+        scatter_charges<true>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
+    else
+        scatter_charges<false>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
 }
 
 }  // namespace
@@ -179,8 +200,7 @@ cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
                             int64_t* const* gmf, const Chunk* chunks, int n_chunks, int rows_per_cta,
                             int F, cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    k_gas_init<<<n_chunks, 256, 0, s>>>(L, parent_grids, gas, pgas, gmf, chunks, rows_per_cta, F,
-                                         L.refine);
+    k_gas_init<<<n_chunks, 256, 0, s>>>(L, parent_grids, gas, pgas, gmf, chunks, rows_per_cta, F);
     return cudaGetLastError();
 }
 
@@ -188,8 +208,8 @@ cudaError_t launch_deposit(const LevelDev& L, const Particles& P, double half_dt
                            int periodic, int F, int64_t* const* gmf, unsigned* status,
                            cudaStream_t s) {
     if (P.n <= 0) return cudaSuccess;
-    unsigned blocks = (unsigned)((P.n + 255) / 256);
-    k_deposit<<<blocks, 256, 0, s>>>(L, P, half_dt, box, periodic, F, gmf, status);
+    unsigned blocks = (unsigned)((P.n + kDepThreads - 1) / kDepThreads);
+    k_deposit<<<blocks, kDepThreads, 0, s>>>(L, P, half_dt, box, periodic, F, gmf, status);
     return cudaGetLastError();
 }
 
