@@ -174,6 +174,19 @@ apm_status apm_deposit(apm_ctx* ctx, int32_t level, const apm_particles* particl
                        double half_dt, const double* const* gas,
                        const double* const* parent_gas, int64_t* const* gmf, void* stream);
 
+/* apm_deposit for every level of the hierarchy at once: the baryons of each
+ * level as apm_deposit (parent gas on the borders), then one pass over the
+ * particles that converts each position and mass once and deposits it level
+ * by level from the root down while it is a candidate of the level.  The
+ * fields are bit-identical to apm_deposit level by level.  Not in the paper:
+ * a batching of its per-level deposits.
+ *  gas : HOST array of n_grids device pointers in hierarchy order (dims^3
+ *        densities, NULL entries for no gas), or NULL for no baryons at all
+ *  gmf : HOST array of n_grids device pointers in hierarchy order (the GMF
+ *        box of each grid), fully overwritten */
+apm_status apm_deposit_all(apm_ctx* ctx, const apm_particles* particles, double half_dt,
+                           const double* const* gas, int64_t* const* gmf, void* stream);
+
 /* Short-range (refined level) or full (root) potential of every grid of
  * `level` (Sec. 2.2, Eq. PoissonFourier with Eq. influence): the GMF cell
  * masses (gmf * 2^-F, converted in FP64) are zero-padded onto the grid's M
@@ -244,6 +257,16 @@ apm_status apm_set_fft_shapes(apm_ctx* ctx, int32_t level, const apm_fft_shapes*
 apm_status apm_interp(apm_ctx* ctx, int32_t level, const void* const* acc,
                       const apm_particles* particles, double half_dt, void* acc_out,
                       void* stream);
+
+/* apm_interp for every level at once: one pass over the particles that
+ * converts each position once, finds its finest owning grid (searching from
+ * the root down) and interpolates that grid's accelerations.  Every particle
+ * owned by some grid is written, with the values apm_interp level by level
+ * writes.  Not in the paper: a batching of its per-level interpolations.
+ *  acc : HOST array of n_grids device pointers in hierarchy order (the
+ *        apm_accel output of each grid) */
+apm_status apm_interp_all(apm_ctx* ctx, const void* const* acc, const apm_particles* particles,
+                          double half_dt, void* acc_out, void* stream);
 
 /* Kernel tracing.  While enabled, every kernel the context launches is
  * bracketed by CUDA events recorded on the stream it runs on (events come from

@@ -51,6 +51,10 @@ SIGNATURES = {
     "apm_deposit": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmParticles), c_dbl,
                             ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                             ctypes.POINTER(c_void_p), c_void_p]),
+    "apm_deposit_all": (c_i32, [c_void_p, ctypes.POINTER(ApmParticles), c_dbl, ctypes.POINTER(c_void_p),
+                                ctypes.POINTER(c_void_p), c_void_p]),
+    "apm_interp_all": (c_i32, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(ApmParticles), c_dbl,
+                               c_void_p, c_void_p]),
     "apm_solve_level": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p),
                                 ctypes.POINTER(c_void_p), c_void_p]),
     "apm_accel": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),

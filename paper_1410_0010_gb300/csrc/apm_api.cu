@@ -81,6 +81,8 @@ struct apm_ctx {
     float* tab32 = nullptr;
     void* wsA = nullptr;
     void* wsB = nullptr;
+    LevelDev* d_levels = nullptr;    // every level's LevelDev (the all-level kernels)
+    void** d_tabs = nullptr;         // [role][level]: each level's device pointer table of the role
     Profiler prof;
 };
 
@@ -136,6 +138,7 @@ void free_hierarchy(apm_ctx* c) {
     c->index_in_level.clear();
     c->tw64 = nullptr; c->tw32 = nullptr; c->tab64 = nullptr; c->tab32 = nullptr;
     c->wsA = nullptr; c->wsB = nullptr;
+    c->d_levels = nullptr; c->d_tabs = nullptr;
     c->has_hier = false;
 }
 
@@ -767,6 +770,18 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
         }
         if (cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess) return APM_E_CUDA;
     }
+    {
+        const int nl = (int)c->levels.size();
+        std::vector<LevelDev> lv(nl);
+        std::vector<void*> tabs((size_t)kRoles * nl);
+        for (int l = 0; l < nl; ++l) {
+            lv[l] = c->levels[l].dev;
+            for (int r = 0; r < kRoles; ++r)
+                tabs[(size_t)r * nl + l] = c->levels[l].d_ptr + (size_t)r * c->levels[l].cap;
+        }
+        if ((st = upload(c, &c->d_levels, lv)) != APM_OK) return st;
+        if ((st = upload(c, &c->d_tabs, tabs)) != APM_OK) return st;
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return APM_E_CUDA;
     c->has_hier = true;
     return APM_OK;
@@ -806,8 +821,54 @@ apm_status apm_deposit(apm_ctx* c, int32_t level, const apm_particles* particles
     }
     Particles P = to_dev(particles);
     Trace t(c, K_DEPOSIT, s);
-    return cuda_status(launch_deposit(L.dev, P, half_dt, c->cfg.box, c->cfg.root_bc == APM_BC_PERIODIC,
-                                      c->cfg.mass_frac_bits, (int64_t* const*)d_gmf, c->d_status, s));
+    return cuda_status(launch_deposit(L.dev, P, half_dt, c->cfg.box, c->cfg.mass_frac_bits,
+                                      (int64_t* const*)d_gmf, c->d_status, s));
+}
+
+apm_status apm_deposit_all(apm_ctx* c, const apm_particles* particles, double half_dt,
+                           const double* const* gas, int64_t* const* gmf, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (!gmf || !particles_ok(particles)) return APM_E_INVALID;
+    const int n = (int)c->grids.size(), nl = (int)c->levels.size();
+    for (int i = 0; i < n; ++i)
+        if (!gmf[i]) return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    apm_status st;
+    // baryons of every level (the parent's gas borders each child), as apm_deposit
+    std::vector<const void*> pg, pgas, pgm;
+    for (int l = 0; l < nl; ++l) {
+        Level& L = c->levels[l];
+        const int ng = (int)L.grids.size();
+        pg.assign(ng, nullptr);
+        for (int k = 0; k < ng; ++k) pg[k] = gmf[L.grids[k]];
+        void **d_gmf, **d_gas = nullptr, **d_pgas = nullptr;
+        if ((st = set_ptrs(c, L, R_GMF, pg.data(), ng, &d_gmf, s)) != APM_OK) return st;
+        const GridDev* pgrids = nullptr;
+        if (gas) {
+            pgas.assign(ng, nullptr);
+            for (int k = 0; k < ng; ++k) pgas[k] = gas[L.grids[k]];
+            if ((st = set_ptrs(c, L, R_GAS, pgas.data(), ng, &d_gas, s)) != APM_OK) return st;
+            if (l > 0) {
+                Level& P = c->levels[l - 1];
+                pgm.assign(P.grids.size(), nullptr);
+                for (size_t k = 0; k < P.grids.size(); ++k) pgm[k] = gas[P.grids[k]];
+                if ((st = set_ptrs(c, L, R_PGAS, pgm.data(), (int)P.grids.size(), &d_pgas, s)) != APM_OK)
+                    return st;
+                pgrids = P.d_grids;
+            }
+        }
+        Trace t(c, K_GAS, s);
+        if (launch_gas_init(L.dev, pgrids, (const double* const*)d_gas, (const double* const*)d_pgas,
+                            (int64_t* const*)d_gmf, L.d_gas, L.n_gas, kChunkCells, c->cfg.mass_frac_bits,
+                            s) != cudaSuccess)
+            return APM_E_CUDA;
+    }
+    Particles P = to_dev(particles);
+    Trace t(c, K_DEPOSIT, s);
+    return cuda_status(launch_deposit_levels(c->d_levels, nl, P, half_dt, c->cfg.box, c->cfg.mass_frac_bits,
+                                             (int64_t* const* const*)(c->d_tabs + (size_t)R_GMF * nl),
+                                             c->d_status, s));
 }
 
 apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
@@ -994,11 +1055,38 @@ apm_status apm_interp(apm_ctx* c, int32_t level, const void* const* acc,
     if ((st = set_ptrs(c, L, R_ACC_IN, acc, (int)L.grids.size(), &d_acc, s)) != APM_OK) return st;
     const LevelDev* finer = level + 1 < (int)c->levels.size() ? &c->levels[level + 1].dev : nullptr;
     Particles P = to_dev(particles);
-    const int periodic = c->cfg.root_bc == APM_BC_PERIODIC;
     Trace t(c, K_INTERP, s);
     cudaError_t e = c->cfg.precision == APM_FP64
-        ? launch_interp<double>(L.dev, finer, P, half_dt, c->cfg.box, periodic, (const void* const*)d_acc, acc_out, s)
-        : launch_interp<float>(L.dev, finer, P, half_dt, c->cfg.box, periodic, (const void* const*)d_acc, acc_out, s);
+        ? launch_interp<double>(L.dev, finer, P, half_dt, (const void* const*)d_acc, acc_out, s)
+        : launch_interp<float>(L.dev, finer, P, half_dt, (const void* const*)d_acc, acc_out, s);
+    return cuda_status(e);
+}
+
+apm_status apm_interp_all(apm_ctx* c, const void* const* acc, const apm_particles* particles,
+                          double half_dt, void* acc_out, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (!acc || !particles_ok(particles) || (!acc_out && particles->n > 0)) return APM_E_INVALID;
+    const int n = (int)c->grids.size(), nl = (int)c->levels.size();
+    for (int i = 0; i < n; ++i)
+        if (!acc[i]) return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<const void*> pa;
+    for (int l = 0; l < nl; ++l) {
+        Level& L = c->levels[l];
+        const int ng = (int)L.grids.size();
+        pa.assign(ng, nullptr);
+        for (int k = 0; k < ng; ++k) pa[k] = acc[L.grids[k]];
+        void** d_acc;
+        apm_status st = set_ptrs(c, L, R_ACC_IN, pa.data(), ng, &d_acc, s);
+        if (st != APM_OK) return st;
+    }
+    Particles P = to_dev(particles);
+    const void* const* const* tabs = (const void* const* const*)(c->d_tabs + (size_t)R_ACC_IN * nl);
+    Trace t(c, K_INTERP, s);
+    cudaError_t e = c->cfg.precision == APM_FP64
+        ? launch_interp_levels<double>(c->d_levels, nl, P, half_dt, tabs, acc_out, s)
+        : launch_interp_levels<float>(c->d_levels, nl, P, half_dt, tabs, acc_out, s);
     return cuda_status(e);
 }
 

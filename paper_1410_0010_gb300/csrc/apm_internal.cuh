@@ -321,8 +321,11 @@ cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
                             int64_t* const* gmf, const Chunk* chunks, int n_chunks, int rows_per_cta,
                             int F, cudaStream_t s);
 cudaError_t launch_deposit(const LevelDev& L, const Particles& P, double half_dt, double box,
-                           int periodic, int F, int64_t* const* gmf, unsigned* status,
-                           cudaStream_t s);
+                           int F, int64_t* const* gmf, unsigned* status, cudaStream_t s);
+// every level in one pass: levels[nl] and gmfs[nl] in device memory
+cudaError_t launch_deposit_levels(const LevelDev* levels, int nl, const Particles& P, double half_dt,
+                                  double box, int F, int64_t* const* const* gmfs, unsigned* status,
+                                  cudaStream_t s);
 
 // FFT passes of one level (T = float or double)
 struct FftArgs {
@@ -357,7 +360,10 @@ cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const v
                          cudaStream_t s);
 template <typename T>
 cudaError_t launch_interp(const LevelDev& L, const LevelDev* finer, const Particles& P,
-                          double half_dt, double box, int periodic, const void* const* acc,
-                          void* out, cudaStream_t s);
+                          double half_dt, const void* const* acc, void* out, cudaStream_t s);
+// every level in one pass: levels[nl] and accs[nl] in device memory
+template <typename T>
+cudaError_t launch_interp_levels(const LevelDev* levels, int nl, const Particles& P, double half_dt,
+                                 const void* const* const* accs, void* out, cudaStream_t s);
 
 }  // namespace apm

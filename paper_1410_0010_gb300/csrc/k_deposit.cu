@@ -137,24 +137,17 @@ __device__ __forceinline__ void scatter_charges(const LevelDev& L, int64_t* cons
     }
 }
 
-__global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(LevelDev L, Particles P, double half_dt,
-                                                 double box, int periodic, int F,
-                                                 int64_t* const* __restrict__ gmf,
-                                                 unsigned* __restrict__ status) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= P.n) return;
-    // fixed-point position and weights (the same for every level)
-    const double xd[3] = {drift_raw(P.x[p], P.vx[p], half_dt), drift_raw(P.y[p], P.vy[p], half_dt),
-                          drift_raw(P.z[p], P.vz[p], half_dt)};
-    long long ic[3];
+// Deposit of one particle (fixed-point position X, integer mass M) into the
+// grids of one level; false when the particle is not a candidate of the level
+// (then it is none of a finer level's either: finer GMF boxes lie inside the
+// interiors of their parents).
+__device__ __forceinline__ bool deposit_level(const LevelDev& L, const long long X[3], long long M,
+                                              bool outside, int64_t* const* __restrict__ gmf,
+                                              unsigned* __restrict__ status) {
     const int PB = L.frac_bits;
-    long long X[3];
+    long long ic[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        X[j] = fixed_position(xd[j], L);
-        ic[j] = X[j] >> PB;
-    }
-
+    for (int j = 0; j < 3; ++j) ic[j] = X[j] >> PB;
     // candidate grids
     int e0 = 0, e1 = 1;
     if (!L.is_root) {
@@ -163,34 +156,98 @@ __global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(Level
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             long long rel = ic[j] - m.lo[j];
+            if (rel < 0) return false;
+            t[j] = rel >> m.shift;
+            if (t[j] >= m.nt[j]) return false;
+        }
+        long long tile = t[0] + (long long)m.nt[0] * (t[1] + (long long)m.nt[1] * t[2]);
+        e0 = m.dep_off[tile];
+        e1 = m.dep_off[tile + 1];
+        if (e0 == e1) return false;
+    }
+    unsigned long long w[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) tsc_fixed(X[j], PB, w[j]);
+    const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
+    if (aM < (1ULL << 32))   // every product has a 32-bit factor: |M|, then (|M| wx), then (|M| wx) wy
+        scatter_charges<true>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
+    else
+        scatter_charges<false>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
+    return true;
+}
+
+// drifted coordinates, fixed-point position and integer mass of particle p;
+// false (and the overflow flag) when |m 2^F| >= 2^62
+__device__ __forceinline__ bool particle_fixed(const LevelDev& L, const Particles& P, long long p,
+                                               double half_dt, double box, int F, long long X[3],
+                                               long long* M, bool* outside, unsigned* __restrict__ status) {
+    const double xd[3] = {drift_raw(P.x[p], P.vx[p], half_dt), drift_raw(P.y[p], P.vy[p], half_dt),
+                          drift_raw(P.z[p], P.vz[p], half_dt)};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) X[j] = fixed_position(xd[j], L);   // the same for every level
+    bool ok;
+    *M = scaled_rint(P.m[p], F, ok);   // rint(m 2^F)
+    if (!ok) {
+        atomicOr(status, kStOverflow);
+        return false;
+    }
+    // isolated root only: a drifted particle outside [0, box) is flagged (its cloud folds)
+    *outside = L.g[0].mode == 1 && L.is_root &&
+               !(xd[0] >= 0.0 && xd[0] < box && xd[1] >= 0.0 && xd[1] < box && xd[2] >= 0.0 && xd[2] < box);
+    return true;
+}
+
+__global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(LevelDev L, Particles P, double half_dt,
+                                                 double box, int F,
+                                                 int64_t* const* __restrict__ gmf,
+                                                 unsigned* __restrict__ status) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P.n) return;
+    long long X[3], M;
+    bool outside;
+    // the candidate test comes first on refined levels (most particles leave there)
+    if (!L.is_root) {
+        const double xd[3] = {drift_raw(P.x[p], P.vx[p], half_dt), drift_raw(P.y[p], P.vy[p], half_dt),
+                              drift_raw(P.z[p], P.vz[p], half_dt)};
+        const TileMap& m = L.map;
+        long long t[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            X[j] = fixed_position(xd[j], L);
+            long long rel = (X[j] >> L.frac_bits) - m.lo[j];
             if (rel < 0) return;
             t[j] = rel >> m.shift;
             if (t[j] >= m.nt[j]) return;
         }
         long long tile = t[0] + (long long)m.nt[0] * (t[1] + (long long)m.nt[1] * t[2]);
-        e0 = m.dep_off[tile];
-        e1 = m.dep_off[tile + 1];
-        if (e0 == e1) return;
-    }
-    unsigned long long w[3][3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) tsc_fixed(X[j], PB, w[j]);
-
-    bool ok;
-    const long long M = scaled_rint(P.m[p], F, ok);   // rint(m 2^F)
-    if (!ok) {                                         // |m 2^F| >= 2^62
-        atomicOr(status, kStOverflow);
+        if (m.dep_off[tile] == m.dep_off[tile + 1]) return;
+        bool ok;
+        M = scaled_rint(P.m[p], F, ok);
+        if (!ok) {
+            atomicOr(status, kStOverflow);
+            return;
+        }
+        deposit_level(L, X, M, false, gmf, status);
         return;
     }
-    const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
-    // isolated root only: a drifted particle outside [0, box) is flagged (its cloud folds)
-    const bool outside = L.is_root && L.g[0].mode == 1 &&
-                         !(xd[0] >= 0.0 && xd[0] < box && xd[1] >= 0.0 && xd[1] < box && xd[2] >= 0.0 &&
-                           xd[2] < box);
-    if (aM < (1ULL << 32))   // every product has a 32-bit factor: |M|, then (|M| wx), then (|M| wx) wy
-        scatter_charges<true>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
-    else
-        scatter_charges<false>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
+    if (!particle_fixed(L, P, p, half_dt, box, F, X, &M, &outside, status)) return;
+    deposit_level(L, X, M, outside, gmf, status);
+}
+
+// Every level in one pass over the particles: the position and mass are
+// converted once, then deposited level by level from the root down while the
+// particle is a candidate.  levels: the LevelDev of each level; gmfs[l]: the
+// GMF pointer table of level l.
+__global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit_levels(
+    const LevelDev* __restrict__ levels, int nl, Particles P, double half_dt, double box, int F,
+    int64_t* const* const* __restrict__ gmfs, unsigned* __restrict__ status) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P.n) return;
+    long long X[3], M;
+    bool outside;
+    if (!particle_fixed(levels[0], P, p, half_dt, box, F, X, &M, &outside, status)) return;
+    for (int l = 0; l < nl; ++l)
+        if (!deposit_level(levels[l], X, M, l == 0 && outside, gmfs[l], status)) break;
 }
 
 }  // namespace
@@ -205,11 +262,19 @@ cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
 }
 
 cudaError_t launch_deposit(const LevelDev& L, const Particles& P, double half_dt, double box,
-                           int periodic, int F, int64_t* const* gmf, unsigned* status,
-                           cudaStream_t s) {
+                           int F, int64_t* const* gmf, unsigned* status, cudaStream_t s) {
     if (P.n <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n + kDepThreads - 1) / kDepThreads);
-    k_deposit<<<blocks, kDepThreads, 0, s>>>(L, P, half_dt, box, periodic, F, gmf, status);
+    k_deposit<<<blocks, kDepThreads, 0, s>>>(L, P, half_dt, box, F, gmf, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_levels(const LevelDev* levels, int nl, const Particles& P, double half_dt,
+                                  double box, int F, int64_t* const* const* gmfs, unsigned* status,
+                                  cudaStream_t s) {
+    if (P.n <= 0 || nl <= 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((P.n + kDepThreads - 1) / kDepThreads);
+    k_deposit_levels<<<blocks, kDepThreads, 0, s>>>(levels, nl, P, half_dt, box, F, gmfs, status);
     return cudaGetLastError();
 }
 

@@ -252,63 +252,64 @@ __device__ int find_owner(const LevelDev& L, const long long ic[3]) {
     return -1;
 }
 
-template <typename T> __device__ __forceinline__ T weight63(unsigned long long W);
-template <> __device__ __forceinline__ double weight63<double>(unsigned long long W) {
-    return __ull2double_rn(W) * 1.0842021724855044e-19;    // 2^-63
-}
-template <> __device__ __forceinline__ float weight63<float>(unsigned long long W) {
-    return __uint2float_rn((unsigned)(W >> 39)) * 5.9604644775390625e-08f;   // 2^-24
-}
-
-// TSC interpolation with the deposit's fixed-point weights: the 26 outer
-// weights are the rounded products ((wx wy) wz), the centre weight is one minus
-// their sum, exactly as the deposit distributes a particle's mass.
-template <typename T>
-__global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_finer, Particles P,
-                                                double half_dt, double box, int periodic,
-                                                const void* const* __restrict__ acc_p,
-                                                T* __restrict__ out) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= P.n) return;
-    long long X[3];
-    X[0] = fixed_position(drift_raw(P.x[p], P.vx[p], half_dt), L);
-    X[1] = fixed_position(drift_raw(P.y[p], P.vy[p], half_dt), L);
-    X[2] = fixed_position(drift_raw(P.z[p], P.vz[p], half_dt), L);
-    long long ic[3];
-    for (int j = 0; j < 3; ++j) ic[j] = X[j] >> L.frac_bits;
-    int gi = find_owner(L, ic);
-    if (gi < 0) return;
-    if (has_finer) {
-        long long fc[3];
-        for (int j = 0; j < 3; ++j) fc[j] = X[j] >> F.frac_bits;
-        if (find_owner(F, fc) >= 0) return;
-    }
+// The 27 interpolation weights of a particle at fixed-point position X on a
+// level with `fb` fraction bits.  FP64: the deposit's fixed-point weights
+// exactly (outer products ((wx wy) wz) rounded on the scale 2^63, the centre one
+// minus their sum).  FP32: the same TSC weights evaluated in FP32 from the
+// offsets (t = f 2^-fb; (1-t)^2/2, 3/4 - (t-1/2)^2, t^2/2; products (wx wy) wz),
+// within a few FP32 roundings of the fixed-point ones.
+__device__ __forceinline__ void interp_weights(const long long X[3], int fb, double wq[3][3][3]) {
     unsigned long long w[3][3];
-    for (int j = 0; j < 3; ++j) tsc_fixed(X[j], L.frac_bits, w[j]);
-    unsigned long long wq[3][3][3];
+    for (int j = 0; j < 3; ++j) tsc_fixed(X[j], fb, w[j]);
     unsigned long long wsum = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
+        for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                if (a == 1 && b == 1 && c == 1) {
-                    wq[c][b][a] = 0;
-                    continue;
-                }
-                wq[c][b][a] = wmul63(wmul63(w[0][a], w[1][b]), w[2][c]);
-                wsum += wq[c][b][a];
+                if (a == 1 && b == 1 && c == 1) continue;
+                const unsigned long long q = wmul63(wmul63(w[0][a], w[1][b]), w[2][c]);
+                wsum += q;
+                wq[c][b][a] = __ull2double_rn(q) * 1.0842021724855044e-19;   // 2^-63
             }
+    wq[1][1][1] = __ull2double_rn(kOne63 - wsum) * 1.0842021724855044e-19;
+}
+__device__ __forceinline__ void interp_weights(const long long X[3], int fb, float wq[3][3][3]) {
+    float w[3][3];
+    const float sc = __int_as_float((127 - fb) << 23);   // 2^-fb
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const long long i = X[j] >> fb;
+        const float t = __ull2float_rn((unsigned long long)(X[j] - (i << fb))) * sc;
+        const float u = 1.0f - t;
+        w[j][0] = 0.5f * u * u;
+        w[j][2] = 0.5f * t * t;
+        w[j][1] = 0.75f - (t - 0.5f) * (t - 0.5f);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float wyz = w[1][b] * w[2][c];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) wq[c][b][a] = w[0][a] * wyz;
         }
-    wq[1][1][1] = kOne63 - wsum;
-    const GridDev& g = L.g[gi];
-    const T* __restrict__ A = reinterpret_cast<const T*>(acc_p[gi]);
+}
+
+// TSC interpolation of the cell accelerations A (3 x (N+2)^3 of grid g, level L)
+// at fixed-point position X; writes out[p], out[n + p], out[2n + p].
+template <typename T>
+__device__ __forceinline__ void interp_from(const LevelDev& L, const GridDev& g, const T* __restrict__ A,
+                                            const long long X[3], long long p, long long n,
+                                            T* __restrict__ out) {
+    T wq[3][3][3];
+    interp_weights(X, L.frac_bits, wq);
     const int E0 = g.N[0] + 2, E1 = g.N[1] + 2;
     const unsigned ncell = (unsigned)E0 * E1 * (g.N[2] + 2);
     const bool fold = g.mode == 1;
     int lc[3];
-    for (int j = 0; j < 3; ++j) lc[j] = (int)(ic[j] - g.start[j]);
+    for (int j = 0; j < 3; ++j) lc[j] = (int)((X[j] >> L.frac_bits) - g.start[j]);
     T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_
             for (int a = 0; a < 3; ++a) {
                 int x = lc[0] + a - 1;
                 if (fold) x = x < 0 ? 0 : (x >= g.N[0] ? g.N[0] - 1 : x);
-                const T wt = weight63<T>(wq[c][b][a]);
+                const T wt = wq[c][b][a];
                 unsigned idx = (unsigned)(x + 1) + (unsigned)E0 * ((unsigned)(y + 1) + (unsigned)E1 * (unsigned)(z + 1));
                 a0 += wt * A[idx];
                 a1 += wt * A[ncell + idx];
@@ -331,8 +332,63 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_
         }
     }
     out[p] = a0;
-    out[P.n + p] = a1;
-    out[2 * P.n + p] = a2;
+    out[n + p] = a1;
+    out[2 * n + p] = a2;
+}
+
+__device__ __forceinline__ void particle_position(const LevelDev& L, const Particles& P, long long p,
+                                                  double half_dt, long long X[3]) {
+    X[0] = fixed_position(drift_raw(P.x[p], P.vx[p], half_dt), L);
+    X[1] = fixed_position(drift_raw(P.y[p], P.vy[p], half_dt), L);
+    X[2] = fixed_position(drift_raw(P.z[p], P.vz[p], half_dt), L);
+}
+
+// One level: the particles owned by a grid of L and by no grid of the finer
+// level F (the finest grid holding a particle supplies its acceleration).
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_finer, Particles P,
+                                                double half_dt, const void* const* __restrict__ acc_p,
+                                                T* __restrict__ out) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P.n) return;
+    long long X[3];
+    particle_position(L, P, p, half_dt, X);
+    long long ic[3];
+    for (int j = 0; j < 3; ++j) ic[j] = X[j] >> L.frac_bits;
+    int gi = find_owner(L, ic);
+    if (gi < 0) return;
+    if (has_finer) {
+        long long fc[3];
+        for (int j = 0; j < 3; ++j) fc[j] = X[j] >> F.frac_bits;
+        if (find_owner(F, fc) >= 0) return;
+    }
+    interp_from<T>(L, L.g[gi], reinterpret_cast<const T*>(acc_p[gi]), X, p, P.n, out);
+}
+
+// Every level in one pass: each particle's position is converted once and its
+// owner searched from the root down (a finer owner lies inside a coarser one);
+// the finest owner supplies the acceleration.  accs[l]: the acceleration
+// pointer table of level l.
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp_levels(const LevelDev* __restrict__ levels, int nl, Particles P,
+                                                       double half_dt, const void* const* const* __restrict__ accs,
+                                                       T* __restrict__ out) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P.n) return;
+    long long X[3];
+    particle_position(levels[0], P, p, half_dt, X);
+    int own_l = -1, own_g = -1;
+    for (int l = 0; l < nl; ++l) {
+        long long ic[3];
+        for (int j = 0; j < 3; ++j) ic[j] = X[j] >> levels[l].frac_bits;
+        const int gi = find_owner(levels[l], ic);
+        if (gi < 0) break;
+        own_l = l;
+        own_g = gi;
+    }
+    if (own_l < 0) return;
+    const LevelDev& L = levels[own_l];
+    interp_from<T>(L, L.g[own_g], reinterpret_cast<const T*>(accs[own_l][own_g]), X, p, P.n, out);
 }
 
 }  // namespace
@@ -350,13 +406,20 @@ cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const v
 
 template <typename T>
 cudaError_t launch_interp(const LevelDev& L, const LevelDev* finer, const Particles& P,
-                          double half_dt, double box, int periodic, const void* const* acc,
-                          void* out, cudaStream_t s) {
+                          double half_dt, const void* const* acc, void* out, cudaStream_t s) {
     if (P.n <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n + 255) / 256);
     LevelDev F = finer ? *finer : L;
-    k_interp<T><<<blocks, 256, 0, s>>>(L, F, finer ? 1 : 0, P, half_dt, box, periodic, acc,
-                                       reinterpret_cast<T*>(out));
+    k_interp<T><<<blocks, 256, 0, s>>>(L, F, finer ? 1 : 0, P, half_dt, acc, reinterpret_cast<T*>(out));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_interp_levels(const LevelDev* levels, int nl, const Particles& P, double half_dt,
+                                 const void* const* const* accs, void* out, cudaStream_t s) {
+    if (P.n <= 0 || nl <= 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((P.n + 255) / 256);
+    k_interp_levels<T><<<blocks, 256, 0, s>>>(levels, nl, P, half_dt, accs, reinterpret_cast<T*>(out));
     return cudaGetLastError();
 }
 
@@ -367,8 +430,12 @@ template cudaError_t launch_accel<double>(const LevelDev&, const GridDev*, const
                                           const void* const*, const void* const*, void* const*,
                                           void* const*, const Chunk*, int, int, cudaStream_t);
 template cudaError_t launch_interp<float>(const LevelDev&, const LevelDev*, const Particles&, double,
-                                          double, int, const void* const*, void*, cudaStream_t);
+                                          const void* const*, void*, cudaStream_t);
 template cudaError_t launch_interp<double>(const LevelDev&, const LevelDev*, const Particles&, double,
-                                           double, int, const void* const*, void*, cudaStream_t);
+                                           const void* const*, void*, cudaStream_t);
+template cudaError_t launch_interp_levels<float>(const LevelDev*, int, const Particles&, double,
+                                                 const void* const* const*, void*, cudaStream_t);
+template cudaError_t launch_interp_levels<double>(const LevelDev*, int, const Particles&, double,
+                                                  const void* const* const*, void*, cudaStream_t);
 
 }  // namespace apm

@@ -127,6 +127,29 @@ class Solver:
         check(lib().apm_deposit(self._ctx, level, ctypes.byref(P.c), float(half_dt), ga, pg, g,
                                 _stream_handle(stream)), "apm_deposit")
 
+    def deposit_all(self, particles, half_dt, gmf, gas=None, stream=None):
+        """apm_deposit_all: gmf / gas are lists over the hierarchy's grids."""
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        ga = None if gas is None else ptr_array([_ptr(t) for t in gas])
+        check(lib().apm_deposit_all(self._ctx, ctypes.byref(P.c), float(half_dt), ga,
+                                    ptr_array([_ptr(t) for t in gmf]), _stream_handle(stream)),
+              "apm_deposit_all")
+
+    def interp_all(self, acc, particles, half_dt, out, stream=None):
+        """apm_interp_all: acc is a list over the hierarchy's grids."""
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        check(lib().apm_interp_all(self._ctx, ptr_array([_ptr(t) for t in acc]), ctypes.byref(P.c),
+                                   float(half_dt), out.data_ptr(), _stream_handle(stream)),
+              "apm_interp_all")
+
+    def _per_grid(self, bufs, key):
+        """One buffer per grid in hierarchy order from the per-level lists of alloc_all()."""
+        out = [None] * len(self.grids)
+        for lev, ids in enumerate(self.level_grids):
+            for k, gi in enumerate(ids):
+                out[gi] = bufs[lev][key][k]
+        return out
+
     def solve_level(self, level, gmf, phis, stream=None):
         check(lib().apm_solve_level(self._ctx, level, ptr_array([_ptr(t) for t in gmf]),
                                     ptr_array([_ptr(t) for t in phis]), _stream_handle(stream)),
@@ -214,27 +237,34 @@ class Solver:
         check(lib().apm_sync_status(self._ctx, _stream_handle(stream)), "apm_sync_status")
 
     # ------------------------------------------------------------------ one solve
-    def step(self, particles, half_dt, bufs, pacc, gas=None, levels=None, stream=None, tune=False):
+    def step(self, particles, half_dt, bufs, pacc, gas=None, levels=None, stream=None, tune=False,
+             batched=True):
         """One APM solve over the hierarchy (Sec. 2, 2.2), levels top-down:
         deposit -> solve -> accel per level, then interpolation on every level.
         bufs: from alloc_all(); pacc: (3, n) tensor of the context precision, or
         None to stop after the cell accelerations; gas: None or a list with one
         device density tensor (or None) per grid; tune: solve through the
-        autotuner."""
+        autotuner; batched: deposit and interpolate every level in one call each
+        (apm_deposit_all / apm_interp_all, bit-identical to the per-level calls)
+        when all levels are stepped."""
         P = particles if isinstance(particles, Particles) else Particles(particles)
         levs = range(self.n_levels) if levels is None else levels
+        whole = batched and (levels is None or list(levels) == list(range(self.n_levels)))
+        if whole:   # every level: one pass over the particles (apm_deposit_all)
+            self.deposit_all(P, half_dt, self._per_grid(bufs, "gmf"), gas, stream)
         for lev in levs:
             b = bufs[lev]
             ids = self.level_grids[lev]
-            g = None if gas is None else [gas[i] for i in ids]
-            pg = None
-            if gas is not None and lev > 0:
-                pg = [gas[i] for i in self.level_grids[lev - 1]]
-                if all(t is None for t in pg):
-                    pg = None
-            if g is not None and all(t is None for t in g):
-                g = None
-            self.deposit(lev, P, half_dt, b["gmf"], g, pg, stream)
+            if not whole:
+                g = None if gas is None else [gas[i] for i in ids]
+                pg = None
+                if gas is not None and lev > 0:
+                    pg = [gas[i] for i in self.level_grids[lev - 1]]
+                    if all(t is None for t in pg):
+                        pg = None
+                if g is not None and all(t is None for t in g):
+                    g = None
+                self.deposit(lev, P, half_dt, b["gmf"], g, pg, stream)
             if tune:
                 self.autotune_level(lev, b["gmf"], b["phis"], stream)
             else:
@@ -245,6 +275,9 @@ class Solver:
             else:
                 self.accel(lev, b["phis"], b["phi"], b["acc"], stream=stream)
         if pacc is None:
+            return
+        if whole:
+            self.interp_all(self._per_grid(bufs, "acc"), P, half_dt, pacc, stream)
             return
         for lev in levs:
             self.interp(lev, bufs[lev]["acc"], P, half_dt, pacc, stream)

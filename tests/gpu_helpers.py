@@ -24,7 +24,7 @@ def rel_l2(a, b):
 
 
 def run_gpu(grids, particles, half_dt, gas=None, periodic=False, precision="fp64",
-            mass_frac_bits=52, root_correction=True, levels=None):
+            mass_frac_bits=52, root_correction=True, levels=None, batched=True):
     import torch
 
     from paper_1410_0010_gb300.solver import Solver
@@ -40,7 +40,7 @@ def run_gpu(grids, particles, half_dt, gas=None, periodic=False, precision="fp64
     bufs = s.alloc_all()
     n = len(particles["x"])
     pacc = torch.zeros((3, n), dtype=s.dtype, device=dev)
-    s.step(tp, half_dt, bufs, pacc, gas=tg, levels=levels)
+    s.step(tp, half_dt, bufs, pacc, gas=tg, levels=levels, batched=batched)
     s.sync_status()
     out = dict(gmf={}, phis={}, phi={}, acc={}, info=s.info, solver=s)
     for lev, ids in enumerate(s.level_grids):

@@ -95,6 +95,24 @@ def test_odd_starts_odd_root_and_grandchild(precision):
     compare(gpu, ref, precision)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_all_level_calls_equal_per_level_calls_bitwise(precision):
+    """apm_deposit_all / apm_interp_all against apm_deposit / apm_interp level by
+    level on a three-level periodic hierarchy with gas and particles everywhere
+    (including outside every refined grid and in the grandchild)."""
+    grids = _periodic_hierarchy()
+    rng = np.random.default_rng(14)
+    parts = W.concat_particles(_random_particles(rng, 800, vscale=0.5),
+                               _random_particles(rng, 400, 0.3, 0.6, vscale=0.5))
+    gas = [rng.random(g.dims[::-1]) + 0.1 for g in grids]
+    a = run_gpu(grids, parts, 2e-3, gas=gas, periodic=True, precision=precision, batched=True)
+    b = run_gpu(grids, parts, 2e-3, gas=gas, periodic=True, precision=precision, batched=False)
+    for gi in a["gmf"]:
+        assert np.array_equal(a["gmf"][gi], b["gmf"][gi]), gi
+        assert np.array_equal(a["acc"][gi], b["acc"][gi]), gi
+    assert np.array_equal(a["pacc"], b["pacc"])
+
+
 def test_edge_particles_faces_corners_border_and_outside():
     grids = [GridDesc(0, -1, (0, 0, 0), (16, 16, 16)), GridDesc(1, 0, (10, 10, 10), (8, 8, 8))]
     d0, d1 = 1 / 16, 1 / 32
