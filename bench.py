@@ -98,10 +98,11 @@ class Clocks:
 # ----------------------------------------------------------------------------
 # algorithmic bytes of each kernel (compulsory HBM traffic of its inputs/outputs)
 # ----------------------------------------------------------------------------
-def algorithmic_bytes(solver, w, levels, csz, rsz):
+def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
     """Bytes per step per kernel, summed over the solved levels.
 
-    csz / rsz: bytes of one complex / real value of the precision."""
+    csz / rsz: bytes of one complex / real value of the precision; batched:
+    the deposit and the interpolation read the particles once for all levels."""
     out = {k: 0 for k in ("gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green",
                           "fft_y_inv", "fft_x_inv", "accel_carry", "tsc_interp")}
     n = w.n_particles
@@ -123,8 +124,12 @@ def algorithmic_bytes(solver, w, levels, csz, rsz):
             ec = F[0] * F[1] * F[2]
             out["accel_carry"] += rsz * Wd[0] * Wd[1] * Wd[2] + 4 * rsz * ec
             out["tsc_interp"] += 3 * rsz * ec
-        out["tsc_deposit"] += 56 * n      # x, y, z, vx, vy, vz, m per level
-        out["tsc_interp"] += 48 * n       # positions and velocities per level
+        if not batched:
+            out["tsc_deposit"] += 56 * n      # x, y, z, vx, vy, vz, m per level
+            out["tsc_interp"] += 48 * n       # positions and velocities per level
+    if batched:                               # one pass over the particles for all levels
+        out["tsc_deposit"] += 56 * n
+        out["tsc_interp"] += 48 * n
     out["tsc_interp"] += 3 * rsz * n      # accelerations written once
     return out
 
@@ -375,7 +380,8 @@ def run_apm(args):
 
     # ---------------- roofline of the dominant kernel
     hbm, peak_src = peaks()
-    ab = algorithmic_bytes(s32, w, levels, 8, 4)
+    batched = levels == list(range(s32.n_levels))
+    ab = algorithmic_bytes(s32, w, levels, 8, 4, batched)
     kernels = {}
     for name, (cnt, tot) in prof.items():
         if cnt == 0:

@@ -608,7 +608,6 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
                 g.acc_sh[j] = (ic0 & 1) ? 0 : 1;
                 g.acc_nb[j] = (g.N[j] + 2 + g.acc_sh[j] + 1) / 2;
             }
-            g.rows_acc = std::max(1, (kChunkCells / 4) / g.acc_nb[0]);
             // green table (cached per shape and level parameters)
             TabKey key{g.kind, g.M[0], g.M[1], g.M[2], delta, a_lev, a_par};
             auto it = tab_off.find(key);
@@ -664,8 +663,9 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             const GridDev& g = L.hg[k];
             const long long grows = (long long)g.G[1] * g.G[2];
             for (long long t = 0; t < (grows + g.rows_gas - 1) / g.rows_gas; ++t) gas.push_back({k, (int)t});
-            const long long brows = (long long)g.acc_nb[1] * g.acc_nb[2];
-            for (long long t = 0; t < (brows + g.rows_acc - 1) / g.rows_acc; ++t) acc.push_back({k, (int)t});
+            const long long nblocks = (long long)g.acc_nb[0] * g.acc_nb[1] * g.acc_nb[2];
+            for (long long t = 0; t < (nblocks + kAccBlocksPerCta - 1) / kAccBlocksPerCta; ++t)
+                acc.push_back({k, (int)t});
         }
         for (int q = 0; q < kFftPasses; ++q) {
             if ((st = build_pass(c, L, q, f64 ? kFftBudgetF64 : kFftBudgetF32, kFftThreads, f64, L.pass[q])) != APM_OK)

@@ -129,7 +129,6 @@ struct GridDev {
     long long cells_gmf; // G0 G1 G2
     int lines[kFftPasses];   // lines per CTA of each pass (row pairs for xf / xi)
     int rows_gas;        // GMF rows per CTA of the baryon initialisation
-    int rows_acc;        // rows of 2x2x2 output blocks per CTA of the acceleration kernel
     int acc_sh[3];       // 1 when output cell 0 is the second cell of its block, else 0
     int acc_nb[3];       // output blocks per axis
     double inv2d;        // 1 / (2 delta)
@@ -152,6 +151,35 @@ struct RowWalk {
         dx = blockDim.x - dr * n;
     }
     __device__ void next() {
+        x += dx;
+        r += dr;
+        if (x >= n) {
+            x -= n;
+            ++r;
+        }
+    }
+};
+
+// 2x2x2 output blocks per CTA of the acceleration kernel (flat ranges of the
+// grid's blocks, x fastest, so every thread gets the same count)
+constexpr int kAccBlocksPerCta = 512;
+
+// Threads of a CTA walking the flat range [f0, f0 + count) of elements of rows
+// of length n: thread t starts at f0 + t and strides by the block size, with
+// (row, x) stepped incrementally (one division per thread).
+struct FlatWalk {
+    int r, x, dr, dx, n, left;
+    __device__ FlatWalk(long long f0, int count, int n_) : n(n_) {
+        const long long f = f0 + threadIdx.x;
+        r = (int)(f / n);
+        x = (int)(f - (long long)r * n);
+        left = count - (int)threadIdx.x;
+        dr = blockDim.x / n;
+        dx = blockDim.x - dr * n;
+    }
+    __device__ bool ok() const { return left > 0; }
+    __device__ void next() {
+        left -= blockDim.x;
         x += dx;
         r += dr;
         if (x >= n) {

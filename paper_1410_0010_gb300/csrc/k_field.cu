@@ -87,13 +87,14 @@ __global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __rest
     }
     const T inv2d = (T)g.inv2d;
     const unsigned sy = W0, sz = (unsigned)W0 * W1;
-    const int r0 = ch.tile * g.rows_acc;
-    const int r1 = min(nbrows, r0 + g.rows_acc);
+    const long long nblocks = (long long)nbx * nbrows;
+    const long long f0 = (long long)ch.tile * kAccBlocksPerCta;
+    const int count = (int)min((long long)kAccBlocksPerCta, nblocks - f0);
     int last = -1;
     int ey0 = 0, ez0 = 0;
     unsigned ybase[4] = {0, 0, 0, 0}, zbase[4] = {0, 0, 0, 0};   // phis offsets of rows -1, 0, 1, 2 of the block
     unsigned prow = 0;
-    for (RowWalk it(r0, nbx); it.r < r1; it.next()) {
+    for (FlatWalk it(f0, count, nbx); it.ok(); it.next()) {
         if (it.r != last) {
             last = it.r;
             const int by = it.r % nby, bz = it.r / nby;
