@@ -54,8 +54,19 @@ __device__ __forceinline__ void load_parent(const T* __restrict__ f, unsigned ba
             for (int dx = 0; dx < 2; ++dx) q[dz][dy][dx] = f[base + dx + dy * P0 + dz * P01];
 }
 
+// CTA size and minimum resident CTAs per SM of the FP32 acceleration kernel
+#ifndef APM_ACC_THREADS
+#define APM_ACC_THREADS 256
+#endif
+#ifndef APM_ACC_MIN_CTAS
+#define APM_ACC_MIN_CTAS 4
+#endif
+constexpr int kAccThreads = APM_ACC_THREADS;
+template <typename T> struct AccMinCtas { static constexpr int value = APM_ACC_MIN_CTAS; };
+template <> struct AccMinCtas<double> { static constexpr int value = 1; };
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_accel(LevelDev L, const GridDev* __restrict__ pgrids,
+__global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(LevelDev L, const GridDev* __restrict__ pgrids,
                                                const void* const* __restrict__ phis_p,
                                                const void* const* __restrict__ pphi_p,
                                                const void* const* __restrict__ pacc_p,
@@ -401,7 +412,7 @@ cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const v
                          cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
     (void)rows_per_cta;
-    k_accel<T><<<n_chunks, 256, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks);
+    k_accel<T><<<n_chunks, kAccThreads, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks);
     return cudaGetLastError();
 }
 
