@@ -43,6 +43,9 @@ __device__ __forceinline__ void lerp_block(const T q[2][2][2], T out[2][2][2]) {
         }
 }
 
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+
 template <typename T>
 __device__ __forceinline__ void load_parent(const T* __restrict__ f, unsigned base, int P0, unsigned P01,
                                             T q[2][2][2]) {
@@ -56,10 +59,10 @@ __device__ __forceinline__ void load_parent(const T* __restrict__ f, unsigned ba
 
 // CTA size and minimum resident CTAs per SM of the FP32 acceleration kernel
 #ifndef APM_ACC_THREADS
-#define APM_ACC_THREADS 256
+#define APM_ACC_THREADS 128
 #endif
 #ifndef APM_ACC_MIN_CTAS
-#define APM_ACC_MIN_CTAS 4
+#define APM_ACC_MIN_CTAS 6
 #endif
 constexpr int kAccThreads = APM_ACC_THREADS;
 template <typename T> struct AccMinCtas { static constexpr int value = APM_ACC_MIN_CTAS; };
@@ -101,6 +104,12 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(Lev
     const long long nblocks = (long long)nbx * nbrows;
     const long long f0 = (long long)ch.tile * kAccBlocksPerCta;
     const int count = (int)min((long long)kAccBlocksPerCta, nblocks - f0);
+    // pair loads and stores need even row lengths and pointers aligned to two elements
+    using V2 = typename Cplx<T>::type;
+    const size_t amask = 2 * sizeof(T) - 1;
+    const bool valign = !(W0 & 1) && !(E0 & 1) && !(reinterpret_cast<size_t>(phis) & amask) &&
+                        !(reinterpret_cast<size_t>(phi) & amask) && !(reinterpret_cast<size_t>(acc) & amask) &&
+                        !((size_t)ncell & 1);
     int last = -1;
     int ey0 = 0, ez0 = 0;
     unsigned ybase[4] = {0, 0, 0, 0}, zbase[4] = {0, 0, 0, 0};   // phis offsets of rows -1, 0, 1, 2 of the block
@@ -128,32 +137,54 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(Lev
         int xi[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) xi[k] = min(max(ex0 + k, 0), W0 - 1);
-        // centre values (phis index e + 1 = ex0 + 1 + a, i.e. xi[1 + a], rows 1 + b, 1 + c)
-        T pc[2][2][2];
+        // phis of the four centre rows at x indices ex0 .. ex0+3 (the x
+        // neighbours and the centres e + 1 = ex0 + 1 + a): two pair loads when
+        // the row is even-aligned and unclamped
+        const bool vload = valign && ex0 >= 0 && ex0 + 3 <= W0 - 1 && !(ex0 & 1);
+        T xr[2][2][4];
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < 2; ++b) {
+                const unsigned row = zbase[1 + c] + ybase[1 + b];
+                if (vload) {
+                    const V2 u = *reinterpret_cast<const V2*>(phis + row + ex0);
+                    const V2 v = *reinterpret_cast<const V2*>(phis + row + ex0 + 2);
+                    xr[c][b][0] = u.x; xr[c][b][1] = u.y; xr[c][b][2] = v.x; xr[c][b][3] = v.y;
+                } else {
 #pragma unroll
-                for (int a = 0; a < 2; ++a) pc[c][b][a] = phis[zbase[1 + c] + ybase[1 + b] + xi[1 + a]];
+                    for (int k = 0; k < 4; ++k) xr[c][b][k] = phis[row + xi[k]];
+                }
+            }
         T out[2][2][2], q[2][2][2];
         unsigned pbase = 0;
         if (carry) {
             const long long kx = ((g.start[0] + ex0 - 1) - 1) >> 1;
             pbase = prow + (unsigned)(kx - ps[0] + 1);
         }
+        // output cells: (ex0 + a, ey0 + b, ez0 + c); the pair a = 0, 1 is one
+        // aligned pair store when both are inside and ex0 is even
         bool wr[2][2][2];
-        unsigned o[2][2][2];
+        unsigned o[2][2];
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const int ex = ex0 + a, ey = ey0 + b, ez = ez0 + c;
-                    wr[c][b][a] = ex >= 0 && ex < E0 && ey >= 0 && ey < E1 && ez >= 0 && ez < E2;
-                    o[c][b][a] = (unsigned)ex + (unsigned)E0 * ((unsigned)ey + (unsigned)E1 * (unsigned)ez);
-                }
+            for (int b = 0; b < 2; ++b) {
+                const int ey = ey0 + b, ez = ez0 + c;
+                const bool yz = ey >= 0 && ey < E1 && ez >= 0 && ez < E2;
+                wr[c][b][0] = yz && ex0 >= 0 && ex0 < E0;
+                wr[c][b][1] = yz && ex0 + 1 < E0;
+                o[c][b] = (unsigned)ex0 + (unsigned)E0 * ((unsigned)ey + (unsigned)E1 * (unsigned)ez);
+            }
+        const bool vpair = valign && !(ex0 & 1);
+        auto put = [&](T* __restrict__ f, int c, int b, T v0, T v1) {
+            if (vpair && wr[c][b][0] && wr[c][b][1]) {
+                *reinterpret_cast<V2*>(f + o[c][b]) = mk2(v0, v1);
+            } else {
+                if (wr[c][b][0]) f[o[c][b]] = v0;
+                if (wr[c][b][1]) f[o[c][b] + 1] = v1;
+            }
+        };
         // phi
         if (carry) {
             load_parent<T>(pphi, pbase, P0, P01, q);
@@ -162,11 +193,15 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(Lev
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-                    if (wr[c][b][a]) phi[o[c][b][a]] = carry ? pc[c][b][a] + out[c][b][a] : pc[c][b][a];
-        // acc_x: neighbours at phis x indices xi[0] and xi[3]
+            for (int b = 0; b < 2; ++b) {
+                T v0 = xr[c][b][1], v1 = xr[c][b][2];
+                if (carry) {
+                    v0 += out[c][b][0];
+                    v1 += out[c][b][1];
+                }
+                put(phi, c, b, v0, v1);
+            }
+        // acc_x: neighbours xr[.][.][0] and xr[.][.][3]
         {
             if (carry) {
                 load_parent<T>(pacc, pbase, P0, P01, q);
@@ -176,16 +211,13 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(Lev
             for (int c = 0; c < 2; ++c)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    const unsigned row = zbase[1 + c] + ybase[1 + b];
-                    const T lo = phis[row + xi[0]], hi = phis[row + xi[3]];
-                    T g0 = -(pc[c][b][1] - lo) * inv2d;
-                    T g1 = -(hi - pc[c][b][0]) * inv2d;
+                    T g0 = -(xr[c][b][2] - xr[c][b][0]) * inv2d;
+                    T g1 = -(xr[c][b][3] - xr[c][b][1]) * inv2d;
                     if (carry) {
                         g0 += out[c][b][0];
                         g1 += out[c][b][1];
                     }
-                    if (wr[c][b][0]) acc[o[c][b][0]] = g0;
-                    if (wr[c][b][1]) acc[o[c][b][1]] = g1;
+                    put(acc, c, b, g0, g1);
                 }
         }
         // acc_y: rows ybase[0] and ybase[3]
@@ -194,20 +226,26 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(Lev
                 load_parent<T>(pacc + pn, pbase, P0, P01, q);
                 lerp_block<T>(q, out);
             }
+            T gy[2][2][2];
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const T lo = phis[zbase[1 + c] + ybase[0] + xi[1 + a]];
                     const T hi = phis[zbase[1 + c] + ybase[3] + xi[1 + a]];
-                    T g0 = -(pc[c][1][a] - lo) * inv2d;
-                    T g1 = -(hi - pc[c][0][a]) * inv2d;
+                    gy[c][0][a] = -(xr[c][1][1 + a] - lo) * inv2d;
+                    gy[c][1][a] = -(hi - xr[c][0][1 + a]) * inv2d;
+                }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    T v0 = gy[c][b][0], v1 = gy[c][b][1];
                     if (carry) {
-                        g0 += out[c][0][a];
-                        g1 += out[c][1][a];
+                        v0 += out[c][b][0];
+                        v1 += out[c][b][1];
                     }
-                    if (wr[c][0][a]) acc[ncell + o[c][0][a]] = g0;
-                    if (wr[c][1][a]) acc[ncell + o[c][1][a]] = g1;
+                    put(acc + ncell, c, b, v0, v1);
                 }
         }
         // acc_z: planes zbase[0] and zbase[3]
@@ -216,20 +254,26 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(Lev
                 load_parent<T>(pacc + 2 * pn, pbase, P0, P01, q);
                 lerp_block<T>(q, out);
             }
+            T gz[2][2][2];
 #pragma unroll
             for (int b = 0; b < 2; ++b)
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const T lo = phis[zbase[0] + ybase[1 + b] + xi[1 + a]];
                     const T hi = phis[zbase[3] + ybase[1 + b] + xi[1 + a]];
-                    T g0 = -(pc[1][b][a] - lo) * inv2d;
-                    T g1 = -(hi - pc[0][b][a]) * inv2d;
+                    gz[0][b][a] = -(xr[1][b][1 + a] - lo) * inv2d;
+                    gz[1][b][a] = -(hi - xr[0][b][1 + a]) * inv2d;
+                }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    T v0 = gz[c][b][0], v1 = gz[c][b][1];
                     if (carry) {
-                        g0 += out[0][b][a];
-                        g1 += out[1][b][a];
+                        v0 += out[c][b][0];
+                        v1 += out[c][b][1];
                     }
-                    if (wr[0][b][a]) acc[2 * ncell + o[0][b][a]] = g0;
-                    if (wr[1][b][a]) acc[2 * ncell + o[1][b][a]] = g1;
+                    put(acc + 2 * ncell, c, b, v0, v1);
                 }
         }
     }
