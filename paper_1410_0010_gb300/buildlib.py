@@ -16,7 +16,13 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libapm.so")
 
-SOURCES = ["apm_api.cu", "k_green.cu", "k_deposit.cu", "k_fft.cu", "k_field.cu", "apm_noalloc.cu"]
+# (source, object, extra flags): k_fft_col.cu is compiled once per precision
+# and column pass
+SOURCES = [("apm_api.cu", "apm_api.o", []), ("k_green.cu", "k_green.o", []),
+           ("k_deposit.cu", "k_deposit.o", []), ("k_fft_x.cu", "k_fft_x.o", []),
+           ("k_field.cu", "k_field.o", []), ("apm_noalloc.cu", "apm_noalloc.o", [])] + [
+    ("k_fft_col.cu", f"k_fft_col_{p}_{m}.o", [f"-DAPM_COL_FP64={1 if p == 'f64' else 0}", f"-DAPM_COL_MODE={m}"])
+    for p in ("f32", "f64") for m in (0, 1, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
           "--expt-relaxed-constexpr"]
@@ -40,14 +46,15 @@ def build(force=False, verbose=False, extra=()):
     flags come from `extra` and the APM_NVCC_FLAGS environment variable."""
     os.makedirs(OUT_DIR, exist_ok=True)
     extra = list(extra) + os.environ.get("APM_NVCC_FLAGS", "").split()
-    headers = [os.path.join(CSRC, "apm_internal.cuh"), os.path.join(INCLUDE, "apm.h")]
+    headers = [os.path.join(CSRC, h) for h in sorted(os.listdir(CSRC)) if h.endswith(".cuh")]
+    headers.append(os.path.join(INCLUDE, "apm.h"))
     objs, jobs = [], []
-    for src in SOURCES:
+    for src, oname, flags in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(OUT_DIR, oname)
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
-            cmd = [nvcc(), *ARCH, *COMMON, *PER_FILE.get(src, []), *extra, "-c", path, "-o", obj]
+            cmd = [nvcc(), *ARCH, *COMMON, *PER_FILE.get(src, []), *flags, *extra, "-c", path, "-o", obj]
             jobs.append(cmd)
 
     def run(cmd):

@@ -594,6 +594,8 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
                 if (!fft_plan(g.M[j], f64 ? 8 : fft_max_radix(), pls[j])) return APM_E_UNSUPPORTED;
                 pls[j]->tw_off = twiddle(g.M[j]);
             }
+            fft_plan_reversed(g.fy, &g.iy);
+            fft_plan_reversed(g.fz, &g.iz);
             g.Hx = g.M[0] / 2 + 1;
             g.Hy2 = g.M[1] / 2 + 1;
             g.Hz2 = g.M[2] / 2 + 1;

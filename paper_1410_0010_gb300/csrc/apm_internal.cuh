@@ -102,6 +102,20 @@ inline bool fft_plan(int L, int max_radix, FftPlan1D* pl) {
     return true;
 }
 
+// The same transform with the radices in reverse order (the inverse column
+// transforms: the z pass's inverse starts with the radix its forward ends on).
+inline void fft_plan_reversed(const FftPlan1D& f, FftPlan1D* r) {
+    *r = f;
+    for (int st = 0; st < f.nst; ++st) r->radix[st] = f.radix[f.nst - 1 - st];
+    int Ns = 1;
+    for (int st = 0; st < r->nst; ++st) {
+        r->ns[st] = (unsigned short)Ns;
+        r->step[st] = (unsigned short)(r->L / (Ns * r->radix[st]));
+        r->magic[st] = Ns == 1 ? 0u : (unsigned)((0x100000000ULL + Ns - 1) / Ns);
+        Ns *= r->radix[st];
+    }
+}
+
 // Column-pass chunks carry (kx tile, line index of the other axis) as
 // (kt << 20) | other: other < 2^20, kt < 2^11.
 constexpr int kColOtherBits = 20;
@@ -124,6 +138,7 @@ struct GridDev {
     long long pstart[3];
     double delta;
     FftPlan1D fx, fy, fz;
+    FftPlan1D iy, iz;    // fy, fz with the radices reversed (inverse column transforms)
     long long tab_off;   // octant table offset (elements) in the table arenas
     long long wsA, wsB;  // workspace offsets (complex elements)
     long long cells_gmf; // G0 G1 G2

@@ -66,6 +66,8 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     if (!fft_plan(n, 16, &g.fx)) return APM_E_INVALID;   // n must be {2,3,5,7}-smooth
     g.fy = g.fx;
     g.fz = g.fx;
+    fft_plan_reversed(g.fx, &g.iy);
+    g.iz = g.iy;
     cudaStream_t s = (cudaStream_t)stream;
 
     // set-up, once per device, with that device current: the scratch address

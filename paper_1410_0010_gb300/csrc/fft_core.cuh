@@ -1,4 +1,4 @@
-// k_fft.cu -- batched 3-D FFT convolution of every grid of a level (Sec. 2.2,
+// fft_core.cuh -- batched 3-D FFT convolution of every grid of a level (Sec. 2.2,
 // Eq. PoissonFourier): the zero-padded GMF of each grid is transformed on its
 // M0 x M1 x M2 grid, multiplied by the Green's table and transformed back; only
 // the window of cells [-2, N+2) of the result is written.
@@ -20,10 +20,14 @@
 //        scaled by 1/(M0 M1 M2)                        -> phi_short[zw][yw][xw]
 // Zero-padded inputs are never read and outputs outside the window never
 // written.  Lines of the y/z passes are tiles of consecutive kx (coalesced).
+#pragma once
 #include <utility>
 
 #include "apm_internal.cuh"
 
+// The pass kernels and their building blocks, as templates; k_fft_x.cu and
+// k_fft_col.cu (once per precision and column pass) instantiate them, so the
+// instantiations compile in parallel.
 namespace apm {
 namespace {
 
@@ -430,7 +434,201 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
 //   yf (AX 1, MODE 0): in A[z][y][kx] (y < G1), out B[z][ky][kx]
 //   z  (AX 2, MODE 1): in B[z][ky][kx] (z < G2), out A[zw][ky][kx]
 //   yi (AX 1, MODE 2): in A[zw][ky][kx],         out B[zw][yw][kx]
-// smem: A, B (L x tx each, element-major), twiddles (L)
+// A CTA holds tx consecutive kx columns (its lines).  The first stage of a
+// transform reads its butterfly inputs straight from global memory (a warp
+// reads consecutive kx: coalesced) and the last stage writes straight to
+// global memory, so a transform of S stages makes S - 1 trips through shared
+// memory.  The z pass runs the forward transform with the plan of M2 and the
+// inverse with the reversed plan, whose first radix is the forward's last:
+// the forward's last butterfly, the table multiply and the inverse's first
+// butterfly act on the same elements in registers.
+// smem: two buffers of L x tx (element-major, line fastest), twiddles (L)
+
+// element i of this thread's line in a shared-memory buffer
+template <typename T> struct SmemIO {
+    C<T>* buf;
+    int tx, line;
+    __device__ C<T> ld(int i) const { return buf[i * tx + line]; }
+    __device__ void st(int i, C<T> v) const { buf[i * tx + line] = v; }
+};
+// element i of this thread's global line: in[i stride] for i < n (zero beyond:
+// the padding), nothing for a column outside [0, Hx)
+template <typename T> struct GlobalIn {
+    const C<T>* __restrict__ p;
+    long long stride;
+    int n;
+    bool live;
+    __device__ C<T> ld(int i) const { return (live && i < n) ? p[i * stride] : mk<T>(0, 0); }
+};
+// output element i of this thread's global line: window index w = (i - s0) mod L,
+// written as out[w stride] when w < n, and again at w + L when that is inside
+// the window too (a periodic root's window N + 4 exceeds M = N)
+template <typename T> struct GlobalOut {
+    C<T>* __restrict__ p;
+    long long stride;
+    int n, s0, L;
+    bool live;
+    __device__ void st(int i, C<T> v) const {
+        int w = i - s0;
+        if (w < 0) w += L;
+        if (!live) return;
+        if (w < n) p[w * stride] = v;
+        if (w + L < n) p[(w + L) * stride] = v;
+    }
+};
+
+// One Stockham stage of radix R = R1 R2 (see stage()) with the butterfly
+// inputs from `in` and the outputs to `out`; no barrier.
+template <typename T, int DIR, int R1, int R2, int NT, class IN, class OUT>
+__device__ __forceinline__ void stage_io(int L, int Ns, int step, unsigned magic, int lg,
+                                         const C<T>* __restrict__ tw, const IN& in, const OUT& out) {
+    constexpr int R = R1 * R2;
+    const int nb = L / R;
+    const int jstep = NT >> lg;
+    int j = threadIdx.x >> lg;
+    if (j >= nb) return;
+    int k = div_small(j, Ns, magic), jm = j - k * Ns;
+    const int dk = div_small(jstep, Ns, magic), djm = jstep - dk * Ns;
+    for (; j < nb; j += jstep) {
+        C<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in.ld(j + r * nb);
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = mul<T>(v[r], twid<T, DIR>(tw, jm * r * step));
+        }
+        if constexpr (R2 == 1) Dft<T, DIR, R1>::run(v);
+        else DftC<T, DIR, R1, R2>::run(v);
+        const int idx = k * Ns * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out.st(idx + r * Ns, v[r]);
+        jm += djm;
+        k += dk;
+        if (jm >= Ns) {
+            jm -= Ns;
+            ++k;
+        }
+    }
+}
+
+template <typename T, int DIR, int NT, class IN, class OUT>
+__device__ void stage_any(int R, int L, int Ns, int step, unsigned magic, int lg, const C<T>* tw,
+                          const IN& in, const OUT& out) {
+    switch (R) {
+        case 2: stage_io<T, DIR, 2, 1, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+        case 3: stage_io<T, DIR, 3, 1, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+        case 4: stage_io<T, DIR, 4, 1, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+        case 5: stage_io<T, DIR, 5, 1, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+        case 7: stage_io<T, DIR, 7, 1, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+        case 8: stage_io<T, DIR, 8, 1, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+        default:
+            if constexpr (sizeof(T) == 4) {
+                switch (R) {
+                    case 6: stage_io<T, DIR, 3, 2, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+                    case 9: stage_io<T, DIR, 3, 3, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+                    case 10: stage_io<T, DIR, 5, 2, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+                    case 12: stage_io<T, DIR, 3, 4, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+                    case 14: stage_io<T, DIR, 7, 2, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+                    case 15: stage_io<T, DIR, 5, 3, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+                    default: stage_io<T, DIR, 4, 4, NT>(L, Ns, step, magic, lg, tw, in, out); break;
+                }
+            }
+            break;
+    }
+}
+
+// Stages [s_first, s_last] of plan pl.  The first reads `in` (IN_SMEM: the
+// shared buffer *cur), the last writes `out` (OUT_SMEM: the shared buffer
+// *nxt); the stages between ping-pong through the shared buffers.  After every
+// stage that wrote shared memory: a barrier, and cur / nxt swap, so on return
+// *cur holds the last shared result.
+template <typename T, int DIR, int NT, bool IN_SMEM, bool OUT_SMEM, class IN, class OUT>
+__device__ void stages_io(const FftPlan1D& pl, int s_first, int s_last, int lg, const C<T>* tw,
+                          const IN& in, const OUT& out, C<T>*& cur, C<T>*& nxt, int tx, int line) {
+    const int L = pl.L;
+    for (int st = s_first; st <= s_last; ++st) {
+        const int R = pl.radix[st], Ns = pl.ns[st], step = pl.step[st];
+        const unsigned mg = pl.magic[st];
+        const bool gin = st == s_first && !IN_SMEM, gout = st == s_last && !OUT_SMEM;
+        const SmemIO<T> sin{cur, tx, line}, sout{nxt, tx, line};
+        if (gin && gout) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, in, out);
+        else if (gin) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, in, sout);
+        else if (gout) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, sin, out);
+        else stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, sin, sout);
+        if (!gout) {
+            __syncthreads();
+            C<T>* t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+    }
+}
+
+// The z pass's middle: the forward plan's last stage (radix R, Ns = L/R), the
+// table multiply of its outputs (element j + r L/R), and the reversed plan's
+// first stage (radix R, Ns = 1) on the same elements, writing j R + r.
+template <typename T, int R1, int R2, int NT, class IN, class OUT, class TAB>
+__device__ __forceinline__ void stage_fwd_tab_inv(int L, int step, int lg, const C<T>* __restrict__ tw,
+                                                  const IN& in, const OUT& out, const TAB& tabf) {
+    constexpr int R = R1 * R2;
+    const int nb = L / R;
+    const int jstep = NT >> lg;
+    for (int j = threadIdx.x >> lg; j < nb; j += jstep) {
+        C<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in.ld(j + r * nb);
+        if (nb > 1) {   // Ns = nb: the twiddle of butterfly j is exp(-2 pi i j r / L)
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = mul<T>(v[r], twid<T, -1>(tw, j * r * step));
+        }
+        if constexpr (R2 == 1) Dft<T, -1, R1>::run(v);
+        else DftC<T, -1, R1, R2>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T t = tabf(j + r * nb);
+            v[r] = mk<T>(v[r].x * t, v[r].y * t);
+        }
+        if constexpr (R2 == 1) Dft<T, 1, R1>::run(v);
+        else DftC<T, 1, R1, R2>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) out.st(j * R + r, v[r]);
+    }
+}
+
+template <typename T, int NT, class IN, class OUT, class TAB>
+__device__ void fwd_tab_inv_any(int R, int L, int step, int lg, const C<T>* tw, const IN& in, const OUT& out,
+                                const TAB& tabf) {
+    switch (R) {
+        case 2: stage_fwd_tab_inv<T, 2, 1, NT>(L, step, lg, tw, in, out, tabf); break;
+        case 3: stage_fwd_tab_inv<T, 3, 1, NT>(L, step, lg, tw, in, out, tabf); break;
+        case 4: stage_fwd_tab_inv<T, 4, 1, NT>(L, step, lg, tw, in, out, tabf); break;
+        case 5: stage_fwd_tab_inv<T, 5, 1, NT>(L, step, lg, tw, in, out, tabf); break;
+        case 7: stage_fwd_tab_inv<T, 7, 1, NT>(L, step, lg, tw, in, out, tabf); break;
+        case 8: stage_fwd_tab_inv<T, 8, 1, NT>(L, step, lg, tw, in, out, tabf); break;
+        default:
+            if constexpr (sizeof(T) == 4) {
+                switch (R) {
+                    case 6: stage_fwd_tab_inv<T, 3, 2, NT>(L, step, lg, tw, in, out, tabf); break;
+                    case 9: stage_fwd_tab_inv<T, 3, 3, NT>(L, step, lg, tw, in, out, tabf); break;
+                    case 10: stage_fwd_tab_inv<T, 5, 2, NT>(L, step, lg, tw, in, out, tabf); break;
+                    case 12: stage_fwd_tab_inv<T, 3, 4, NT>(L, step, lg, tw, in, out, tabf); break;
+                    case 14: stage_fwd_tab_inv<T, 7, 2, NT>(L, step, lg, tw, in, out, tabf); break;
+                    case 15: stage_fwd_tab_inv<T, 5, 3, NT>(L, step, lg, tw, in, out, tabf); break;
+                    default: stage_fwd_tab_inv<T, 4, 4, NT>(L, step, lg, tw, in, out, tabf); break;
+                }
+            }
+            break;
+    }
+}
+
+// table value of element kz of this thread's (ky, kx) column: T is even in
+// every component, stored as an octant
+template <typename T> struct TabCol {
+    const T* __restrict__ p;   // at (|ky|, kx)
+    int zst, L;
+    __device__ T operator()(int kz) const { return p[(kz <= L / 2 ? kz : L - kz) * zst]; }
+};
+
 template <typename T, int AX, int MODE, int NT>
 __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_col(const GridDev* __restrict__ grids,
                                                      const Chunk* __restrict__ chunks,
@@ -444,93 +642,60 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     const int lg = ilog2(tx);
     const int other = ch.tile & ((1 << kColOtherBits) - 1);    // z (yf), ky (z), zw (yi)
     const int kx0 = (ch.tile >> kColOtherBits) << lg;
-    const FftPlan1D& pl = AX == 1 ? g.fy : g.fz;
+    const FftPlan1D& pl = AX == 1 ? (MODE == 0 ? g.fy : g.iy) : g.fz;
     const int L = pl.L;
     const int M1 = g.M[1];
-    C<T>* s = smem_c<T>();
-    C<T>* s2 = s + L * tx;
-    C<T>* tw = s2 + L * tx;
+    C<T>* cur = smem_c<T>();
+    C<T>* nxt = cur + L * tx;
+    C<T>* tw = nxt + L * tx;
     load_twiddles<T, NT>(tw, tw_arena + pl.tw_off, L);
-
-    const C<T>* in;
-    long long in_base, in_stride;
-    int n_in;
-    if (AX == 1 && MODE == 0) {
-        in = wsA + g.wsA; n_in = g.G[1];
-        in_base = (long long)other * g.G[1] * Hx; in_stride = Hx;
-    } else if (AX == 2) {
-        in = wsB + g.wsB; n_in = g.G[2];
-        in_base = (long long)other * Hx; in_stride = (long long)M1 * Hx;
-    } else {
-        in = wsA + g.wsA; n_in = M1;
-        in_base = (long long)other * M1 * Hx; in_stride = Hx;
-    }
     const int line = threadIdx.x & (tx - 1);
-    const int istep = NT >> lg;
     const int kx = kx0 + line;
     const bool live = kx < Hx;
-    {
-        // element i of this thread's line from in[in_base + i in_stride + kx];
-        // elements [n_in, L) are the zero padding
-        int i = threadIdx.x >> lg;
-        C<T>* sp = s + i * tx + line;
-        const int sstep = istep * tx;
-        if (live) {
-            const C<T>* __restrict__ ip = in + (in_base + (long long)i * in_stride + kx);
-            const long long istride = (long long)istep * in_stride;
-            for (; i < n_in; i += istep, ip += istride, sp += sstep) *sp = *ip;
-        }
-        for (; i < L; i += istep, sp += sstep) *sp = mk<T>(0, 0);
-    }
-    __syncthreads();
-    if (MODE == 2) {
-        s = fft_lines<T, 1, NT>(s, s2, pl, lg, tx, tw);
+
+    GlobalIn<T> in;
+    GlobalOut<T> out;
+    in.live = out.live = live;
+    out.L = L;
+    if (AX == 1 && MODE == 0) {
+        in.p = wsA + (g.wsA + (long long)other * g.G[1] * Hx + kx); in.stride = Hx; in.n = g.G[1];
+        out.p = wsB + (g.wsB + (long long)other * M1 * Hx + kx); out.stride = Hx; out.n = M1; out.s0 = 0;
+    } else if (AX == 2) {
+        in.p = wsB + (g.wsB + (long long)other * Hx + kx); in.stride = (long long)M1 * Hx; in.n = g.G[2];
+        out.p = wsA + (g.wsA + (long long)other * Hx + kx); out.stride = (long long)M1 * Hx;
+        out.n = g.W[2]; out.s0 = g.s0[2];
     } else {
-        s = fft_lines<T, -1, NT>(s, s2, pl, lg, tx, tw);
+        in.p = wsA + (g.wsA + (long long)other * M1 * Hx + kx); in.stride = Hx; in.n = M1;
+        out.p = wsB + (g.wsB + (long long)other * g.W[1] * Hx + kx); out.stride = Hx;
+        out.n = g.W[1]; out.s0 = g.s0[1];
     }
-    if (MODE == 1) {
-        // phi-hat = T(kappa) rho-hat; the table is even in every component
-        s2 = (s == smem_c<T>()) ? s + L * tx : smem_c<T>();
+    __syncthreads();   // twiddles
+    if (MODE == 0) {
+        stages_io<T, -1, NT, false, false>(pl, 0, pl.nst - 1, lg, tw, in, out, cur, nxt, tx, line);
+    } else if (MODE == 2) {
+        stages_io<T, 1, NT, false, false>(pl, 0, pl.nst - 1, lg, tw, in, out, cur, nxt, tx, line);
+    } else {
+        // phi-hat = T(kappa) rho-hat between the forward and the inverse transform
+        const FftPlan1D& ipl = g.iz;
         const int ky = other;
         const int fy = ky <= M1 / 2 ? ky : M1 - ky;
-        const T* __restrict__ tb = tab + (g.tab_off + (long long)fy * Hx + kx);
-        const int zst = g.Hy2 * Hx;     // the octant table holds < 2^31 entries
-        if (live) {
-            for (int kz = threadIdx.x >> lg; kz < L; kz += istep) {
-                const int fz = kz <= L / 2 ? kz : L - kz;
-                const T t = tb[fz * zst];
-                C<T> v = s[kz * tx + line];
-                s[kz * tx + line] = mk<T>(v.x * t, v.y * t);
-            }
-        }
-        __syncthreads();
-        s = fft_lines<T, 1, NT>(s, s2, pl, lg, tx, tw);
-    }
-    // store
-    C<T>* out;
-    long long out_base, out_stride;
-    int n_out, s0;
-    if (AX == 1 && MODE == 0) {
-        out = wsB + g.wsB; n_out = M1; s0 = 0;
-        out_base = (long long)other * M1 * Hx; out_stride = Hx;
-    } else if (AX == 2) {
-        out = wsA + g.wsA; n_out = g.W[2]; s0 = g.s0[2];
-        out_base = (long long)other * Hx; out_stride = (long long)M1 * Hx;
-    } else {
-        out = wsB + g.wsB; n_out = g.W[1]; s0 = g.s0[1];
-        out_base = (long long)other * g.W[1] * Hx; out_stride = Hx;
-    }
-    if (live) {
-        int o = threadIdx.x >> lg;
-        int i = s0 + o, di = istep;     // (s0 + o) mod L and istep mod L
-        while (i >= L) i -= L;
-        while (di >= L) di -= L;
-        C<T>* __restrict__ op = out + (out_base + (long long)o * out_stride + kx);
-        const long long ostride = (long long)istep * out_stride;
-        for (; o < n_out; o += istep, op += ostride) {
-            *op = s[i * tx + line];
-            i += di;
-            if (i >= L) i -= L;
+        TabCol<T> tabf;
+        tabf.p = tab + (g.tab_off + (long long)fy * Hx + kx);
+        tabf.zst = g.Hy2 * Hx;     // the octant table holds < 2^31 entries
+        tabf.L = L;
+        const int n = pl.nst;
+        const int R = pl.radix[n - 1];
+        if (n == 1) {
+            fwd_tab_inv_any<T, NT>(R, L, pl.step[0], lg, tw, in, out, tabf);
+        } else {
+            stages_io<T, -1, NT, false, true>(pl, 0, n - 2, lg, tw, in, out, cur, nxt, tx, line);
+            fwd_tab_inv_any<T, NT>(R, L, pl.step[n - 1], lg, tw, SmemIO<T>{cur, tx, line},
+                                   SmemIO<T>{nxt, tx, line}, tabf);
+            __syncthreads();
+            C<T>* t = cur;
+            cur = nxt;
+            nxt = t;
+            stages_io<T, 1, NT, true, false>(ipl, 1, n - 1, lg, tw, in, out, cur, nxt, tx, line);
         }
     }
 }
@@ -605,73 +770,4 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
 }
 
 }  // namespace
-
-// Allows every pass kernel up to 200 KB of dynamic shared memory (above the
-// 48 KB default).
-cudaError_t fft_configure() {
-    const int lim = kFftSmemLimit;
-    const void* fns[] = {
-#define APM_FNS(T, NT)                                                                          \
-    (const void*)k_xf<T, NT>, (const void*)k_col<T, 1, 0, NT>, (const void*)k_col<T, 2, 1, NT>, \
-        (const void*)k_col<T, 1, 2, NT>, (const void*)k_xi<T, NT>,
-        APM_FNS(float, 128) APM_FNS(float, 256) APM_FNS(double, 128) APM_FNS(double, 256)
-#undef APM_FNS
-    };
-    for (const void* f : fns) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-// The CTA size is a template parameter of the pass kernels (128 or 256 threads).
-template <typename T>
-cudaError_t launch_fft_xf(const FftArgs& a, const int64_t* const* gmf, cudaStream_t s) {
-    if (a.n_chunks <= 0) return cudaSuccess;
-    if (a.threads == 128)
-        k_xf<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F);
-    else
-        k_xf<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F);
-    return cudaGetLastError();
-}
-
-template <typename T, int AX, int MODE>
-cudaError_t launch_col(const FftArgs& a, cudaStream_t s) {
-    if (a.n_chunks <= 0) return cudaSuccess;
-    if (a.threads == 128)
-        k_col<T, AX, MODE, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
-                                                               (const T*)a.tab, (C<T>*)a.wsA, (C<T>*)a.wsB);
-    else
-        k_col<T, AX, MODE, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw,
-                                                               (const T*)a.tab, (C<T>*)a.wsA, (C<T>*)a.wsB);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_fft_yf(const FftArgs& a, cudaStream_t s) { return launch_col<T, 1, 0>(a, s); }
-template <typename T>
-cudaError_t launch_fft_z(const FftArgs& a, cudaStream_t s) { return launch_col<T, 2, 1>(a, s); }
-template <typename T>
-cudaError_t launch_fft_yi(const FftArgs& a, cudaStream_t s) { return launch_col<T, 1, 2>(a, s); }
-
-template <typename T>
-cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s) {
-    if (a.n_chunks <= 0) return cudaSuccess;
-    if (a.threads == 128)
-        k_xi<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis);
-    else
-        k_xi<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis);
-    return cudaGetLastError();
-}
-
-#define APM_INST(T)                                                                       \
-    template cudaError_t launch_fft_xf<T>(const FftArgs&, const int64_t* const*, cudaStream_t); \
-    template cudaError_t launch_fft_yf<T>(const FftArgs&, cudaStream_t);                   \
-    template cudaError_t launch_fft_z<T>(const FftArgs&, cudaStream_t);                    \
-    template cudaError_t launch_fft_yi<T>(const FftArgs&, cudaStream_t);                   \
-    template cudaError_t launch_fft_xi<T>(const FftArgs&, void* const*, cudaStream_t);
-APM_INST(float)
-APM_INST(double)
-#undef APM_INST
-
 }  // namespace apm
