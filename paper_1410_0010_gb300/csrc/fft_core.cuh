@@ -368,67 +368,6 @@ template <> __device__ __forceinline__ double pow2_neg<double>(int F) {
     return __longlong_as_double((long long)(1023 - F) << 52);
 }
 
-// ---- xf: GMF rows -> half spectra along x ----------------------------------
-// smem: A, B (M0 x (np+1) each, element-major, padded), twiddles (M0)
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_xf(const GridDev* __restrict__ grids,
-                                                    const Chunk* __restrict__ chunks,
-                                                    const int64_t* const* __restrict__ gmf,
-                                                    const C<T>* __restrict__ tw_arena,
-                                                    C<T>* __restrict__ wsA, int F) {
-    const Chunk ch = chunks[blockIdx.x];
-    const GridDev& g = grids[ch.grid];
-    const int M0 = g.M[0], G0 = g.G[0], Hx = g.Hx, np = g.lines[kPassXf], lg = ilog2(np), es = np + 1;
-    C<T>* s = smem_c<T>();
-    C<T>* s2 = s + M0 * es;
-    C<T>* tw = s2 + M0 * es;
-    // this CTA's rows: r_first + [0, nr), nr <= 2 np; 32-bit offsets from there
-    const long long r_first = 2LL * ch.tile * np;
-    const int nr = (int)min(2LL * np, (long long)g.G[1] * g.G[2] - r_first);
-    const int64_t* __restrict__ in = gmf[ch.grid] + r_first * G0;
-    load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
-    const T scale = pow2_neg<T>(F);
-    // rows r0 = 2p, r1 = 2p + 1 packed as one complex line p; x fastest over threads
-    {
-        int p = 0, x = threadIdx.x;
-        while (x >= M0) { x -= M0; ++p; }
-        const int dp = NT / M0, dx = NT % M0;
-        for (; p < np; ) {
-            const int q0 = 2 * p;
-            T a = 0, b = 0;
-            if (x < G0) {
-                if (q0 < nr) a = fixed_to_real<T>(in[q0 * G0 + x], scale);
-                if (q0 + 1 < nr) b = fixed_to_real<T>(in[(q0 + 1) * G0 + x], scale);
-            }
-            s[x * es + p] = mk<T>(a, b);
-            x += dx;
-            p += dp;
-            if (x >= M0) { x -= M0; ++p; }
-        }
-    }
-    __syncthreads();
-    s = fft_lines<T, -1, NT>(s, s2, g.fx, lg, es, tw);
-    // separate the two real rows: A_k = (Z_k + conj Z_{M-k}) / 2, B_k = (Z_k - conj Z_{M-k}) / 2i
-    C<T>* out = wsA + (g.wsA + r_first * Hx);
-    {
-        int p = 0, k = threadIdx.x;
-        while (k >= Hx) { k -= Hx; ++p; }
-        const int dp = NT / Hx, dk = NT % Hx;
-        for (; p < np; ) {
-            const int q0 = 2 * p;
-            if (q0 < nr) {
-                C<T> z = s[k * es + p];
-                C<T> zm = s[(k == 0 ? 0 : M0 - k) * es + p];
-                out[q0 * Hx + k] = mk<T>((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
-                if (q0 + 1 < nr) out[(q0 + 1) * Hx + k] = mk<T>((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
-            }
-            k += dk;
-            p += dp;
-            if (k >= Hx) { k -= Hx; ++p; }
-        }
-    }
-}
-
 // ---- column passes -----------------------------------------------------------
 // AX = 1 (y) or 2 (z).  MODE 0: forward only; 1: forward, table, inverse; 2: inverse only.
 //   yf (AX 1, MODE 0): in A[z][y][kx] (y < G1), out B[z][ky][kx]
@@ -551,10 +490,19 @@ __device__ void stages_io(const FftPlan1D& pl, int s_first, int s_last, int lg, 
         const unsigned mg = pl.magic[st];
         const bool gin = st == s_first && !IN_SMEM, gout = st == s_last && !OUT_SMEM;
         const SmemIO<T> sin{cur, tx, line}, sout{nxt, tx, line};
-        if (gin && gout) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, in, out);
-        else if (gin) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, in, sout);
-        else if (gout) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, sin, out);
-        else stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, sin, sout);
+        if (gin) {
+            if constexpr (!IN_SMEM) {
+                if (gout) {
+                    if constexpr (!OUT_SMEM) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, in, out);
+                } else {
+                    stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, in, sout);
+                }
+            }
+        } else if (gout) {
+            if constexpr (!OUT_SMEM) stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, sin, out);
+        } else {
+            stage_any<T, DIR, NT>(R, L, Ns, step, mg, lg, tw, sin, sout);
+        }
         if (!gout) {
             __syncthreads();
             C<T>* t = cur;
@@ -700,8 +648,110 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     }
 }
 
-// ---- xi: half spectra -> real rows of the window -------------------------------
-// smem: A, B (M0 x (np+1) each), twiddles (M0)
+// ---- x passes ------------------------------------------------------------------
+// A CTA holds np complex lines, each packing two real rows (2p, 2p+1) of the
+// grid (two-for-one real transforms); the same thread mapping as the column
+// passes (line fastest), so a warp reads 32 / np consecutive x of each of its
+// rows.  smem: two buffers of M0 x (np+1) (element-major, padded), twiddles (M0)
+
+// xi input: Z_k = A_k + i B_k, A, B the half spectra of rows 2p, 2p+1 extended
+// by Hermitian symmetry (A_{M-k} = conj A_k)
+template <typename T> struct XiIn {
+    const C<T>* __restrict__ p;      // row 2 line of this CTA
+    int Hx, M0, nr0, nr1;
+    __device__ C<T> ld(int k) const {
+        const int kk = k < Hx ? k : M0 - k;
+        C<T> a = mk<T>(0, 0), b = mk<T>(0, 0);
+        if (nr0) a = p[kk];
+        if (nr1) b = p[Hx + kk];
+        if (k >= Hx) {
+            a.y = -a.y;
+            b.y = -b.y;
+        }
+        return mk<T>(a.x - b.y, a.y + b.x);
+    }
+};
+// xi output: element i of line p is (row 2p + i row 2p+1) at window cell
+// w = (i - s0) mod M0 (and w + M0 when inside the window), times 1/(M0 M1 M2)
+template <typename T> struct XiOut {
+    T* __restrict__ p;               // row 2 line of this CTA
+    int W0, s0, M0, nr0, nr1;
+    T norm;
+    __device__ void st(int i, C<T> v) const {
+        int w = i - s0;
+        if (w < 0) w += M0;
+        for (; w < W0; w += M0) {
+            if (nr0) p[w] = v.x * norm;
+            if (nr1) p[W0 + w] = v.y * norm;
+        }
+    }
+};
+
+// xf: GMF rows -> half spectra along x, A[z][y][kx]
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_xf(const GridDev* __restrict__ grids,
+                                                    const Chunk* __restrict__ chunks,
+                                                    const int64_t* const* __restrict__ gmf,
+                                                    const C<T>* __restrict__ tw_arena,
+                                                    C<T>* __restrict__ wsA, int F) {
+    const Chunk ch = chunks[blockIdx.x];
+    const GridDev& g = grids[ch.grid];
+    const int M0 = g.M[0], G0 = g.G[0], Hx = g.Hx, np = g.lines[kPassXf], lg = ilog2(np), es = np + 1;
+    C<T>* cur = smem_c<T>();
+    C<T>* nxt = cur + M0 * es;
+    C<T>* tw = nxt + M0 * es;
+    // this CTA's rows: r_first + [0, nr), nr <= 2 np; 32-bit offsets from there
+    const long long r_first = 2LL * ch.tile * np;
+    const int nr = (int)min(2LL * np, (long long)g.G[1] * g.G[2] - r_first);
+    load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
+    const int line = threadIdx.x & (np - 1);
+    // rows staged with x fastest over threads (full-sector int64 reads; a
+    // line-fastest first stage would read a fraction of each sector)
+    {
+        const int64_t* __restrict__ in = gmf[ch.grid] + r_first * G0;
+        const T scale = pow2_neg<T>(F);
+        int p = 0, x = threadIdx.x;
+        while (x >= M0) { x -= M0; ++p; }
+        const int dp = NT / M0, dx = NT % M0;
+        for (; p < np; ) {
+            const int q0 = 2 * p;
+            T a = 0, b = 0;
+            if (x < G0) {
+                if (q0 < nr) a = fixed_to_real<T>(in[q0 * G0 + x], scale);
+                if (q0 + 1 < nr) b = fixed_to_real<T>(in[(q0 + 1) * G0 + x], scale);
+            }
+            cur[x * es + p] = mk<T>(a, b);
+            x += dx;
+            p += dp;
+            if (x >= M0) { x -= M0; ++p; }
+        }
+    }
+    __syncthreads();
+    const SmemIO<T> none{nullptr, 0, 0};
+    stages_io<T, -1, NT, true, true>(g.fx, 0, g.fx.nst - 1, lg, tw, none, none, cur, nxt, es, line);
+    // separate the two real rows: A_k = (Z_k + conj Z_{M-k}) / 2, B_k = (Z_k - conj Z_{M-k}) / 2i
+    C<T>* out = wsA + (g.wsA + r_first * Hx);
+    const C<T>* s = cur;
+    {
+        int p = 0, k = threadIdx.x;
+        while (k >= Hx) { k -= Hx; ++p; }
+        const int dp = NT / Hx, dk = NT % Hx;
+        for (; p < np; ) {
+            const int q0 = 2 * p;
+            if (q0 < nr) {
+                C<T> z = s[k * es + p];
+                C<T> zm = s[(k == 0 ? 0 : M0 - k) * es + p];
+                out[q0 * Hx + k] = mk<T>((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
+                if (q0 + 1 < nr) out[(q0 + 1) * Hx + k] = mk<T>((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
+            }
+            k += dk;
+            p += dp;
+            if (k >= Hx) { k -= Hx; ++p; }
+        }
+    }
+}
+
+// xi: half spectra -> real rows of the window, C2R two rows per complex line
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_xi(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
@@ -711,62 +761,29 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
     const int M0 = g.M[0], Hx = g.Hx, np = g.lines[kPassXi], W0 = g.W[0], lg = ilog2(np), es = np + 1;
-    C<T>* s = smem_c<T>();
-    C<T>* s2 = s + M0 * es;
-    C<T>* tw = s2 + M0 * es;
+    C<T>* cur = smem_c<T>();
+    C<T>* nxt = cur + M0 * es;
+    C<T>* tw = nxt + M0 * es;
     const long long r_first = 2LL * ch.tile * np;
     const int nr = (int)min(2LL * np, (long long)g.W[1] * g.W[2] - r_first);
-    const C<T>* __restrict__ in = wsB + (g.wsB + r_first * Hx);
     load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
-    // Z_k = A_k + i B_k with A, B extended by Hermitian symmetry
-    {
-        int p = 0, k = threadIdx.x;
-        while (k >= M0) { k -= M0; ++p; }
-        const int dp = NT / M0, dk = NT % M0;
-        for (; p < np; ) {
-            const int q0 = 2 * p;
-            int kk = k < Hx ? k : M0 - k;
-            C<T> a = mk<T>(0, 0), b = mk<T>(0, 0);
-            if (q0 < nr) a = in[q0 * Hx + kk];
-            if (q0 + 1 < nr) b = in[(q0 + 1) * Hx + kk];
-            if (k >= Hx) { a.y = -a.y; b.y = -b.y; }
-            s[k * es + p] = mk<T>(a.x - b.y, a.y + b.x);
-            k += dk;
-            p += dp;
-            if (k >= M0) { k -= M0; ++p; }
-        }
-    }
+    const int line = threadIdx.x & (np - 1);
+    XiIn<T> in;
+    in.p = wsB + (g.wsB + (r_first + 2 * line) * Hx);
+    in.Hx = Hx;
+    in.M0 = M0;
+    in.nr0 = 2 * line < nr;
+    in.nr1 = 2 * line + 1 < nr;
+    XiOut<T> out;
+    out.p = reinterpret_cast<T*>(phis[ch.grid]) + (r_first + 2 * line) * W0;
+    out.W0 = W0;
+    out.s0 = g.s0[0];
+    out.M0 = M0;
+    out.nr0 = in.nr0;
+    out.nr1 = in.nr1;
+    out.norm = (T)g.inv_m3;
     __syncthreads();
-    s = fft_lines<T, 1, NT>(s, s2, g.fx, lg, es, tw);
-    const T norm = (T)g.inv_m3;
-    T* out = reinterpret_cast<T*>(phis[ch.grid]) + r_first * W0;
-    {
-        int p = 0, xw = threadIdx.x;
-        while (xw >= W0) { xw -= W0; ++p; }
-        const int dp = NT / W0, dx = NT % W0;
-        int x = g.s0[0] + xw;             // (s0 + xw) mod M0, stepped with xw
-        while (x >= M0) x -= M0;
-        int dxm = dx;
-        while (dxm >= M0) dxm -= M0;
-        for (; p < np; ) {
-            const int q0 = 2 * p;
-            if (q0 < nr) {
-                C<T> z = s[x * es + p];
-                out[q0 * W0 + xw] = z.x * norm;
-                if (q0 + 1 < nr) out[(q0 + 1) * W0 + xw] = z.y * norm;
-            }
-            xw += dx;
-            p += dp;
-            x += dxm;
-            if (x >= M0) x -= M0;
-            if (xw >= W0) {
-                xw -= W0;
-                ++p;
-                x -= W0 % M0;
-                if (x < 0) x += M0;
-            }
-        }
-    }
+    stages_io<T, 1, NT, false, false>(g.fx, 0, g.fx.nst - 1, lg, tw, in, out, cur, nxt, es, line);
 }
 
 }  // namespace
