@@ -134,6 +134,39 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
     return out
 
 
+def cufft_convolution_ms(solver, levels, dev, steps, timed):
+    """The same convolutions done with cuFFT (torch.fft), for comparison: per
+    level, every grid's FP32 field on its M grid (batched by M shape),
+    forward R2C, multiplied by a real half-spectrum table, inverse C2R.  No
+    zero-padding pruning or windowing; the table is a stand-in of the right
+    shape.  Returns {"ms_per_step": ..., "batches": [...]}."""
+    import torch
+    groups = {}
+    for lev in levels:
+        for gi in solver.level_grids[lev]:
+            M = tuple(solver.info[gi]["fft"])
+            groups[M] = groups.get(M, 0) + 1
+    bufs = []
+    for M, cnt in groups.items():
+        x = torch.rand((cnt, M[2], M[1], M[0]), dtype=torch.float32, device=dev)
+        t = torch.rand((M[2], M[1], M[0] // 2 + 1), dtype=torch.float32, device=dev)
+        bufs.append((x, t))
+
+    def conv():
+        for x, t in bufs:
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)) * t, s=x.shape[1:], dim=(1, 2, 3))
+            del y
+
+    for _ in range(2):
+        conv()
+    ms = timed(conv, max(steps, 1))
+    out = {"ms_per_step": ms, "batches": [{"M": list(M), "grids": c} for M, c in groups.items()],
+           "library": "cuFFT via torch.fft (R2C, multiply, C2R; full M grids)"}
+    del bufs
+    torch.cuda.empty_cache()
+    return out
+
+
 def kernel_source_hash():
     """sha256 over the CUDA sources of the library (file names and contents, in
     name order): identifies the kernels a DRAM-traffic capture was taken on."""
@@ -343,7 +376,7 @@ def run_apm(args):
     def e2e_step():
         for k in dparts:
             dparts[k].copy_(host[k], non_blocking=True)
-        step32()
+        run()                     # the captured step (same launches as step32)
         hout.copy_(pacc, non_blocking=True)
 
     e2e_ms = timed(e2e_step, args.steps)
@@ -377,6 +410,14 @@ def run_apm(args):
         fp64 = {"value": job_rate(ranks, cells, ms64), "ms_per_step": ms64,
                 "fp32_speedup": ms64 / ms, "fp32_rel_l2_vs_fp64": {"phi_finest": e_phi, "pacc": e_pacc}}
         s64.close()
+
+    # ---------------- cuFFT comparison (context only: cuFFT is not on the product path)
+    cufft = None
+    if not args.no_cufft:
+        cufft = cufft_convolution_ms(s32, levels, dev, args.steps, timed)
+        ours = sum(prof[k][1] for k in ("fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv")
+                   if k in prof) / max(args.steps, 1)
+        cufft["ours_ms_per_step"] = ours
 
     # ---------------- roofline of the dominant kernel
     hbm, peak_src = peaks()
@@ -429,6 +470,7 @@ def run_apm(args):
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "fp64": fp64,
+        "cufft_compare": cufft,
         "clocks": clk,
     }
     s32.close()
@@ -449,6 +491,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
