@@ -266,9 +266,9 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
         const GridDev& g = L.hg[k];
         const int len = (q == kPassXf || q == kPassXi) ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
         int lines = fft_pass_lines(q, len, budget, f64);
-        while (lines > 1 && fft_pass_smem(q, len, lines, csz) > (size_t)kFftSmemLimit) lines /= 2;
+        while (lines > 1 && fft_pass_smem(q, len, lines, csz, g.G[0]) > (size_t)kFftSmemLimit) lines /= 2;
         P.lines[k] = lines;
-        P.smem = std::max(P.smem, fft_pass_smem(q, len, lines, csz));
+        P.smem = std::max(P.smem, fft_pass_smem(q, len, lines, csz, g.G[0]));
         if (q == kPassXf || q == kPassXi) {
             const long long rows = q == kPassXf ? (long long)g.G[1] * g.G[2] : (long long)g.W[1] * g.W[2];
             const long long n = ((rows + 1) / 2 + lines - 1) / lines;
@@ -308,6 +308,7 @@ cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void*
     a.n_chunks = P.n;
     a.smem = P.smem;
     a.threads = P.threads;
+    a.status = c->d_status;
     switch (q) {
         case kPassXf:
             return f64 ? launch_fft_xf<double>(a, (const int64_t* const*)d_gmf, s)

@@ -38,10 +38,17 @@ inline int fft_pass_lines(int pass, int L, int budget, bool f64) {
     if (pass == kPassXf || pass == kPassXi) return std::min(32, v);
     return std::min(32, std::max(f64 ? 2 : 4, v));
 }
+// bytes of the x-forward pass's int64 row staging area (2 lines rows of G0
+// cells, rounded to 128 bytes) plus its mbarrier
+__host__ __device__ inline size_t fft_xf_stage_bytes(int lines, int G0) {
+    return ((size_t)2 * lines * G0 * 8 + 127) / 128 * 128 + 128;
+}
 // dynamic shared memory of a pass CTA: two buffers plus the twiddles (the x
-// passes pad each element row to lines + 1)
-inline size_t fft_pass_smem(int pass, int L, int lines, size_t csz) {
-    if (pass == kPassXf || pass == kPassXi) return (size_t)(2 * L * (lines + 1) + L) * csz;
+// passes pad each element row to lines + 1); the x-forward pass also stages
+// its GMF rows (G0: the GMF row length)
+inline size_t fft_pass_smem(int pass, int L, int lines, size_t csz, int G0 = 0) {
+    if (pass == kPassXf) return (size_t)(2 * L * (lines + 1) + L) * csz + fft_xf_stage_bytes(lines, G0);
+    if (pass == kPassXi) return (size_t)(2 * L * (lines + 1) + L) * csz;
     return (size_t)(2 * L * lines + L) * csz;
 }
 constexpr int kMaxFft = 1024;       // longest supported transform
@@ -331,6 +338,44 @@ __device__ __forceinline__ unsigned long long wmul63(unsigned long long a, unsig
     return (hi << 1) | (lo2 >> 63);
 }
 
+// ---- bulk asynchronous copies (TMA engine, no tensor map) and mbarriers ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// makes the initialised barrier visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned), completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// waits for phase `parity` of `bar` at most `limit` polls; false when it ran out
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+constexpr unsigned kWaitPolls = 1u << 22;   // each poll suspends for at most a short hardware interval
+
 // wmul63 for a < 2^32: with b = bh 2^32 + bl, (a b + 2^62) >> 63 equals
 // (a bh + ((a bl) >> 32) + 2^30) >> 31 (the low 32 bits of a bl cannot carry
 // into the result); two 32 x 32 -> 64 products
@@ -382,6 +427,7 @@ struct FftArgs {
     int F;
     size_t smem;
     int threads;           // threads per CTA: 128 or 256
+    unsigned* status;      // device status word (bounded waits that ran out), or null
 };
 cudaError_t fft_configure();
 template <typename T>

@@ -168,7 +168,8 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     a.wsB = wsB;
     a.F = mass_frac_bits;
     a.threads = kFftThreads;
-    const size_t smem_rows = fft_pass_smem(kPassXf, n, g.lines[kPassXf], sizeof(float2));
+    a.status = nullptr;   // a wait that runs out leaves the output unfinished, unreported
+    const size_t smem_rows = fft_pass_smem(kPassXf, n, g.lines[kPassXf], sizeof(float2), n);
     const size_t smem_cols = fft_pass_smem(kPassYf, n, g.lines[kPassYf], sizeof(float2));
     a.n_chunks = n_xf;
     a.smem = smem_rows;

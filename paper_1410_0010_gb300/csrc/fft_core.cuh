@@ -687,29 +687,59 @@ template <typename T> struct XiOut {
     }
 };
 
-// xf: GMF rows -> half spectra along x, A[z][y][kx]
+// xf: GMF rows -> half spectra along x, A[z][y][kx].  The CTA's 2 np GMF rows
+// are one contiguous range of int64; when G0 is even and the range 16-byte
+// aligned, one bulk asynchronous copy (TMA engine) stages it in shared memory
+// while the twiddles load, completing on an mbarrier (bounded wait; a wait
+// that runs out sets the status word's timeout bit and the CTA returns).
+// Otherwise every thread loads its cells.  The cells are then converted and
+// packed x-fastest.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_xf(const GridDev* __restrict__ grids,
                                                     const Chunk* __restrict__ chunks,
                                                     const int64_t* const* __restrict__ gmf,
                                                     const C<T>* __restrict__ tw_arena,
-                                                    C<T>* __restrict__ wsA, int F) {
+                                                    C<T>* __restrict__ wsA, int F,
+                                                    unsigned* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_xf[];
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
     const int M0 = g.M[0], G0 = g.G[0], Hx = g.Hx, np = g.lines[kPassXf], lg = ilog2(np), es = np + 1;
-    C<T>* cur = smem_c<T>();
+    const size_t stage = fft_xf_stage_bytes(np, G0);
+    int64_t* rows = reinterpret_cast<int64_t*>(smem_xf);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_xf + stage - 128);
+    C<T>* cur = reinterpret_cast<C<T>*>(smem_xf + stage);
     C<T>* nxt = cur + M0 * es;
     C<T>* tw = nxt + M0 * es;
     // this CTA's rows: r_first + [0, nr), nr <= 2 np; 32-bit offsets from there
     const long long r_first = 2LL * ch.tile * np;
     const int nr = (int)min(2LL * np, (long long)g.G[1] * g.G[2] - r_first);
+    const int64_t* __restrict__ in = gmf[ch.grid] + r_first * G0;
+    const bool bulk = !(G0 & 1) && !(reinterpret_cast<size_t>(in) & 15);
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            fence_proxy_async_smem();
+            const unsigned bytes = (unsigned)nr * (unsigned)G0 * 8u;
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(rows, in, bytes, bar);
+        }
+    }
     load_twiddles<T, NT>(tw, tw_arena + g.fx.tw_off, M0);
     const int line = threadIdx.x & (np - 1);
-    // rows staged with x fastest over threads (full-sector int64 reads; a
-    // line-fastest first stage would read a fraction of each sector)
+    if (bulk) {
+        __syncthreads();   // the barrier's initialisation is visible to every thread
+        const bool ok = mbar_wait_bounded(bar, 0, kWaitPolls);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && status) atomicOr(status, kStTimeout);
+            mbar_wait_bounded(bar, 0, kWaitPolls);   // the copy may still land: wait for it once more
+            return;
+        }
+    }
+    // cells packed x-fastest over threads: rows 2p, 2p+1 are complex line p
     {
-        const int64_t* __restrict__ in = gmf[ch.grid] + r_first * G0;
         const T scale = pow2_neg<T>(F);
+        const int64_t* src = bulk ? rows : in;
         int p = 0, x = threadIdx.x;
         while (x >= M0) { x -= M0; ++p; }
         const int dp = NT / M0, dx = NT % M0;
@@ -717,8 +747,8 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
             const int q0 = 2 * p;
             T a = 0, b = 0;
             if (x < G0) {
-                if (q0 < nr) a = fixed_to_real<T>(in[q0 * G0 + x], scale);
-                if (q0 + 1 < nr) b = fixed_to_real<T>(in[(q0 + 1) * G0 + x], scale);
+                if (q0 < nr) a = fixed_to_real<T>(src[q0 * G0 + x], scale);
+                if (q0 + 1 < nr) b = fixed_to_real<T>(src[(q0 + 1) * G0 + x], scale);
             }
             cur[x * es + p] = mk<T>(a, b);
             x += dx;

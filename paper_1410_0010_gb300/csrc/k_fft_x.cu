@@ -37,9 +37,11 @@ template <typename T>
 cudaError_t launch_fft_xf(const FftArgs& a, const int64_t* const* gmf, cudaStream_t s) {
     if (a.n_chunks <= 0) return cudaSuccess;
     if (a.threads == 128)
-        k_xf<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F);
+        k_xf<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F,
+                                                      a.status);
     else
-        k_xf<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F);
+        k_xf<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F,
+                                                      a.status);
     return cudaGetLastError();
 }
 
