@@ -93,6 +93,14 @@ bool fault_alloc() {
     return f && std::strcmp(f, "alloc") == 0;
 }
 
+// APM_FAULT_INJECT=wait: the x-forward pass's bulk copy waits for 16 bytes
+// more than it copies, so its bounded mbarrier wait runs out (tests the
+// timeout path; nothing faults)
+bool fault_wait() {
+    const char* f = std::getenv("APM_FAULT_INJECT");
+    return f && std::strcmp(f, "wait") == 0;
+}
+
 apm_status dmalloc(apm_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
@@ -309,6 +317,7 @@ cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void*
     a.smem = P.smem;
     a.threads = P.threads;
     a.status = c->d_status;
+    a.inject_wait = fault_wait() ? 1 : 0;
     switch (q) {
         case kPassXf:
             return f64 ? launch_fft_xf<double>(a, (const int64_t* const*)d_gmf, s)

@@ -358,23 +358,27 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// one poll of phase `parity`; a thread may be suspended up to kWaitHintNs
+// nanoseconds inside it
+constexpr unsigned kWaitHintNs = 1000;
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
         : "memory");
     return ok != 0;
 }
-// waits for phase `parity` of `bar` at most `limit` polls; false when it ran out
+// waits for phase `parity` of `bar` at most `limit` polls (about a second in
+// all); false when it ran out
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned limit) {
     for (unsigned it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
-constexpr unsigned kWaitPolls = 1u << 22;   // each poll suspends for at most a short hardware interval
+constexpr unsigned kWaitPolls = 1u << 20;
 
 // wmul63 for a < 2^32: with b = bh 2^32 + bl, (a b + 2^62) >> 63 equals
 // (a bh + ((a bl) >> 32) + 2^30) >> 31 (the low 32 bits of a bl cannot carry
@@ -428,6 +432,7 @@ struct FftArgs {
     size_t smem;
     int threads;           // threads per CTA: 128 or 256
     unsigned* status;      // device status word (bounded waits that ran out), or null
+    int inject_wait = 0;   // fault injection: the x-forward bulk copy's wait runs out
 };
 cudaError_t fft_configure();
 template <typename T>

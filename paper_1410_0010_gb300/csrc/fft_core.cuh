@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
                                                     const int64_t* const* __restrict__ gmf,
                                                     const C<T>* __restrict__ tw_arena,
                                                     C<T>* __restrict__ wsA, int F,
-                                                    unsigned* __restrict__ status) {
+                                                    unsigned* __restrict__ status, int inject_wait) {
     extern __shared__ __align__(128) unsigned char smem_xf[];
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
             mbar_init(bar, 1);
             fence_proxy_async_smem();
             const unsigned bytes = (unsigned)nr * (unsigned)G0 * 8u;
-            mbar_arrive_expect_tx(bar, bytes);
+            mbar_arrive_expect_tx(bar, bytes + (inject_wait ? 16u : 0u));
             bulk_g2s(rows, in, bytes, bar);
         }
     }

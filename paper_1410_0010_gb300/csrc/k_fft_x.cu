@@ -38,10 +38,10 @@ cudaError_t launch_fft_xf(const FftArgs& a, const int64_t* const* gmf, cudaStrea
     if (a.n_chunks <= 0) return cudaSuccess;
     if (a.threads == 128)
         k_xf<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F,
-                                                      a.status);
+                                                      a.status, a.inject_wait);
     else
         k_xf<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, gmf, (const C<T>*)a.tw, (C<T>*)a.wsA, a.F,
-                                                      a.status);
+                                                      a.status, a.inject_wait);
     return cudaGetLastError();
 }
 
