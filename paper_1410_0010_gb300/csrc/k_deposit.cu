@@ -69,8 +69,12 @@ __device__ __forceinline__ int edge_rule(long long v, int G, int mode) {
     return (v < 0 || v >= G) ? -1 : (int)v;
 }
 
+// out[idx] += q as a fire-and-forget reduction (red: no value comes back, so
+// the issuing warp never waits on it); two's-complement addition mod 2^64 is
+// the same for signed and unsigned operands
 __device__ __forceinline__ void add_charge(int64_t* __restrict__ out, unsigned idx, long long q) {
-    if (q != 0) atomicAdd(reinterpret_cast<unsigned long long*>(out + idx), (unsigned long long)q);
+    if (q != 0)
+        asm volatile("red.global.add.u64 [%0], %1;" ::"l"(out + idx), "l"((unsigned long long)q));
 }
 
 // CTA size and minimum resident CTAs per SM of the particle deposit
@@ -78,7 +82,7 @@ __device__ __forceinline__ void add_charge(int64_t* __restrict__ out, unsigned i
 #define APM_DEP_THREADS 128
 #endif
 #ifndef APM_DEP_MIN_CTAS
-#define APM_DEP_MIN_CTAS 5
+#define APM_DEP_MIN_CTAS 6
 #endif
 constexpr int kDepThreads = APM_DEP_THREADS;
 
