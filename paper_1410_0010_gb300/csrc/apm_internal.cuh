@@ -285,9 +285,9 @@ __device__ __forceinline__ long long scaled_rint(double x, int K, bool& ok) {
     return (b >> 63) ? -(long long)r : (long long)r;
 }
 
-// x' = x + v half_dt in FP64 (two rounded operations; x itself when half_dt = 0)
+// x' = x + v half_dt in FP64 (two rounded operations)
 __device__ __forceinline__ double drift_raw(double x, double v, double half_dt) {
-    return half_dt == 0.0 ? x : __dadd_rn(x, __dmul_rn(v, half_dt));
+    return __dadd_rn(x, __dmul_rn(v, half_dt));
 }
 
 // X = rint(x'/delta0 2^31), canonical: modulo the box on a periodic domain; on

@@ -337,7 +337,7 @@ __device__ __forceinline__ void interp_weights(const long long X[3], int fb, flo
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const long long i = X[j] >> fb;
-        const float t = __ull2float_rn((unsigned long long)(X[j] - (i << fb))) * sc;
+        const float t = __uint2float_rn((unsigned)(X[j] - (i << fb))) * sc;   // offset < 2^fb <= 2^31
         const float u = 1.0f - t;
         w[j][0] = 0.5f * u * u;
         w[j][2] = 0.5f * t * t;
@@ -425,8 +425,17 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_
 // owner searched from the root down (a finer owner lies inside a coarser one);
 // the finest owner supplies the acceleration.  accs[l]: the acceleration
 // pointer table of level l.
+// CTA size and minimum resident CTAs per SM of the all-level interpolation
+#ifndef APM_INT_THREADS
+#define APM_INT_THREADS 128
+#endif
+#ifndef APM_INT_MIN_CTAS
+#define APM_INT_MIN_CTAS 8
+#endif
+constexpr int kIntThreads = APM_INT_THREADS;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_interp_levels(const LevelDev* __restrict__ levels, int nl, Particles P,
+__global__ void __launch_bounds__(kIntThreads, APM_INT_MIN_CTAS) k_interp_levels(const LevelDev* __restrict__ levels, int nl, Particles P,
                                                        double half_dt, const void* const* const* __restrict__ accs,
                                                        T* __restrict__ out) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -474,8 +483,8 @@ template <typename T>
 cudaError_t launch_interp_levels(const LevelDev* levels, int nl, const Particles& P, double half_dt,
                                  const void* const* const* accs, void* out, cudaStream_t s) {
     if (P.n <= 0 || nl <= 0) return cudaSuccess;
-    unsigned blocks = (unsigned)((P.n + 255) / 256);
-    k_interp_levels<T><<<blocks, 256, 0, s>>>(levels, nl, P, half_dt, accs, reinterpret_cast<T*>(out));
+    unsigned blocks = (unsigned)((P.n + kIntThreads - 1) / kIntThreads);
+    k_interp_levels<T><<<blocks, kIntThreads, 0, s>>>(levels, nl, P, half_dt, accs, reinterpret_cast<T*>(out));
     return cudaGetLastError();
 }
 
