@@ -392,9 +392,11 @@ template <typename T> struct SmemIO {
 };
 // element i of this thread's global line: in[i stride] for i < n (zero beyond:
 // the padding), nothing for a column outside [0, Hx)
+// (i stride < 2^31: lines hold at most 1024 elements and strides are below
+// 1024 x 513 elements, so the offsets stay 32-bit)
 template <typename T> struct GlobalIn {
     const C<T>* __restrict__ p;
-    long long stride;
+    int stride;
     int n;
     bool live;
     __device__ C<T> ld(int i) const { return (live && i < n) ? p[i * stride] : mk<T>(0, 0); }
@@ -404,7 +406,7 @@ template <typename T> struct GlobalIn {
 // the window too (a periodic root's window N + 4 exceeds M = N)
 template <typename T> struct GlobalOut {
     C<T>* __restrict__ p;
-    long long stride;
+    int stride;
     int n, s0, L;
     bool live;
     __device__ void st(int i, C<T> v) const {
@@ -609,8 +611,8 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
         in.p = wsA + (g.wsA + (long long)other * g.G[1] * Hx + kx); in.stride = Hx; in.n = g.G[1];
         out.p = wsB + (g.wsB + (long long)other * M1 * Hx + kx); out.stride = Hx; out.n = M1; out.s0 = 0;
     } else if (AX == 2) {
-        in.p = wsB + (g.wsB + (long long)other * Hx + kx); in.stride = (long long)M1 * Hx; in.n = g.G[2];
-        out.p = wsA + (g.wsA + (long long)other * Hx + kx); out.stride = (long long)M1 * Hx;
+        in.p = wsB + (g.wsB + (long long)other * Hx + kx); in.stride = M1 * Hx; in.n = g.G[2];
+        out.p = wsA + (g.wsA + (long long)other * Hx + kx); out.stride = M1 * Hx;
         out.n = g.W[2]; out.s0 = g.s0[2];
     } else {
         in.p = wsA + (g.wsA + (long long)other * M1 * Hx + kx); in.stride = Hx; in.n = M1;
