@@ -827,7 +827,7 @@ apm_status apm_deposit(apm_ctx* c, int32_t level, const apm_particles* particles
     {
     Trace t(c, K_GAS, s);
     if (launch_gas_init(L.dev, pgrids, (const double* const*)d_gas, (const double* const*)d_pgas,
-                        (int64_t* const*)d_gmf, L.d_gas, L.n_gas, kChunkCells, c->cfg.mass_frac_bits,
+                        (int64_t* const*)d_gmf, L.d_gas, L.n_gas, c->cfg.mass_frac_bits,
                         s) != cudaSuccess)
         return APM_E_CUDA;
     }
@@ -872,7 +872,7 @@ apm_status apm_deposit_all(apm_ctx* c, const apm_particles* particles, double ha
         }
         Trace t(c, K_GAS, s);
         if (launch_gas_init(L.dev, pgrids, (const double* const*)d_gas, (const double* const*)d_pgas,
-                            (int64_t* const*)d_gmf, L.d_gas, L.n_gas, kChunkCells, c->cfg.mass_frac_bits,
+                            (int64_t* const*)d_gmf, L.d_gas, L.n_gas, c->cfg.mass_frac_bits,
                             s) != cudaSuccess)
             return APM_E_CUDA;
     }
@@ -1047,9 +1047,9 @@ apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,
     Trace t(c, K_ACCEL, s);
     cudaError_t e = c->cfg.precision == APM_FP64
         ? launch_accel<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                               (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, kChunkCells, s)
+                               (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s)
         : launch_accel<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                              (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, kChunkCells, s);
+                              (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s);
     return cuda_status(e);
 }
 

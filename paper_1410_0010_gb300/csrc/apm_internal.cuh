@@ -410,7 +410,7 @@ cudaError_t launch_to_f32(const double* in, float* out, long long n, cudaStream_
 // GMF: baryons (initialises every cell) then particles
 cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
                             const double* const* gas, const double* const* pgas,
-                            int64_t* const* gmf, const Chunk* chunks, int n_chunks, int rows_per_cta,
+                            int64_t* const* gmf, const Chunk* chunks, int n_chunks,
                             int F, cudaStream_t s);
 cudaError_t launch_deposit(const LevelDev& L, const Particles& P, double half_dt, double box,
                            int F, int64_t* const* gmf, unsigned* status, cudaStream_t s);
@@ -450,7 +450,7 @@ cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
 template <typename T>
 cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
                          const void* const* pphi, const void* const* pacc, void* const* phi,
-                         void* const* acc, const Chunk* chunks, int n_chunks, int rows_per_cta,
+                         void* const* acc, const Chunk* chunks, int n_chunks,
                          cudaStream_t s);
 template <typename T>
 cudaError_t launch_interp(const LevelDev& L, const LevelDev* finer, const Particles& P,

@@ -15,7 +15,7 @@ namespace {
 __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __restrict__ pgrids,
                            const double* const* __restrict__ gas,
                            const double* const* __restrict__ pgas, int64_t* const* __restrict__ gmf,
-                           const Chunk* __restrict__ chunks, int rows_per_cta, int F) {
+                           const Chunk* __restrict__ chunks, int F) {
     const Chunk c = chunks[blockIdx.x];
     const GridDev& g = L.g[c.grid];
     const int G0 = g.G[0], G1 = g.G[1];
@@ -258,10 +258,10 @@ __global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit_level
 
 cudaError_t launch_gas_init(const LevelDev& L, const GridDev* parent_grids,
                             const double* const* gas, const double* const* pgas,
-                            int64_t* const* gmf, const Chunk* chunks, int n_chunks, int rows_per_cta,
+                            int64_t* const* gmf, const Chunk* chunks, int n_chunks,
                             int F, cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    k_gas_init<<<n_chunks, 256, 0, s>>>(L, parent_grids, gas, pgas, gmf, chunks, rows_per_cta, F);
+    k_gas_init<<<n_chunks, 256, 0, s>>>(L, parent_grids, gas, pgas, gmf, chunks, F);
     return cudaGetLastError();
 }
 

@@ -461,10 +461,9 @@ __global__ void __launch_bounds__(kIntThreads, APM_INT_MIN_CTAS) k_interp_levels
 template <typename T>
 cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
                          const void* const* pphi, const void* const* pacc, void* const* phi,
-                         void* const* acc, const Chunk* chunks, int n_chunks, int rows_per_cta,
+                         void* const* acc, const Chunk* chunks, int n_chunks,
                          cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    (void)rows_per_cta;
     k_accel<T><<<n_chunks, kAccThreads, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks);
     return cudaGetLastError();
 }
@@ -490,10 +489,10 @@ cudaError_t launch_interp_levels(const LevelDev* levels, int nl, const Particles
 
 template cudaError_t launch_accel<float>(const LevelDev&, const GridDev*, const void* const*,
                                          const void* const*, const void* const*, void* const*,
-                                         void* const*, const Chunk*, int, int, cudaStream_t);
+                                         void* const*, const Chunk*, int, cudaStream_t);
 template cudaError_t launch_accel<double>(const LevelDev&, const GridDev*, const void* const*,
                                           const void* const*, const void* const*, void* const*,
-                                          void* const*, const Chunk*, int, int, cudaStream_t);
+                                          void* const*, const Chunk*, int, cudaStream_t);
 template cudaError_t launch_interp<float>(const LevelDev&, const LevelDev*, const Particles&, double,
                                           const void* const*, void*, cudaStream_t);
 template cudaError_t launch_interp<double>(const LevelDev&, const LevelDev*, const Particles&, double,
