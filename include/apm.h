@@ -268,6 +268,20 @@ apm_status apm_interp(apm_ctx* ctx, int32_t level, const void* const* acc,
 apm_status apm_interp_all(apm_ctx* ctx, const void* const* acc, const apm_particles* particles,
                           double half_dt, void* acc_out, void* stream);
 
+/* One timestep of n particles (SoA, device arrays, updated in place) given
+ * their accelerations `acc` (device, 3n values of the context precision, as
+ * apm_interp writes them) evaluated at the half-step drifted positions
+ * x + v dt/2, which is where apm_deposit and apm_interp place the particles
+ * for half_dt = dt/2:
+ *   v' = v + a dt,   x' = x + ((v + v')/2) dt
+ * (drift-kick-drift leapfrog), every FP64 operation rounded in this order.
+ * All levels advance with the same dt: the paper's evolutions without
+ * subcycling (Sec. 3.1, 3.5).  The paper names no integrator; this one drives
+ * those tests.  Positions are not wrapped (the deposit wraps periodic
+ * coordinates itself). */
+apm_status apm_kick_drift(apm_ctx* ctx, int64_t n, double* x, double* y, double* z, double* vx,
+                          double* vy, double* vz, const void* acc, double dt, void* stream);
+
 /* Kernel tracing.  While enabled, every kernel the context launches is
  * bracketed by CUDA events recorded on the stream it runs on (events come from
  * a pool of `capacity` pairs allocated here; launches beyond it are not

@@ -48,6 +48,10 @@
  *       product rounded half up to the scale 2^63, and the centre cell's weight
  *       is 2^63 minus theirs (deposit and interpolation weights sum to one
  *       exactly).
+ *   R14 Time evolution (Sec. 3.1, 3.5 without subcycling; the paper names no
+ *       integrator): every level advances with one timestep dt; the solve
+ *       evaluates accelerations at the half-step drifted positions
+ *       x + v dt/2 (Sec. 2), then v' = v + a dt and x' = x + (v + v')/2 dt.
  *   Fixed point: cell masses are int64 with F fractional bits.  With
  *   M = rint(m 2^F), each of the 26 outer cells receives ((|M| wx) wy) wz,
  *   every product (a b + 2^62) >> 63 (sign of M), the centre cell M minus the
@@ -334,6 +338,30 @@ double orc_drift(double x, double v, double half_dt, double box, int periodic) {
     double xd = x + t;
     if (periodic) xd = xd - box * floor(xd / box);
     return xd;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One timestep of the particles with accelerations a evaluated at the        */
+/* half-step drifted positions x + v dt/2 (the drift of Sec. 2 that the       */
+/* deposit and interpolation apply): v' = v + a dt, then                      */
+/* x' = x + ((v + v')/2) dt, i.e. x + v dt + a dt^2/2, second order.  Each    */
+/* operation is one IEEE rounding in this order (no contraction), over n      */
+/* particles stored as SoA.  Not in the paper: a driver of the time           */
+/* evolutions of Sec. 3.1 and 3.5 without subcycling (reading R14).           */
+/* ------------------------------------------------------------------------ */
+void orc_kick_drift(int64_t n, double* px, double* py, double* pz, double* pvx, double* pvy,
+                    double* pvz, const double* acc, double dt) {
+    double* pos[3] = {px, py, pz};
+    double* vel[3] = {pvx, pvy, pvz};
+    for (int64_t p = 0; p < n; ++p)
+        for (int j = 0; j < 3; ++j) {
+            double v = vel[j][p];
+            double a = acc[(int64_t)j * n + p];
+            double vn = v + a * dt;
+            double vm = (v + vn) * 0.5;
+            pos[j][p] = pos[j][p] + vm * dt;
+            vel[j][p] = vn;
+        }
 }
 
 /* Fixed-point position (reading R11): the drifted coordinate in root cells,

@@ -49,6 +49,8 @@ def lib():
         L.orc_green_table.argtypes = [ci, P, d, d, d, ci, P, ci]
         L.orc_drift.restype = d
         L.orc_drift.argtypes = [d, d, d, d, ci]
+        L.orc_kick_drift.restype = None
+        L.orc_kick_drift.argtypes = [i64, P, P, P, P, P, P, P, d]
         L.orc_tsc_weights.restype = i64
         L.orc_tsc_weights.argtypes = [d, d, P]
         L.orc_cic_weights.restype = i64
@@ -134,6 +136,18 @@ def cic_weights(x, delta):
 
 def drift(x, v, half_dt, box, periodic):
     return lib().orc_drift(float(x), float(v), float(half_dt), float(box), int(periodic))
+
+
+def kick_drift(particles, acc, dt):
+    """One timestep in place (orc_kick_drift): particles is a dict of float64
+    arrays x, y, z, vx, vy, vz; acc is (3, n), evaluated at x + v dt/2."""
+    n = len(particles["x"])
+    arr = {k: np.ascontiguousarray(particles[k], dtype=np.float64) for k in ("x", "y", "z", "vx", "vy", "vz")}
+    a = np.ascontiguousarray(acc, dtype=np.float64).reshape(3, n)
+    lib().orc_kick_drift(n, *[_p(arr[k]) for k in ("x", "y", "z", "vx", "vy", "vz")], _p(a), float(dt))
+    for k in arr:
+        particles[k] = arr[k]
+    return particles
 
 
 # --------------------------------------------------------------------------

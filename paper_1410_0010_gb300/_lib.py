@@ -66,6 +66,8 @@ SIGNATURES = {
                                    ctypes.POINTER(c_void_p), c_void_p]),
     "apm_get_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
     "apm_set_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
+    "apm_kick_drift": (c_i32, [c_void_p, c_i64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p, c_dbl, c_void_p]),
     "apm_sync_status": (c_i32, [c_void_p, c_void_p]),
     "apm_profile_enable": (c_i32, [c_void_p, c_i32, c_i32]),
     "apm_profile_read": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl)]),

@@ -1102,6 +1102,17 @@ apm_status apm_interp_all(apm_ctx* c, const void* const* acc, const apm_particle
     return cuda_status(e);
 }
 
+apm_status apm_kick_drift(apm_ctx* c, int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                          double* vz, const void* acc, double dt, void* stream) {
+    if (!c) return APM_E_INVALID;
+    if (n < 0 || (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !acc))) return APM_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = c->cfg.precision == APM_FP64
+                        ? launch_kick_drift<double>(n, x, y, z, vx, vy, vz, acc, dt, s)
+                        : launch_kick_drift<float>(n, x, y, z, vx, vy, vz, acc, dt, s);
+    return cuda_status(e);
+}
+
 int32_t apm_kernel_count(void) { return K_COUNT; }
 
 const char* apm_kernel_name(int32_t k) { return (k >= 0 && k < K_COUNT) ? kKernelNames[k] : nullptr; }

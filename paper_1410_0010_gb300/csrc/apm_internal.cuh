@@ -460,4 +460,9 @@ template <typename T>
 cudaError_t launch_interp_levels(const LevelDev* levels, int nl, const Particles& P, double half_dt,
                                  const void* const* const* accs, void* out, cudaStream_t s);
 
+// one leapfrog step of the particles (k_evolve.cu); acc: 3n values of T
+template <typename T>
+cudaError_t launch_kick_drift(long long n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
+                              const void* acc, double dt, cudaStream_t s);
+
 }  // namespace apm

@@ -218,6 +218,27 @@ class Solver:
                                ctypes.byref(P.c), float(half_dt), out.data_ptr(),
                                _stream_handle(stream)), "apm_interp")
 
+    def kick_drift(self, particles, acc, dt, stream=None):
+        """apm_kick_drift: one leapfrog step in place, acc (3, n) evaluated at
+        the half-step drifted positions (step with half_dt = dt / 2)."""
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        t = P.t
+        check(lib().apm_kick_drift(self._ctx, P.n, t["x"].data_ptr(), t["y"].data_ptr(), t["z"].data_ptr(),
+                                   t["vx"].data_ptr(), t["vy"].data_ptr(), t["vz"].data_ptr(),
+                                   acc.data_ptr(), float(dt), _stream_handle(stream)), "apm_kick_drift")
+
+    def evolve(self, particles, dt, steps, bufs, pacc, gas=None, callback=None, stream=None):
+        """`steps` timesteps without subcycling: each solves the hierarchy at
+        the half-step drifted positions (half_dt = dt / 2) and applies
+        apm_kick_drift.  callback(k, particles, pacc), if given, runs after
+        step k (k = 1 .. steps)."""
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        for k in range(1, steps + 1):
+            self.step(P, 0.5 * dt, bufs, pacc, gas=gas, stream=stream)
+            self.kick_drift(P, pacc, dt, stream)
+            if callback is not None:
+                callback(k, P, pacc)
+
     def profile(self, on, capacity=65536):
         """Turns kernel tracing on (event pool of `capacity` launches) or off."""
         check(lib().apm_profile_enable(self._ctx, 1 if on else 0, int(capacity)), "apm_profile_enable")
