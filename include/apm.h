@@ -122,7 +122,10 @@ apm_status apm_create(const apm_config* cfg, apm_ctx** out);
  *  - validates the tree: levels 0..L each non-empty, every child's parent on the
  *    level above, sibling interiors disjoint, and every parent cell a child
  *    reads (its GMF border, Sec. 2, and the trilinear carry of its cells
- *    [-1, dims]) inside the parent's interior; otherwise APM_E_NESTING;
+ *    [-1, dims]) inside the parent's interior; otherwise APM_E_NESTING.  On an
+ *    isolated root the GMF border of a level-1 grid may extend past the box:
+ *    nothing lies outside an isolated domain, so its baryons there are zero
+ *    (the carry must still stay inside the root);
  *  - plans each grid's border B and FFT lengths M (FFT lengths up to 1024);
  *  - builds on the GPU, in FP64, the Green's-function table of every distinct
  *    (grid type, M) (Sec. 2.2 Eq. influence with the Brillouin sum of

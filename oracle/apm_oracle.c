@@ -514,6 +514,9 @@ int orc_deposit(int64_t n, const double* px, const double* py, const double* pz,
 /* onto the boundary); mass = rint((rho * delta^3) * 2^F).  G = N + 2B.       */
 /* start: global level index of interior cell 0; pstart: parent's, in parent */
 /* cells; R: refinement factor.  pgas may be NULL (no baryons in the border). */
+/* A border cell whose parent cell lies outside the parent (a child of an     */
+/* isolated root reaching past the box) has no baryons: nothing lies outside  */
+/* an isolated domain.                                                        */
 /* ------------------------------------------------------------------------ */
 void orc_gas(const double* gas, const int64_t N[3], int64_t B, const double* pgas,
              const int64_t Np[3], const int64_t pstart[3], const int64_t start[3], int R,
@@ -533,8 +536,12 @@ void orc_gas(const double* gas, const int64_t N[3], int64_t B, const double* pga
                     if (gas) rho = gas[c[0] + N[0] * (c[1] + N[1] * c[2])];
                 } else if (pgas) {
                     int64_t pc[3];
-                    for (int j = 0; j < 3; ++j) pc[j] = floor_div(start[j] + c[j], R) - pstart[j];
-                    rho = pgas[pc[0] + Np[0] * (pc[1] + Np[1] * pc[2])];
+                    int inside = 1;
+                    for (int j = 0; j < 3; ++j) {
+                        pc[j] = floor_div(start[j] + c[j], R) - pstart[j];
+                        if (pc[j] < 0 || pc[j] >= Np[j]) inside = 0;
+                    }
+                    if (inside) rho = pgas[pc[0] + Np[0] * (pc[1] + Np[1] * pc[2])];
                 }
                 int64_t q = (int64_t)rint((rho * vol) * scale);
                 int64_t idx = x + G[0] * (y + G[1] * z);

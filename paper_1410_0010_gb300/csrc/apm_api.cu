@@ -204,13 +204,17 @@ apm_status validate(const apm_config& cfg, const apm_grid* gr, int n) {
     for (int i = 1; i < n; ++i) {
         const apm_grid& g = gr[i];
         const apm_grid& p = gr[g.parent];
+        // nothing lies outside an isolated root: the GMF border of its children
+        // may extend past it (those baryons are zero); the carry may not
+        const bool past_root = g.parent == 0 && cfg.root_bc == APM_BC_ISOLATED;
         for (int j = 0; j < 3; ++j) {
             // parent cells read by the GMF border (baryons) and by the carry of cells [-1, N]
             long long lo_b = floor_div(g.start[j] - B, R);
             long long hi_b = floor_div(g.start[j] + g.dims[j] + B - 1, R);
             long long lo_c = (long long)std::floor((g.start[j] - 1 + 0.5) / R - 0.5);
             long long hi_c = (long long)std::floor((g.start[j] + g.dims[j] + 0.5) / R - 0.5) + 1;
-            long long lo = std::min(lo_b, lo_c), hi = std::max(hi_b, hi_c);
+            long long lo = past_root ? lo_c : std::min(lo_b, lo_c);
+            long long hi = past_root ? hi_c : std::max(hi_b, hi_c);
             if (lo < p.start[j] || hi >= p.start[j] + p.dims[j]) return APM_E_NESTING;
         }
     }

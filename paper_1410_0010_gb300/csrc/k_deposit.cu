@@ -49,11 +49,14 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
         if (yz_in && cx >= 0 && cx < g.N[0]) {
             if (own) rho = own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)];
         } else if (par) {
-            // parent cell floor(c / 2): the refinement factor is 2 (checked on the host)
+            // parent cell floor(c / 2): the refinement factor is 2 (checked on the host);
+            // past an isolated root's faces (the only border cells with no parent
+            // cell, checked on the host) there are no baryons
             long long px = ((g.start[0] + cx) >> 1) - p->start[0];
             long long py = ((g.start[1] + cy) >> 1) - p->start[1];
             long long pz = ((g.start[2] + cz) >> 1) - p->start[2];
-            rho = par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
+            if (px >= 0 && px < p->N[0] && py >= 0 && py < p->N[1] && pz >= 0 && pz < p->N[2])
+                rho = par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
         }
         row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
     }

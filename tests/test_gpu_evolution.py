@@ -3,15 +3,16 @@ half-step drifted positions followed by apm_kick_drift, against the oracle
 step by step, and the paper's evolutions:
 * Sec. 3.1 self-force test: one particle crossing the Fig. 1 hierarchy (16^3
   root, three static levels) keeps its velocity;
-* Sec. 3.5 orbit test, case 2 (particles on different levels, one timestep for
-  every level): a circular binary on a 16^3 isolated root with the central
-  particle refined on level 1 keeps its separation and centre of mass."""
+* Sec. 3.5 orbit test without subcycling: case 2 (the central particle on
+  level 1, the other on the root) against the oracle's trajectory, and case 4
+  (both on level 2) against the paper's centre-of-mass stability."""
 import math
 
 import numpy as np
 import pytest
 
 import apm_inputs as W
+from apm_inputs import GridDesc
 
 pytestmark = pytest.mark.gpu
 
@@ -92,7 +93,7 @@ def test_evolution_matches_oracle_across_levels():
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_self_force_particle_crossing_the_hierarchy(precision, tol):
     """Sec. 3.1: m = 1 at (0.15, 0.15, 0.15) with v = (1, 1, 1) crosses levels 0-3
     of the Fig. 1 hierarchy to t = 0.4 at dt = 3e-3; without subcycling the
@@ -129,69 +130,127 @@ def test_self_force_particle_crossing_the_hierarchy(precision, tol):
     s.close()
 
 
-def _orbit_case2():
-    grids = W.grids_from_bounds(16, [(0.375, 0.625)])
-    m1, m2, a = 1.0, 0.1, 0.3
+ORBIT_A = 0.3
+CASE2 = W.grids_from_bounds(16, [(0.375, 0.625)])
+# Case 4 with static grids: level 2 ([11, 53)^2 x [28, 36) cells of 1/64) holds
+# both orbits for all 10 of them; its parent level 1 reaches to 3/32 from the
+# root's faces, so its GMF border leaves the isolated root (no baryons there).
+CASE4 = [GridDesc(0, -1, (0, 0, 0), (16, 16, 16)), GridDesc(1, 0, (3, 3, 11), (26, 26, 10)),
+         GridDesc(2, 1, (11, 11, 28), (42, 42, 8))]
+
+
+def _binary():
+    """Sec. 3.5: M1 = 1 at the centre, M2 = 0.1 at (0.2, 0.5, 0.5), circular
+    orbit of separation 0.3 about the centre of mass in the x-y plane."""
+    m1, m2, a = 1.0, 0.1, ORBIT_A
     vrel = math.sqrt((m1 + m2) / a)
-    # circular orbit about the centre of mass, counter-clockwise in the x-y plane
     parts = dict(x=np.array([0.5, 0.2]), y=np.array([0.5, 0.5]), z=np.array([0.5, 0.5]),
                  vx=np.zeros(2), vy=np.array([m2 / (m1 + m2) * vrel, -m1 / (m1 + m2) * vrel]),
                  vz=np.zeros(2), m=np.array([m1, m2]))
     period = 2 * math.pi * math.sqrt(a ** 3 / (m1 + m2))
-    return grids, parts, a, period
+    return parts, period
 
 
-def _sample(x, m):
-    """(separation, centre of mass) of the pair from a (3, 2) position array."""
-    return float(np.linalg.norm(x[:, 1] - x[:, 0])), (x * m).sum(1) / m.sum()
-
-
-def test_orbit_case2_follows_the_oracle():
-    """Sec. 3.5 case 2: M1 = 1 at the centre, refined on level 1
-    ([0.375, 0.625]^3), M2 = 0.1 at (0.2, 0.5, 0.5) on the root only, circular
-    orbit of a = 0.3, dt = 3e-3 for every level, 10 orbits, FP64.  The paper
-    prints no figure for this case, so the GPU trajectory is compared with the
-    oracle's, sampled every 20 steps: positions to 1e-8 (the two sum the FFTs
-    in different orders, and 1e-12 differences per step grow along the orbit;
-    3281 steps end near 1e-9)."""
+def _gpu_orbit(grids, parts, dt, steps, every, precision="fp64"):
+    """Positions (3, 2) after every `every`-th step and after the last one."""
     import torch
 
-    import oracle
     from paper_1410_0010_gb300.solver import Solver
-    grids, parts, a, period = _orbit_case2()
-    dt = 3e-3
-    steps = int(round(10 * period / dt))
-    s = Solver(grids, periodic=False, precision="fp64", device=0)
+    s = Solver(grids, periodic=False, precision=precision, device=0)
     bufs = s.alloc_all()
     P = _dev_particles(parts)
-    pacc = torch.zeros((3, 2), dtype=torch.float64, device="cuda")
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    pacc = torch.zeros((3, 2), dtype=dtype, device="cuda")
     got = {}
 
     def watch(k, P, pacc):
-        if k % 20 == 0 or k == steps:
+        if k % every == 0 or k == steps:
             got[k] = np.stack([P.t[c].cpu().numpy() for c in ("x", "y", "z")])
 
     s.evolve(P, dt, steps, bufs, pacc, callback=watch)
     s.sync_status()
     s.close()
+    return got
+
+
+def _oracle_orbit(grids, parts, dt, steps, every):
+    import oracle
     cfg = oracle.Config(periodic=False)
     og = [oracle.Grid(*g) for g in grids]
     ref = {k: v.copy() for k, v in parts.items()}
-    worst = 0.0
-    seps, coms = [], []
+    out = {}
     for k in range(1, steps + 1):
         r = oracle.apm_step(cfg, og, ref, 0.5 * dt)
         oracle.kick_drift(ref, r.pacc, dt)
-        if k in got:
-            x = np.stack([ref[c] for c in ("x", "y", "z")])
-            worst = max(worst, float(np.abs(got[k] - x).max()))
-            sep, com = _sample(got[k], parts["m"])
-            seps.append(sep)
-            coms.append(com)
-    com0 = _sample(np.stack([parts[c] for c in ("x", "y", "z")]), parts["m"])[1]
-    drift = float(np.abs(np.array(coms) - com0).max())
-    print(f"orbit case 2: {steps} steps, separation [{min(seps):.4f}, {max(seps):.4f}] "
-          f"(a = {a}), centre-of-mass shift {drift:.3e}, GPU - oracle {worst:.2e}")
+        if k % every == 0 or k == steps:
+            out[k] = np.stack([ref[c] for c in ("x", "y", "z")])
+    return out
+
+
+def _orbit_stats(samples, parts):
+    m = parts["m"]
+    x0 = np.stack([parts[c] for c in ("x", "y", "z")])
+    com0 = (x0 * m).sum(1) / m.sum()
+    seps = np.array([np.linalg.norm(x[:, 1] - x[:, 0]) for x in samples.values()])
+    shift = max(float(np.abs((x * m).sum(1) / m.sum() - com0).max()) for x in samples.values())
+    return seps, shift, com0
+
+
+def test_orbit_case2_follows_the_oracle():
+    """Sec. 3.5 case 2: M1 refined on level 1 ([0.375, 0.625]^3), M2 on the root
+    only, dt = 3e-3 for every level, 10 orbits, FP64.  The paper prints no
+    figure for this case, so the GPU trajectory is compared with the oracle's,
+    sampled every 20 steps: positions to 1e-8 (the two sum the FFTs in
+    different orders, and 1e-12 differences per step grow along the orbit;
+    3281 steps end near 1e-9)."""
+    parts, period = _binary()
+    dt = 3e-3
+    steps = int(round(10 * period / dt))
+    got = _gpu_orbit(CASE2, parts, dt, steps, 20)
+    ref = _oracle_orbit(CASE2, parts, dt, steps, 20)
+    worst = max(float(np.abs(got[k] - ref[k]).max()) for k in ref)
+    seps, shift, _ = _orbit_stats(got, parts)
+    print(f"orbit case 2: {steps} steps, separation [{seps.min():.4f}, {seps.max():.4f}], "
+          f"centre-of-mass shift {shift:.3e}, GPU - oracle {worst:.2e}")
     assert worst < 1e-8, worst
     # the pair stays bound near its initial separation for all 10 orbits
-    assert 0.85 * a < min(seps) and max(seps) < 1.1 * a
+    assert 0.85 * ORBIT_A < seps.min() and seps.max() < 1.1 * ORBIT_A
+
+
+@pytest.mark.parametrize("precision,com_tol", [("fp64", 1e-9), ("fp32", 1e-3)])
+def test_orbit_case4_centre_of_mass_is_stable(precision, com_tol):
+    """Sec. 3.5 case 4: both particles on level 2, dt = 3e-3 for every level,
+    10 orbits.  The paper finds the centre of mass stable to a relative 1e-5;
+    with both particles in one level-2 grid the pair forces are opposite to
+    rounding, so FP64 holds it to 1e-9 (the oracle: 7e-11).  FP32 forces
+    carry rounding errors near 1e-5 of the field; that imbalance, integrated
+    over 10 orbits (t = 9.8), moves the centre of mass by up to about
+    e F t^2 / 2M = 5e-4, so FP32 is held to 1e-3 (measured: 2.6e-4).
+    The separation stays within [0.88, 1.01] a: at 4.8 root cells the root's
+    force, which alone acts at this range, is 4% above Newton on average in a
+    coordinate plane (two-point gradient, reading R8), so the circular start
+    becomes an eccentric orbit (the oracle: [0.266, 0.301])."""
+    parts, period = _binary()
+    dt = 3e-3
+    steps = int(round(10 * period / dt))
+    got = _gpu_orbit(CASE4, parts, dt, steps, 20, precision)
+    seps, shift, com0 = _orbit_stats(got, parts)
+    lo2, hi2 = np.array([11, 11, 28]) / 64, np.array([53, 53, 36]) / 64
+    inside = all(np.all((x >= lo2[:, None]) & (x < hi2[:, None])) for x in got.values())
+    print(f"orbit case 4 {precision}: {steps} steps, separation [{seps.min():.4f}, {seps.max():.4f}], "
+          f"relative centre-of-mass shift {shift / np.linalg.norm(com0):.2e}")
+    assert inside                                   # both stay on level 2
+    assert shift / np.linalg.norm(com0) < com_tol
+    assert 0.88 * ORBIT_A < seps.min() and seps.max() < 1.01 * ORBIT_A
+
+
+def test_orbit_case4_first_orbit_follows_the_oracle():
+    """One orbit of case 4 (328 steps), FP64 GPU against the oracle: 1e-9."""
+    parts, period = _binary()
+    dt = 3e-3
+    steps = int(round(period / dt))
+    got = _gpu_orbit(CASE4, parts, dt, steps, 8)
+    ref = _oracle_orbit(CASE4, parts, dt, steps, 8)
+    worst = max(float(np.abs(got[k] - ref[k]).max()) for k in ref)
+    print(f"orbit case 4, first orbit: GPU - oracle {worst:.2e}")
+    assert worst < 1e-9, worst

@@ -96,6 +96,27 @@ def test_odd_starts_odd_root_and_grandchild(precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+def test_borders_past_an_isolated_root(precision):
+    """Level-1 grids at the faces of an isolated 24^3 root: their GMF borders
+    reach past the box (no baryons there), the carry stays inside; a level-2
+    grid below one of them; gas everywhere and particles crowding the faces."""
+    grids = [GridDesc(0, -1, (0, 0, 0), (24, 24, 24)),
+             GridDesc(1, 0, (2, 3, 36), (12, 10, 10)),
+             GridDesc(1, 0, (30, 30, 2), (16, 14, 12)),
+             GridDesc(2, 1, (9, 11, 78), (14, 10, 8))]
+    rng = np.random.default_rng(29)
+    near = _random_particles(rng, 400, 0.002, 0.3, vscale=0.1)
+    near["z"] = 0.75 + 0.248 * rng.random(400)
+    far = _random_particles(rng, 400, 0.6, 0.998, vscale=0.1)
+    far["z"] = 0.002 + 0.248 * rng.random(400)
+    parts = W.concat_particles(near, far, _random_particles(rng, 300, 0.02, 0.98, vscale=0.1))
+    gas = [rng.random(g.dims[::-1]) + 0.1 for g in grids]
+    ref = run_oracle(grids, parts, 1e-3, gas=gas)
+    gpu = run_gpu(grids, parts, 1e-3, gas=gas, precision=precision)
+    compare(gpu, ref, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_all_level_calls_equal_per_level_calls_bitwise(precision):
     """apm_deposit_all / apm_interp_all against apm_deposit / apm_interp level by
     level on a three-level periodic hierarchy with gas and particles everywhere

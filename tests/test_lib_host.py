@@ -82,10 +82,12 @@ def _grids(descs):
     return arr
 
 
-def _validate(L, descs):
-    from paper_1410_0010_gb300._lib import ApmConfig
+def _validate(L, descs, periodic=False):
+    from paper_1410_0010_gb300._lib import APM_BC_PERIODIC, ApmConfig
     c = ApmConfig()
     L.apm_config_default(ctypes.byref(c))
+    if periodic:
+        c.root_bc = APM_BC_PERIODIC
     return L.apm_validate_hierarchy(ctypes.byref(c), _grids(descs), len(descs))
 
 
@@ -104,12 +106,25 @@ def test_validation_nesting_rules(L):
     ok = [ROOT32, (1, 0, (12, 12, 12), (20, 20, 20))]
     assert _validate(L, ok) == 0
     # parent cells of the border: child start 10 -> border cells from 5 -> parent 2: ok;
-    # start 4 -> border from -1 -> parent -1: outside the root
-    assert _validate(L, [ROOT32, (1, 0, (4, 12, 12), (8, 8, 8))]) == 2
-    assert _validate(L, [ROOT32, (1, 0, (6, 12, 12), (8, 8, 8))]) == 0
+    # start 4 -> border from -1 -> parent -1: outside a periodic root
+    assert _validate(L, [ROOT32, (1, 0, (4, 12, 12), (8, 8, 8))], periodic=True) == 2
+    assert _validate(L, [ROOT32, (1, 0, (6, 12, 12), (8, 8, 8))], periodic=True) == 0
     # upper edge: parent cell floor((start + N + B - 1)/2) must be < 32
-    assert _validate(L, [ROOT32, (1, 0, (12, 12, 52), (8, 8, 8))]) == 2
-    assert _validate(L, [ROOT32, (1, 0, (12, 12, 52), (8, 8, 6))]) == 0
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 52), (8, 8, 8))], periodic=True) == 2
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 52), (8, 8, 6))], periodic=True) == 0
+    # an isolated root has nothing outside it: the border may leave the box, the
+    # carry of cells [-1, N] may not (start 1: cell -1 reads parent cell -1)
+    assert _validate(L, [ROOT32, (1, 0, (4, 12, 12), (8, 8, 8))]) == 0
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 52), (8, 8, 8))]) == 0
+    assert _validate(L, [ROOT32, (1, 0, (2, 12, 12), (8, 8, 8))]) == 0
+    assert _validate(L, [ROOT32, (1, 0, (1, 12, 12), (8, 8, 8))]) == 2
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 54), (8, 8, 8))]) == 0
+    assert _validate(L, [ROOT32, (1, 0, (12, 12, 55), (8, 8, 8))]) == 2
+    # deeper levels keep the full rule: level 2 at start 8 has border cells from 3,
+    # in level-1 cell 1, outside its parent (cells [2, 22))
+    lev1 = (1, 0, (2, 2, 2), (20, 20, 20))
+    assert _validate(L, [ROOT32, lev1, (2, 1, (10, 10, 10), (8, 8, 8))]) == 0
+    assert _validate(L, [ROOT32, lev1, (2, 1, (8, 10, 10), (8, 8, 8))]) == 2
     # overlapping siblings
     assert _validate(L, [ROOT32, (1, 0, (12, 12, 12), (10, 10, 10)),
                          (1, 0, (20, 20, 20), (10, 10, 10))]) == 2

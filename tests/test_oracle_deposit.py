@@ -203,3 +203,39 @@ def test_status_flags(oracle_mod):
     assert st & 2   # out of box (still folded)
     _, st = oracle_mod.deposit(cfg, grids, 0, _parts(pos[:, 1:], [4096.0]), 0.0)
     assert st & 1   # 4096 * 2^52 >= 2^62: overflow, skipped
+
+
+def test_border_past_an_isolated_root_has_no_baryons(oracle_mod):
+    """A level-1 grid whose GMF border reaches past an isolated root (start 2 on
+    a 16^3 root: border cells from -3, root cells from -2): nothing lies outside
+    an isolated domain, so those border cells hold zero baryon mass, the others
+    the parent's density, and every particle's mass is still conserved."""
+    cfg = oracle_mod.Config(periodic=False)
+    grids = [oracle_mod.Grid(0, -1, (0, 0, 0), (16, 16, 16)), oracle_mod.Grid(1, 0, (2, 10, 10), (8, 8, 8))]
+    plan = oracle_mod.plan_grid(cfg, grids, 1)
+    B = plan.B
+    rng = np.random.default_rng(8)
+    pgas = rng.random((16, 16, 16)) + 0.5
+    empty = _parts(np.zeros((3, 0)), [])
+    gmf, _ = oracle_mod.deposit(cfg, grids, 1, empty, 0.0, gas=None, parent_gas=pgas)
+    vol = plan.delta ** 3
+    F = cfg.mass_frac_bits
+    for x in range(plan.G[0]):
+        gx = 2 + x - B                               # global level-1 cell
+        for (y, z) in [(0, 0), (B, B + 3), (plan.G[1] - 1, B)]:
+            c = np.array([x, y, z]) - B
+            if np.all(c >= 0) and np.all(c < 8):
+                want = 0                             # interior, no own gas
+            elif gx < 0:
+                want = 0                             # past the root's face
+            else:
+                pc = (np.array([2, 10, 10]) + c) // 2
+                want = int(np.rint(pgas[pc[2], pc[1], pc[0]] * vol * 2.0 ** F))
+            assert gmf[z, y, x] == want, (x, y, z)
+    # particles in the root cells next to the face deposit their whole mass
+    pos = np.array([[0.01, 0.02], [0.33, 0.34], [0.35, 0.36]])
+    m = [1.0, 0.5]
+    parts = _parts(pos, m)
+    gmf, st = oracle_mod.deposit(cfg, grids, 1, parts, 0.0)
+    assert st == 0
+    assert int(gmf.sum()) == sum(int(np.rint(v * 2.0 ** F)) for v in m)
