@@ -48,6 +48,15 @@
  *       product rounded half up to the scale 2^63, and the centre cell's weight
  *       is 2^63 minus theirs (deposit and interpolation weights sum to one
  *       exactly).
+ *   R15 Gradient operator (Sec. 2.2 allows a finite difference or the direct
+ *       Fourier-space gradient D = -ik): the two-point difference (R8), the
+ *       four-point difference D = (8 sin(k delta) - sin(2 k delta))/(6 delta),
+ *       or D = k with 0 on an even M's Nyquist mode; the influence function
+ *       is built for the operator the accelerations use.  With the four-point
+ *       difference the potential window is [-3, N+3) and an isolated root's
+ *       M is the smallest even {2,3,5,7}-smooth length >= 2N + 2, so that the
+ *       edge cells' stencils read unwrapped offsets; the spectral gradient
+ *       transforms -i D_j phi-hat back once per component.
  *   R14 Time evolution (Sec. 3.1, 3.5 without subcycling; the paper names no
  *       integrator): every level advances with one timestep dt; the solve
  *       evaluates accelerations at the half-step drifted positions
@@ -151,23 +160,39 @@ double orc_alias_sum(const int64_t kap[3], const int64_t M[3]) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Gradient operator D_j at the centred mode kc of an M grid (Sec. 2.2: a     */
+/* finite difference or the Fourier-space gradient D = -ik; the factor -i is  */
+/* common to all and left out here).  grad 0: two-point difference,           */
+/* sin(k delta)/delta (reading R8); grad 1: four-point difference             */
+/* (8 sin(k delta) - sin(2 k delta))/(6 delta); grad 2: spectral, k itself,   */
+/* except 0 on the Nyquist mode kc = M/2 of an even M (reading R15).          */
+/* ------------------------------------------------------------------------ */
+double orc_grad_d(int grad, int64_t kc, int64_t M, double delta) {
+    double th = 2.0 * ORC_PI * (double)kc / (double)M;   /* k delta */
+    if (grad == 0) return sin(th) / delta;
+    if (grad == 1) return (8.0 * sin(th) - sin(2.0 * th)) / (6.0 * delta);
+    if (2 * kc == M) return 0.0;
+    return th / delta;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Optimal influence function, Sec. 2.2 Eq. influence with Eq. brillouin     */
 /* truncated to n in [-1,1]^3, Eq. assignment/assignment2 (reading R2),       */
-/* Eq. reference (readings R1, R3) and the FD gradient (reading R8).          */
+/* Eq. reference (readings R1, R3) and the gradient D of orc_grad_d.          */
 /* kap[j] in [0, M_j); it is centred to (-M/2, M/2] before use.              */
 /* use_parent = 0: reference force S(a_lev)^2/k^2 (root);                     */
 /* use_parent = 1: (S(a_lev)^2 - S(a_par)^2)/k^2 (refined level).            */
 /* Returns G-hat in continuum units (potential = G-hat * density).            */
 /* ------------------------------------------------------------------------ */
 double orc_green_opt(const int64_t kap[3], const int64_t M[3], double delta,
-                     double a_lev, double a_par, int use_parent) {
+                     double a_lev, double a_par, int use_parent, int grad) {
     double k[3], D[3];
     double alias = orc_alias_sum(kap, M), D2 = 0.0;
     for (int j = 0; j < 3; ++j) {
         int64_t kc = kap[j];
         if (kc > M[j] / 2) kc -= M[j];
         k[j] = 2.0 * ORC_PI * (double)kc / ((double)M[j] * delta);
-        D[j] = sin(2.0 * ORC_PI * (double)kc / (double)M[j]) / delta;
+        D[j] = orc_grad_d(grad, kc, M[j], delta);
         D2 += D[j] * D[j];
     }
     double num = 0.0;
@@ -196,7 +221,8 @@ double orc_green_opt(const int64_t kap[3], const int64_t M[3], double delta,
     return -4.0 * ORC_PI * num / (D2 * alias * alias);
 }
 
-/* 1 when the FD gradient vanishes identically at this mode (reading R5). */
+/* 1 when the gradient vanishes identically at this mode (reading R5): every */
+/* kappa_j is 0 or M_j/2, for each of the three operators.                    */
 static int degenerate(const int64_t kap[3], const int64_t M[3]) {
     for (int j = 0; j < 3; ++j)
         if (!(kap[j] == 0 || 2 * kap[j] == M[j])) return 0;
@@ -267,7 +293,7 @@ void orc_dft3(double* re, double* im, const int64_t M[3], int sign, int nthreads
 /* kind 1: periodic root; kind 2: isolated root on the doubled grid.          */
 /* ------------------------------------------------------------------------ */
 void orc_green_table(int kind, const int64_t M[3], double delta, double a_lev, double a_par,
-                     int correction, double* T, int nthreads) {
+                     int correction, int grad, double* T, int nthreads) {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -307,9 +333,9 @@ void orc_green_table(int kind, const int64_t M[3], double delta, double a_lev, d
                     if (zero)
                         v = -4.0 * ORC_PI * (a_par * a_par - a_lev * a_lev) / 30.0 / vol;
                     else if (!deg)
-                        v = orc_green_opt(kap, M, delta, a_lev, a_par, 1) / vol;
+                        v = orc_green_opt(kap, M, delta, a_lev, a_par, 1, grad) / vol;
                 } else if (kind == 1) {
-                    if (!zero && !deg) v = orc_green_opt(kap, M, delta, a_lev, 0.0, 0) / vol;
+                    if (!zero && !deg) v = orc_green_opt(kap, M, delta, a_lev, 0.0, 0, grad) / vol;
                 } else {
                     v = gre[x + M[0] * (y + M[1] * z)];
                     if (correction && !zero && !deg) {
@@ -320,7 +346,7 @@ void orc_green_table(int kind, const int64_t M[3], double delta, double a_lev, d
                         }
                         double s = orc_shat(sqrt(kk) * a_lev / 2.0);
                         double gcont = -4.0 * ORC_PI * s * s / kk;
-                        v += (orc_green_opt(kap, M, delta, a_lev, 0.0, 0) - gcont) / vol;
+                        v += (orc_green_opt(kap, M, delta, a_lev, 0.0, 0, grad) - gcont) / vol;
                     }
                 }
                 T[x + H[0] * (y + H[1] * z)] = v;
@@ -594,18 +620,93 @@ void orc_solve(const int64_t* gmf, const int64_t G[3], int F, const int64_t M[3]
 }
 
 /* ------------------------------------------------------------------------ */
-/* Cell-centred acceleration and carry from the parent, Sec. 2.2 (reading R8, */
-/* R10): for c in [-1, N]^3                                                   */
-/*   phi(c)   = phis(c) + I(parent phi)(c)                                    */
-/*   acc_j(c) = -(phis(c+e_j) - phis(c-e_j)) / (2 delta) + I(parent acc_j)(c) */
-/* phis spans [-2, N+2)^3, phi and acc (3 SoA components) span [-1, N+1)^3,   */
-/* parent fields span the parent's [-1, Np+1)^3.  I is trilinear from the    */
-/* parent cell centres.  pphi == NULL: no parent term (root).                 */
+/* Spectral gradient (Sec. 2.2, D = -ik; reading R15): phi-hat = T rho-hat as */
+/* in orc_solve, and each short-range acceleration component                  */
+/* A_j = -d phi / dx_j is the inverse transform of -i D_j phi-hat, D_j = k_j  */
+/* (0 on an even M_j's Nyquist mode).  Writes four windows of W cells one     */
+/* after the other: phi, A_x, A_y, A_z.                                       */
 /* ------------------------------------------------------------------------ */
-void orc_accel(const double* phis, const int64_t N[3], double delta, const int64_t start[3],
-               const double* pphi, const double* pacc, const int64_t Np[3],
+void orc_solve_spectral(const int64_t* gmf, const int64_t G[3], int F, const int64_t M[3],
+                        const int64_t s0[3], const int64_t W[3], const double* T, double delta,
+                        double* out, int nthreads) {
+    int64_t tot = M[0] * M[1] * M[2];
+    int64_t nw = W[0] * W[1] * W[2];
+    int64_t H[3] = {M[0] / 2 + 1, M[1] / 2 + 1, M[2] / 2 + 1};
+    double* sre = (double*)calloc((size_t)tot, sizeof(double));
+    double* sim = (double*)calloc((size_t)tot, sizeof(double));
+    double* re = (double*)malloc((size_t)tot * sizeof(double));
+    double* im = (double*)malloc((size_t)tot * sizeof(double));
+    for (int64_t z = 0; z < G[2]; ++z)
+        for (int64_t y = 0; y < G[1]; ++y)
+            for (int64_t x = 0; x < G[0]; ++x)
+                sre[x + M[0] * (y + M[1] * z)] = ldexp((double)gmf[x + G[0] * (y + G[1] * z)], -F);
+    orc_dft3(sre, sim, M, -1, nthreads);
+    for (int64_t z = 0; z < M[2]; ++z)
+        for (int64_t y = 0; y < M[1]; ++y)
+            for (int64_t x = 0; x < M[0]; ++x) {
+                int64_t fx = x <= M[0] / 2 ? x : M[0] - x;
+                int64_t fy = y <= M[1] / 2 ? y : M[1] - y;
+                int64_t fz = z <= M[2] / 2 ? z : M[2] - z;
+                double t = T[fx + H[0] * (fy + H[1] * fz)];
+                int64_t i = x + M[0] * (y + M[1] * z);
+                sre[i] *= t;
+                sim[i] *= t;
+            }
+    double norm = 1.0 / ((double)M[0] * (double)M[1] * (double)M[2]);
+    for (int comp = 0; comp < 4; ++comp) {
+        for (int64_t z = 0; z < M[2]; ++z)
+            for (int64_t y = 0; y < M[1]; ++y)
+                for (int64_t x = 0; x < M[0]; ++x) {
+                    int64_t i = x + M[0] * (y + M[1] * z);
+                    if (comp == 0) {
+                        re[i] = sre[i];
+                        im[i] = sim[i];
+                        continue;
+                    }
+                    int64_t kap[3] = {x, y, z};
+                    int j = comp - 1;
+                    int64_t kc = kap[j] > M[j] / 2 ? kap[j] - M[j] : kap[j];
+                    double d = orc_grad_d(2, kc, M[j], delta);
+                    /* -i d (a + i b) = d b - i d a */
+                    re[i] = d * sim[i];
+                    im[i] = -d * sre[i];
+                }
+        orc_dft3(re, im, M, +1, nthreads);
+        for (int64_t z = 0; z < W[2]; ++z)
+            for (int64_t y = 0; y < W[1]; ++y)
+                for (int64_t x = 0; x < W[0]; ++x) {
+                    int64_t mx = mod_pos(s0[0] + x, M[0]);
+                    int64_t my = mod_pos(s0[1] + y, M[1]);
+                    int64_t mz = mod_pos(s0[2] + z, M[2]);
+                    out[comp * nw + x + W[0] * (y + W[1] * z)] = re[mx + M[0] * (my + M[1] * mz)] * norm;
+                }
+    }
+    free(sre);
+    free(sim);
+    free(re);
+    free(im);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell-centred acceleration and carry from the parent, Sec. 2.2 (reading R8, */
+/* R10, R15): for c in [-1, N]^3                                              */
+/*   phi(c)   = phis(c) + I(parent phi)(c)                                    */
+/*   acc_j(c) = A_j(c) + I(parent acc_j)(c), where A_j is                     */
+/*     grad 0: -(phis(c+e_j) - phis(c-e_j)) / (2 delta)                       */
+/*     grad 1: -(8 (phis(c+e_j) - phis(c-e_j))                                */
+/*               - (phis(c+2e_j) - phis(c-2e_j))) / (12 delta)                */
+/*     grad 2: the spectral component j + 1 of orc_solve_spectral             */
+/* phis spans [-h, N+h)^3 (h = 3 for grad 1, else 2; grad 2: four such        */
+/* windows), phi and acc (3 SoA components) span [-1, N+1)^3, parent fields   */
+/* span the parent's [-1, Np+1)^3.  I is trilinear from the parent cell      */
+/* centres.  pphi == NULL: no parent term (root).                             */
+/* ------------------------------------------------------------------------ */
+void orc_accel(const double* phis, const int64_t N[3], int grad, double delta,
+               const int64_t start[3], const double* pphi, const double* pacc, const int64_t Np[3],
                const int64_t pstart[3], int R, double* phi, double* acc) {
-    int64_t S[3] = {N[0] + 4, N[1] + 4, N[2] + 4};
+    int64_t h = grad == 1 ? 3 : 2;
+    int64_t S[3] = {N[0] + 2 * h, N[1] + 2 * h, N[2] + 2 * h};
+    int64_t nw = S[0] * S[1] * S[2];
     int64_t E[3] = {N[0] + 2, N[1] + 2, N[2] + 2};
     int64_t Ep[3] = {Np[0] + 2, Np[1] + 2, Np[2] + 2};
     int64_t ncell = E[0] * E[1] * E[2];
@@ -614,11 +715,25 @@ void orc_accel(const double* phis, const int64_t N[3], double delta, const int64
         for (int64_t y = -1; y <= N[1]; ++y)
             for (int64_t x = -1; x <= N[0]; ++x) {
                 int64_t c[3] = {x, y, z};
-#define PHIS(a, b, d) phis[((a) + 2) + S[0] * (((b) + 2) + S[1] * ((d) + 2))]
+#define PHIS(a, b, d) phis[((a) + h) + S[0] * (((b) + h) + S[1] * ((d) + h))]
                 double p0 = PHIS(x, y, z);
-                double a0 = -(PHIS(x + 1, y, z) - PHIS(x - 1, y, z)) / (2.0 * delta);
-                double a1 = -(PHIS(x, y + 1, z) - PHIS(x, y - 1, z)) / (2.0 * delta);
-                double a2 = -(PHIS(x, y, z + 1) - PHIS(x, y, z - 1)) / (2.0 * delta);
+                double a0, a1, a2;
+                if (grad == 0) {
+                    a0 = -(PHIS(x + 1, y, z) - PHIS(x - 1, y, z)) / (2.0 * delta);
+                    a1 = -(PHIS(x, y + 1, z) - PHIS(x, y - 1, z)) / (2.0 * delta);
+                    a2 = -(PHIS(x, y, z + 1) - PHIS(x, y, z - 1)) / (2.0 * delta);
+                } else if (grad == 1) {
+                    a0 = -(8.0 * (PHIS(x + 1, y, z) - PHIS(x - 1, y, z))
+                           - (PHIS(x + 2, y, z) - PHIS(x - 2, y, z))) / (12.0 * delta);
+                    a1 = -(8.0 * (PHIS(x, y + 1, z) - PHIS(x, y - 1, z))
+                           - (PHIS(x, y + 2, z) - PHIS(x, y - 2, z))) / (12.0 * delta);
+                    a2 = -(8.0 * (PHIS(x, y, z + 1) - PHIS(x, y, z - 1))
+                           - (PHIS(x, y, z + 2) - PHIS(x, y, z - 2))) / (12.0 * delta);
+                } else {
+                    a0 = (phis + nw)[(x + h) + S[0] * ((y + h) + S[1] * (z + h))];
+                    a1 = (phis + 2 * nw)[(x + h) + S[0] * ((y + h) + S[1] * (z + h))];
+                    a2 = (phis + 3 * nw)[(x + h) + S[0] * ((y + h) + S[1] * (z + h))];
+                }
 #undef PHIS
                 if (pphi) {
                     int64_t i0[3];

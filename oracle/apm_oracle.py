@@ -42,11 +42,13 @@ def lib():
         L.orc_alias_sum.restype = d
         L.orc_alias_sum.argtypes = [P, P]
         L.orc_green_opt.restype = d
-        L.orc_green_opt.argtypes = [P, P, d, d, d, ci]
+        L.orc_green_opt.argtypes = [P, P, d, d, d, ci, ci]
+        L.orc_grad_d.restype = d
+        L.orc_grad_d.argtypes = [ci, i64, i64, d]
         L.orc_dft3.restype = None
         L.orc_dft3.argtypes = [P, P, P, ci, ci]
         L.orc_green_table.restype = None
-        L.orc_green_table.argtypes = [ci, P, d, d, d, ci, P, ci]
+        L.orc_green_table.argtypes = [ci, P, d, d, d, ci, ci, P, ci]
         L.orc_drift.restype = d
         L.orc_drift.argtypes = [d, d, d, d, ci]
         L.orc_kick_drift.restype = None
@@ -62,7 +64,9 @@ def lib():
         L.orc_solve.restype = None
         L.orc_solve.argtypes = [P, P, ci, P, P, P, P, P, ci]
         L.orc_accel.restype = None
-        L.orc_accel.argtypes = [P, P, d, P, P, P, P, P, ci, P, P]
+        L.orc_solve_spectral.restype = None
+        L.orc_solve_spectral.argtypes = [P, P, ci, P, P, P, P, d, P, ci]
+        L.orc_accel.argtypes = [P, P, ci, d, P, P, P, P, P, ci, P, P]
         L.orc_interp.restype = None
         L.orc_interp.argtypes = [i64, P, P, P, P, P, P, d, d, ci, d, ci, P, P, ci, P, P, i32, P]
         L.orc_cells.restype = None
@@ -105,12 +109,20 @@ def alias_sum(kappa, M):
     return lib().orc_alias_sum(_p(_i64(kappa)), _p(_i64(M)))
 
 
-def green_opt(kappa, M, delta, a_lev, a_par, use_parent):
+GRADIENTS = {"fd2": 0, "fd4": 1, "spectral": 2}
+
+
+def grad_d(gradient, kc, M, delta):
+    """Gradient operator D_j at the centred mode kc of an M grid (orc_grad_d)."""
+    return lib().orc_grad_d(GRADIENTS[gradient], int(kc), int(M), float(delta))
+
+
+def green_opt(kappa, M, delta, a_lev, a_par, use_parent, gradient="fd2"):
     """Optimal influence function at one mode (Eq. influence), continuum units."""
     k = _i64(kappa)
     m = _i64(M)
     return lib().orc_green_opt(_p(k), _p(m), float(delta), float(a_lev), float(a_par),
-                               int(use_parent))
+                               int(use_parent), GRADIENTS[gradient])
 
 
 def dft3(re, im, sign):
@@ -162,6 +174,7 @@ class Config:
     periodic: bool = False       # root boundary (Sec. 3: isolated except Sec. 3.4)
     mass_frac_bits: int = 52     # fixed-point fraction bits of the GMF
     root_correction: bool = True # reading R4
+    gradient: str = "fd2"        # Sec. 2.2 gradient operator: "fd2", "fd4", "spectral" (R15)
 
 
 @dataclass
@@ -185,6 +198,14 @@ def smooth7_at_least(n):
         m += 1
 
 
+def even_smooth7_at_least(n):
+    """Smallest even integer >= n whose prime factors are all in {2, 3, 5, 7}."""
+    m = smooth7_at_least(n)
+    while m % 2:
+        m = smooth7_at_least(m + 1)
+    return m
+
+
 def border_cells(cfg):
     """Reading R6: B = ceil(0.65 R a/delta) cells per side (= 5 for R = 2, 3.4)."""
     return int(math.ceil(cfg.pad_factor * cfg.refine * cfg.a_over_dx - 1e-12))
@@ -200,8 +221,8 @@ class Plan:
     G: tuple       # GMF box (x, y, z)
     lo: tuple      # global level index of GMF cell 0
     M: tuple       # FFT lengths
-    s0: tuple      # M-grid index of output cell -2
-    W: tuple       # output window (N + 4)
+    s0: tuple      # M-grid index of output cell -h
+    W: tuple       # output window (N + 2h), h = 3 for the four-point gradient, else 2
     mode: int      # 0 refined (drop), 1 isolated root (fold), 2 periodic root (wrap)
     kind: int      # green table kind: 0 refined, 1 periodic root, 2 isolated root
 
@@ -217,21 +238,28 @@ def plan_grid(cfg, grids, gi):
     delta = cfg.box / (N0 * cfg.refine ** g.level)
     a_lev = cfg.a_over_dx * delta
     N = tuple(int(v) for v in g.dims)
+    h = 3 if cfg.gradient == "fd4" else 2
+    W = tuple(v + 2 * h for v in N)
     if g.level == 0:
         if cfg.periodic:
             M = N
             kind, mode = 1, 2
+        elif cfg.gradient == "fd4":
+            # reading R15: the four-point difference at the root's edge cells
+            # reads phi two cells outside, at offsets up to N + 1 from the
+            # masses, which the doubled grid must hold without wrapping
+            M = tuple(even_smooth7_at_least(2 * v + 2) for v in N)
+            kind, mode = 2, 1
         else:
             M = tuple(2 * v for v in N)
             kind, mode = 2, 1
-        return Plan(0, delta, a_lev, 0.0, 0, N, (0, 0, 0), M, (-2, -2, -2),
-                    tuple(v + 4 for v in N), mode, kind)
+        return Plan(0, delta, a_lev, 0.0, 0, N, (0, 0, 0), M, (-h, -h, -h), W, mode, kind)
     B = border_cells(cfg)
     G = tuple(v + 2 * B for v in N)
     M = tuple(smooth7_at_least(v + 4 * B) for v in N)
     lo = tuple(int(s) - B for s in g.start)
     return Plan(g.level, delta, a_lev, cfg.refine * a_lev, B, G, lo, M,
-                (B - 2, B - 2, B - 2), tuple(v + 4 for v in N), 0, 0)
+                (B - h, B - h, B - h), W, 0, 0)
 
 
 _table_cache = {}
@@ -239,12 +267,12 @@ _table_cache = {}
 
 def green_table(cfg, plan):
     """Octant table T[kz, ky, kx] (kappa_j in [0, M_j/2]) in DFT units."""
-    key = (plan.kind, plan.M, plan.delta, plan.a_lev, plan.a_par, cfg.root_correction)
+    key = (plan.kind, plan.M, plan.delta, plan.a_lev, plan.a_par, cfg.root_correction, cfg.gradient)
     if key not in _table_cache:
         H = tuple(m // 2 + 1 for m in plan.M)
         T = np.zeros(H[::-1], dtype=np.float64)
         lib().orc_green_table(plan.kind, _p(_i64(plan.M)), plan.delta, plan.a_lev, plan.a_par,
-                              int(cfg.root_correction), _p(T), nthreads())
+                              int(cfg.root_correction), GRADIENTS[cfg.gradient], _p(T), nthreads())
         _table_cache[key] = T
     return _table_cache[key]
 
@@ -293,19 +321,27 @@ def deposit(cfg, grids, gi, particles, half_dt, gas=None, parent_gas=None):
 
 
 def solve(cfg, grids, gi, gmf):
-    """Phi_short on [-2, N+2)^3 ([z, y, x]) of grid gi (Sec. 2.2, readings R4-R6)."""
+    """Phi_short on [-h, N+h)^3 ([z, y, x]) of grid gi (Sec. 2.2, readings R4-R6);
+    with the spectral gradient (R15) a (4, ...) array: phi_short, A_x, A_y, A_z."""
     plan = plan_grid(cfg, grids, gi)
     T = green_table(cfg, plan)
     W = plan.W
-    phis = np.zeros(W[::-1], dtype=np.float64)
     g = np.ascontiguousarray(gmf, dtype=np.int64)
+    if cfg.gradient == "spectral":
+        phis = np.zeros((4,) + W[::-1], dtype=np.float64)
+        lib().orc_solve_spectral(_p(g), _p(_i64(plan.G)), cfg.mass_frac_bits, _p(_i64(plan.M)),
+                                 _p(_i64(plan.s0)), _p(_i64(W)), _p(T), plan.delta, _p(phis),
+                                 nthreads())
+        return phis
+    phis = np.zeros(W[::-1], dtype=np.float64)
     lib().orc_solve(_p(g), _p(_i64(plan.G)), cfg.mass_frac_bits, _p(_i64(plan.M)),
                     _p(_i64(plan.s0)), _p(_i64(W)), _p(T), _p(phis), nthreads())
     return phis
 
 
 def accel(cfg, grids, gi, phis, parent_phi=None, parent_acc=None):
-    """(phi, acc) on [-1, N+1)^3: FD of Phi_short plus trilinear parent carry."""
+    """(phi, acc) on [-1, N+1)^3: gradient of Phi_short (R8, R15) plus trilinear
+    parent carry."""
     plan = plan_grid(cfg, grids, gi)
     g = grids[gi]
     E = tuple(v + 2 for v in g.dims)
@@ -319,8 +355,9 @@ def accel(cfg, grids, gi, phis, parent_phi=None, parent_acc=None):
     else:
         Np, pstart, pphi, pacc = _i64([1, 1, 1]), _i64([0, 0, 0]), None, None
     ps = np.ascontiguousarray(phis, dtype=np.float64)
-    lib().orc_accel(_p(ps), _p(_i64(g.dims)), plan.delta, _p(_i64(g.start)), _p(pphi), _p(pacc),
-                    _p(Np), _p(pstart), cfg.refine, _p(phi), _p(acc))
+    lib().orc_accel(_p(ps), _p(_i64(g.dims)), GRADIENTS[cfg.gradient], plan.delta,
+                    _p(_i64(g.start)), _p(pphi), _p(pacc), _p(Np), _p(pstart), cfg.refine, _p(phi),
+                    _p(acc))
     return phi, acc
 
 
