@@ -59,6 +59,19 @@ typedef enum {
 typedef enum { APM_FP32 = 0, APM_FP64 = 1 } apm_precision;
 typedef enum { APM_BC_ISOLATED = 0, APM_BC_PERIODIC = 1 } apm_bc;
 
+/* Gradient operator D (Sec. 2.2: the influence function Eq. influence is built
+ * for the operator the accelerations use; the paper allows a finite difference
+ * or the direct Fourier-space gradient D = -ik):
+ *  APM_GRAD_FD2      two-point centred difference, D_j = sin(k_j delta)/delta;
+ *                    A_j(c) = -(phi(c+1) - phi(c-1)) / (2 delta)
+ *  APM_GRAD_FD4      four-point difference,
+ *                    D_j = (8 sin(k_j delta) - sin(2 k_j delta)) / (6 delta);
+ *                    A_j(c) = -(8 (phi(c+1) - phi(c-1)) - (phi(c+2) - phi(c-2))) / (12 delta)
+ *  APM_GRAD_SPECTRAL D_j = k_j (0 on the Nyquist mode of an even M_j); the
+ *                    short-range accelerations are transformed back from
+ *                    -i D_j T rho-hat, one inverse transform per component. */
+typedef enum { APM_GRAD_FD2 = 0, APM_GRAD_FD4 = 1, APM_GRAD_SPECTRAL = 2 } apm_gradient;
+
 /* Method parameters.  Defaults (apm_config_default) are the paper's:
  * a = 3.4 delta_l and R = 2 (Sec. 2.2), padding factor 0.65 (Sec. 2.2),
  * isolated root (Sec. 3), FP32 field arithmetic, 52 fraction bits. */
@@ -74,6 +87,7 @@ typedef struct {
     int32_t root_correction; /* isolated root: 1 adds the k-space optimal correction
                                 to the real-space kernel (see apm_set_hierarchy) */
     int32_t device;          /* CUDA device ordinal of the context; -1: current device */
+    int32_t gradient;        /* apm_gradient (default APM_GRAD_FD2) */
 } apm_config;
 
 /* One grid.  start: global level-`level` cell index of the first interior cell
@@ -98,12 +112,17 @@ typedef struct {
     int32_t level;
     int32_t border;       /* B: GMF border cells per side (0 on the root) */
     int32_t gmf[3];       /* GMF box: dims + 2B (root: dims) */
-    int32_t fft[3];       /* FFT lengths M (isolated root 2 N0, periodic root N0,
-                             refined: smallest {2,3,5,7}-smooth >= dims + 4B) */
-    int32_t phi_short[3]; /* dims + 4: cells [-2, dims+2) */
+    int32_t fft[3];       /* FFT lengths M (isolated root 2 N0, or with APM_GRAD_FD4
+                             the smallest even {2,3,5,7}-smooth >= 2 N0 + 2;
+                             periodic root N0; refined: smallest
+                             {2,3,5,7}-smooth >= dims + 4B) */
+    int32_t phi_short[3]; /* dims + 2h: cells [-h, dims+h), h = 3 for APM_GRAD_FD4,
+                             else 2 */
     int32_t field[3];     /* dims + 2: cells [-1, dims+1) of phi and each acc component */
     int32_t level_index;  /* position of the grid among the grids of its level */
     double delta;         /* cell size box / (N0 R^level) */
+    int32_t phi_short_comps; /* components of phi_short: 1, or 4 (phi, A_x, A_y, A_z
+                                short-range) for APM_GRAD_SPECTRAL */
 } apm_grid_info;
 
 typedef struct apm_ctx apm_ctx;
@@ -194,12 +213,17 @@ apm_status apm_deposit_all(apm_ctx* ctx, const apm_particles* particles, double 
  * `level` (Sec. 2.2, Eq. PoissonFourier with Eq. influence): the GMF cell
  * masses (gmf * 2^-F, converted in FP64) are zero-padded onto the grid's M
  * grid, transformed, multiplied by the Green's table, transformed back, and
- * the window of cells [-2, dims+2) is written:
+ * the window of cells [-h, dims+h) is written:
  *  phi_short: HOST array (grids of the level) of device pointers to
- *             (dims+4)^3 floats/doubles (apm_grid_info.phi_short)
+ *             comps x (dims+2h)^3 floats/doubles (apm_grid_info.phi_short,
+ *             phi_short_comps; h = 3 for APM_GRAD_FD4, else 2).  With
+ *             APM_GRAD_SPECTRAL the components are phi_short and the
+ *             short-range accelerations A_x, A_y, A_z, each the inverse
+ *             transform of -i D_j T rho-hat.
  * The FFTs are hand-written mixed-radix Stockham passes (radices 2-8; the
  * FP32 path also 6, 9, 10, 12, 14, 15, 16 in registers), five launches: x
- * forward, y forward, z forward + table + z inverse, y inverse, x inverse. */
+ * forward, y forward, z forward + table + z inverse, y inverse, x inverse
+ * (the last three once per component). */
 apm_status apm_solve_level(apm_ctx* ctx, int32_t level, const int64_t* const* gmf,
                            void* const* phi_short, void* stream);
 
@@ -208,7 +232,9 @@ apm_status apm_solve_level(apm_ctx* ctx, int32_t level, const int64_t* const* gm
  * acceleration interpolated onto the refined grid):
  *   phi      = phi_short + I(parent phi)
  *   acc_j    = -(phi_short(c + e_j) - phi_short(c - e_j)) / (2 delta) + I(parent acc_j)
- * with I the trilinear interpolation from parent cell centres, in FP64.
+ * with I the trilinear interpolation from parent cell centres, in FP64.  With
+ * APM_GRAD_FD4 the difference is the four-point one, with APM_GRAD_SPECTRAL
+ * the short-range term is the solve's A_j component (see apm_gradient).
  *  parent_phi, parent_acc: HOST arrays (grids of level-1) of the parent level's
  *             phi / acc outputs, or NULL at level 0 (no parent term)
  *  phi      : HOST array of device pointers to (dims+2)^3 values

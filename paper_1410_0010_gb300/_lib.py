@@ -13,12 +13,14 @@ STATUS_NAMES = {0: "APM_OK", 1: "APM_E_INVALID", 2: "APM_E_NESTING", 3: "APM_E_N
                 8: "APM_E_UNSUPPORTED", 9: "APM_E_STATE"}
 APM_FP32, APM_FP64 = 0, 1
 APM_BC_ISOLATED, APM_BC_PERIODIC = 0, 1
+APM_GRAD_FD2, APM_GRAD_FD4, APM_GRAD_SPECTRAL = 0, 1, 2
+GRADIENTS = {"fd2": APM_GRAD_FD2, "fd4": APM_GRAD_FD4, "spectral": APM_GRAD_SPECTRAL}
 
 
 class ApmConfig(ctypes.Structure):
     _fields_ = [("box", c_dbl), ("a_over_dx", c_dbl), ("refine", c_i32), ("pad_factor", c_dbl),
                 ("root_bc", c_i32), ("precision", c_i32), ("mass_frac_bits", c_i32),
-                ("root_correction", c_i32), ("device", c_i32)]
+                ("root_correction", c_i32), ("device", c_i32), ("gradient", c_i32)]
 
 
 class ApmGrid(ctypes.Structure):
@@ -33,7 +35,7 @@ class ApmParticles(ctypes.Structure):
 class ApmGridInfo(ctypes.Structure):
     _fields_ = [("level", c_i32), ("border", c_i32), ("gmf", c_i32 * 3), ("fft", c_i32 * 3),
                 ("phi_short", c_i32 * 3), ("field", c_i32 * 3), ("level_index", c_i32),
-                ("delta", c_dbl)]
+                ("delta", c_dbl), ("phi_short_comps", c_i32)]
 
 
 class ApmFftShapes(ctypes.Structure):

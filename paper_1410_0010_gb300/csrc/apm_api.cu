@@ -18,6 +18,7 @@ namespace {
 constexpr int kRoles = 11;
 enum Role { R_GMF = 0, R_GAS, R_PGAS, R_GMF_IN, R_PHIS, R_PHIS_IN, R_PPHI, R_PACC, R_PHI, R_ACC, R_ACC_IN };
 constexpr int kChunkCells = 2048;
+constexpr double kPiHost = 3.141592653589793238462643383279502884;
 
 // kernels, in launch order of one level
 enum Kern { K_GAS = 0, K_DEPOSIT, K_XF, K_YF, K_Z, K_YI, K_XI, K_ACCEL, K_INTERP, K_COUNT };
@@ -81,6 +82,7 @@ struct apm_ctx {
     float* tab32 = nullptr;
     void* wsA = nullptr;
     void* wsB = nullptr;
+    void* wsC = nullptr;             // spectral gradient: the y-inverse output, so wsB keeps the forward
     LevelDev* d_levels = nullptr;    // every level's LevelDev (the all-level kernels)
     void** d_tabs = nullptr;         // [role][level]: each level's device pointer table of the role
     Profiler prof;
@@ -145,7 +147,7 @@ void free_hierarchy(apm_ctx* c) {
     c->level_of.clear();
     c->index_in_level.clear();
     c->tw64 = nullptr; c->tw32 = nullptr; c->tab64 = nullptr; c->tab32 = nullptr;
-    c->wsA = nullptr; c->wsB = nullptr;
+    c->wsA = nullptr; c->wsB = nullptr; c->wsC = nullptr;
     c->d_levels = nullptr; c->d_tabs = nullptr;
     c->has_hier = false;
 }
@@ -157,6 +159,15 @@ int smooth7_at_least(int n) {
             while (r % p == 0) r /= p;
         if (r == 1) return m;
     }
+}
+
+// the isolated root's transform length with the four-point gradient: even, and
+// at least 2 N + 2 so that phi at cells -2 and N + 1 (read by the stencils of
+// the edge cells) sees every mass at its true offset
+int even_smooth7_at_least(int n) {
+    int m = smooth7_at_least(n);
+    while (m & 1) m = smooth7_at_least(m + 1);
+    return m;
 }
 
 long long floor_div(long long a, long long b) {
@@ -306,8 +317,11 @@ void apply_pass(Level& L, int q) {
 }
 
 // launches FFT pass q of a level with plan P
+// comp: with the spectral gradient, the component (0 phi, 1-3 A_x..A_z) of
+// the z, y-inverse and x-inverse passes; the y inverse then writes wsC, so
+// the y-forward output in wsB stays for the next component's z pass.
 cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void** d_gmf, void** d_phis,
-                     cudaStream_t s) {
+                     cudaStream_t s, int comp = 0) {
     const bool f64 = c->cfg.precision == APM_FP64;
     FftArgs a;
     a.g = L.d_grids;
@@ -322,12 +336,16 @@ cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void*
     a.threads = P.threads;
     a.status = c->d_status;
     a.inject_wait = fault_wait() ? 1 : 0;
+    a.comp = comp;
+    if (c->cfg.gradient == APM_GRAD_SPECTRAL && (q == kPassYi || q == kPassXi)) a.wsB = c->wsC;
     switch (q) {
         case kPassXf:
             return f64 ? launch_fft_xf<double>(a, (const int64_t* const*)d_gmf, s)
                        : launch_fft_xf<float>(a, (const int64_t* const*)d_gmf, s);
         case kPassYf: return f64 ? launch_fft_yf<double>(a, s) : launch_fft_yf<float>(a, s);
-        case kPassZ: return f64 ? launch_fft_z<double>(a, s) : launch_fft_z<float>(a, s);
+        case kPassZ:
+            if (comp > 0) return f64 ? launch_fft_zgrad<double>(a, s) : launch_fft_zgrad<float>(a, s);
+            return f64 ? launch_fft_z<double>(a, s) : launch_fft_z<float>(a, s);
         case kPassYi: return f64 ? launch_fft_yi<double>(a, s) : launch_fft_yi<float>(a, s);
         default: return f64 ? launch_fft_xi<double>(a, d_phis, s) : launch_fft_xi<float>(a, d_phis, s);
     }
@@ -416,6 +434,7 @@ void apm_config_default(apm_config* cfg) {
     cfg->mass_frac_bits = 52;
     cfg->root_correction = 1;
     cfg->device = -1;
+    cfg->gradient = APM_GRAD_FD2;
 }
 
 const char* apm_version(void) { return "apm-gb300 0.1 (sm_103a)"; }
@@ -442,7 +461,8 @@ apm_status apm_create(const apm_config* cfg, apm_ctx** out) {
     if (!(cfg->box > 0) || !(cfg->a_over_dx > 0) || cfg->refine < 2 || !(cfg->pad_factor >= 0) ||
         (cfg->root_bc != APM_BC_ISOLATED && cfg->root_bc != APM_BC_PERIODIC) ||
         (cfg->precision != APM_FP32 && cfg->precision != APM_FP64) || cfg->mass_frac_bits < 1 ||
-        cfg->mass_frac_bits > 62)
+        cfg->mass_frac_bits > 62 ||
+        (cfg->gradient != APM_GRAD_FD2 && cfg->gradient != APM_GRAD_FD4 && cfg->gradient != APM_GRAD_SPECTRAL))
         return APM_E_INVALID;
     if (cfg->refine != 2) return APM_E_UNSUPPORTED;
     apm_ctx* c = new apm_ctx();
@@ -504,6 +524,7 @@ apm_status apm_get_grid_info(const apm_ctx* c, int32_t grid, apm_grid_info* out)
     }
     out->level_index = c->index_in_level[grid];
     out->delta = g.delta;
+    out->phi_short_comps = c->cfg.gradient == APM_GRAD_SPECTRAL ? 4 : 1;
     return APM_OK;
 }
 
@@ -563,10 +584,12 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             const double delta = cfg.box / ((double)N0 * std::pow((double)cfg.refine, a.level));
             const double a_lev = cfg.a_over_dx * delta;
             g.delta = delta;
+            g.grad = cfg.gradient;
+            g.h = cfg.gradient == APM_GRAD_FD4 ? 3 : 2;
             for (int j = 0; j < 3; ++j) {
                 g.N[j] = a.dims[j];
                 g.start[j] = a.start[j];
-                g.W[j] = a.dims[j] + 4;
+                g.W[j] = a.dims[j] + 2 * g.h;
             }
             double a_par = 0.0;
             if (a.level == 0) {
@@ -574,9 +597,11 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
                 g.mode = periodic ? 2 : 1;
                 for (int j = 0; j < 3; ++j) {
                     g.G[j] = a.dims[j];
-                    g.M[j] = periodic ? a.dims[j] : 2 * a.dims[j];
+                    g.M[j] = periodic ? a.dims[j]
+                                      : (cfg.gradient == APM_GRAD_FD4 ? even_smooth7_at_least(2 * a.dims[j] + 2)
+                                                                      : 2 * a.dims[j]);
                     g.lo[j] = 0;
-                    g.s0[j] = g.M[j] - 2;
+                    g.s0[j] = ((g.M[j] - g.h) % g.M[j] + g.M[j]) % g.M[j];
                 }
                 g.parent = -1;
             } else {
@@ -587,7 +612,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
                     g.G[j] = a.dims[j] + 2 * B;
                     g.M[j] = smooth7_at_least(a.dims[j] + 4 * B);
                     g.lo[j] = a.start[j] - B;
-                    g.s0[j] = B - 2;
+                    g.s0[j] = ((B - g.h) % g.M[j] + g.M[j]) % g.M[j];
                 }
                 const apm_grid& p = grids[a.parent];
                 g.parent = c->index_in_level[a.parent];
@@ -601,7 +626,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             }
             // 32-bit cell indices inside the kernels
             if ((long long)g.G[0] * g.G[1] * g.G[2] >= (1LL << 31) ||
-                (long long)(g.N[0] + 4) * (g.N[1] + 4) * (g.N[2] + 4) >= (1LL << 31))
+                (long long)g.W[0] * g.W[1] * g.W[2] * (cfg.gradient == APM_GRAD_SPECTRAL ? 4 : 1) >= (1LL << 31))
                 return APM_E_UNSUPPORTED;
             FftPlan1D* pls[3] = {&g.fx, &g.fy, &g.fz};
             for (int j = 0; j < 3; ++j) {
@@ -615,6 +640,8 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             g.Hz2 = g.M[2] / 2 + 1;
             g.cells_gmf = (long long)g.G[0] * g.G[1] * g.G[2];
             g.inv2d = 0.5 / delta;
+            g.inv12d = 1.0 / (12.0 * delta);
+            for (int j = 0; j < 3; ++j) g.dk[j] = 2.0 * kPiHost / ((double)g.M[j] * delta);
             g.inv_m3 = 1.0 / ((double)g.M[0] * (double)g.M[1] * (double)g.M[2]);
             g.rows_gas = std::max(1, kChunkCells / g.G[0]);
             // 2x2x2 output blocks pair level cells (2k+1, 2k+2), the two children
@@ -657,6 +684,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
     if (!f64 && (st = dmalloc(c, (void**)&c->tab32, tab_total * sizeof(float))) != APM_OK) return st;
     if ((st = dmalloc(c, &c->wsA, wsA_max * csz)) != APM_OK) return st;
     if ((st = dmalloc(c, &c->wsB, wsB_max * csz)) != APM_OK) return st;
+    if (cfg.gradient == APM_GRAD_SPECTRAL && (st = dmalloc(c, &c->wsC, wsB_max * csz)) != APM_OK) return st;
     double* scratch = nullptr;
     if ((st = dmalloc(c, (void**)&scratch, tab_max * sizeof(double))) != APM_OK) return st;
     for (auto& kv : tw_off)
@@ -666,7 +694,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
         const TabKey& k = t.first;
         int M[3] = {std::get<1>(k), std::get<2>(k), std::get<3>(k)};
         if (launch_green_table(std::get<0>(k), M, std::get<4>(k), std::get<5>(k), std::get<6>(k),
-                               cfg.root_correction, c->tab64 + t.second, scratch, 0) != cudaSuccess)
+                               cfg.root_correction, cfg.gradient, c->tab64 + t.second, scratch, 0) != cudaSuccess)
             return APM_E_CUDA;
     }
     if (!f64 && launch_to_f32(c->tab64, c->tab32, tab_total, 0) != cudaSuccess) return APM_E_CUDA;
@@ -679,9 +707,15 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             const GridDev& g = L.hg[k];
             const long long grows = (long long)g.G[1] * g.G[2];
             for (long long t = 0; t < (grows + g.rows_gas - 1) / g.rows_gas; ++t) gas.push_back({k, (int)t});
-            const long long nblocks = (long long)g.acc_nb[0] * g.acc_nb[1] * g.acc_nb[2];
-            for (long long t = 0; t < (nblocks + kAccBlocksPerCta - 1) / kAccBlocksPerCta; ++t)
-                acc.push_back({k, (int)t});
+            if (cfg.gradient == APM_GRAD_FD2) {   // k_accel: 2x2x2 blocks
+                const long long nblocks = (long long)g.acc_nb[0] * g.acc_nb[1] * g.acc_nb[2];
+                for (long long t = 0; t < (nblocks + kAccBlocksPerCta - 1) / kAccBlocksPerCta; ++t)
+                    acc.push_back({k, (int)t});
+            } else {                              // k_accel_cells: output cells
+                const long long ncell = (long long)(g.N[0] + 2) * (g.N[1] + 2) * (g.N[2] + 2);
+                for (long long t = 0; t < (ncell + kCellsPerCta - 1) / kCellsPerCta; ++t)
+                    acc.push_back({k, (int)t});
+            }
         }
         for (int q = 0; q < kFftPasses; ++q) {
             if ((st = build_pass(c, L, q, f64 ? kFftBudgetF64 : kFftBudgetF32, kFftThreads, f64, L.pass[q])) != APM_OK)
@@ -902,10 +936,18 @@ apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
     if ((st = set_ptrs(c, L, R_GMF_IN, (const void* const*)gmf, ng, &d_gmf, s)) != APM_OK) return st;
     if ((st = set_ptrs(c, L, R_PHIS, (const void* const*)phi_short, ng, &d_phis, s)) != APM_OK) return st;
     const Kern kind[kFftPasses] = {K_XF, K_YF, K_Z, K_YI, K_XI};
+    const int ncomp = c->cfg.gradient == APM_GRAD_SPECTRAL ? 4 : 1;
     for (int q = 0; q < kFftPasses; ++q) {
         Trace t(c, kind[q], s);
         if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) return APM_E_CUDA;
     }
+    // the spectral gradient's acceleration components: z (table times
+    // -i D_comp), y inverse and x inverse again on the kept forward transform
+    for (int comp = 1; comp < ncomp; ++comp)
+        for (int q = kPassZ; q < kFftPasses; ++q) {
+            Trace t(c, kind[q], s);
+            if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, comp) != cudaSuccess) return APM_E_CUDA;
+        }
     return APM_OK;
 }
 
@@ -981,6 +1023,11 @@ apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* g
         // the chosen shape leaves this pass's output in place for the next pass
         if (st == APM_OK && run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) st = APM_E_CUDA;
     }
+    // the spectral gradient's other components with the chosen shapes
+    const int ncomp = c->cfg.gradient == APM_GRAD_SPECTRAL ? 4 : 1;
+    for (int comp = 1; comp < ncomp && st == APM_OK; ++comp)
+        for (int q = kPassZ; q < kFftPasses && st == APM_OK; ++q)
+            if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, comp) != cudaSuccess) st = APM_E_CUDA;
     if (st != APM_OK) {   // keep the descriptors consistent with the plans in use
         for (int q = 0; q < kFftPasses; ++q) apply_pass(L, q);
         cudaStreamSynchronize(s);
@@ -1049,11 +1096,20 @@ apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,
         pgrids = P.d_grids;
     }
     Trace t(c, K_ACCEL, s);
-    cudaError_t e = c->cfg.precision == APM_FP64
-        ? launch_accel<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                               (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s)
-        : launch_accel<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                              (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s);
+    const int grad = c->cfg.gradient;
+    cudaError_t e;
+    if (grad == APM_GRAD_FD2)
+        e = c->cfg.precision == APM_FP64
+            ? launch_accel<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                   (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s)
+            : launch_accel<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                  (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s);
+    else
+        e = c->cfg.precision == APM_FP64
+            ? launch_accel_cells<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                         (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, grad, s)
+            : launch_accel_cells<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                        (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, grad, s);
     return cuda_status(e);
 }
 

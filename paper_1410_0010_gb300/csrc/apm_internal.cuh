@@ -155,6 +155,10 @@ struct GridDev {
     int acc_nb[3];       // output blocks per axis
     double inv2d;        // 1 / (2 delta)
     double inv_m3;       // 1 / (M0 M1 M2), the inverse transform's normalisation
+    int grad;            // gradient operator (apm_gradient): 0 two-point, 1 four-point, 2 spectral
+    int h;               // phi_short window half-width: cells [-h, N+h) (3 four-point, else 2)
+    double dk[3];        // 2 pi / (M_j delta): the spectral gradient's k per mode index
+    double inv12d;       // 1 / (12 delta)
 };
 
 // Threads of a CTA walking a batch of rows [r0, r1) of length n in row-major
@@ -403,7 +407,7 @@ cudaError_t launch_twiddles(double2* tw64, float2* tw32, int L, cudaStream_t s);
 
 // Green's tables (FP64 octant), kind 0/1 directly, kind 2 from the real-space kernel
 cudaError_t launch_green_table(int kind, const int M[3], double delta, double a_lev,
-                               double a_par, int correction, double* out, double* scratch,
+                               double a_par, int correction, int grad, double* out, double* scratch,
                                cudaStream_t s);
 cudaError_t launch_to_f32(const double* in, float* out, long long n, cudaStream_t s);
 
@@ -433,6 +437,7 @@ struct FftArgs {
     int threads;           // threads per CTA: 128 or 256
     unsigned* status;      // device status word (bounded waits that ran out), or null
     int inject_wait = 0;   // fault injection: the x-forward bulk copy's wait runs out
+    int comp = 0;          // spectral gradient: component of the z / xi passes (0 phi, 1-3 A_x..A_z)
 };
 cudaError_t fft_configure();
 template <typename T>
@@ -443,8 +448,22 @@ template <typename T>
 cudaError_t launch_fft_z(const FftArgs& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_yi(const FftArgs& a, cudaStream_t s);
+// the z pass of a spectral-gradient component (a.comp in 1..3): the table
+// times -i D_comp between the forward and the inverse transform
+template <typename T>
+cudaError_t launch_fft_zgrad(const FftArgs& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
+
+// accelerations + parent carry, one thread per output cell, for the four-point
+// and spectral gradients (the two-point one runs launch_accel); chunks hold
+// kCellsPerCta output cells of one grid each
+constexpr int kCellsPerCta = 1024;
+template <typename T>
+cudaError_t launch_accel_cells(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
+                               const void* const* pphi, const void* const* pacc, void* const* phi,
+                               void* const* acc, const Chunk* chunks, int n_chunks, int grad,
+                               cudaStream_t s);
 
 // FD accelerations + parent carry; TSC interpolation
 template <typename T>

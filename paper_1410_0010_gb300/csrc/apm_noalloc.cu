@@ -155,7 +155,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     if (cudaGetLastError() != cudaSuccess) return APM_E_CUDA;
     if (launch_twiddles(tw64, tw32, n, s) != cudaSuccess) return APM_E_CUDA;
     const int M[3] = {n, n, n};
-    if (launch_green_table(1, M, delta, a_over_dx * delta, 0.0, 0, tab64, nullptr, s) != cudaSuccess)
+    if (launch_green_table(1, M, delta, a_over_dx * delta, 0.0, 0, APM_GRAD_FD2, tab64, nullptr, s) != cudaSuccess)
         return APM_E_CUDA;
     if (launch_to_f32(tab64, tab32, tab, s) != cudaSuccess) return APM_E_CUDA;
 

@@ -21,6 +21,7 @@
 // Zero-padded inputs are never read and outputs outside the window never
 // written.  Lines of the y/z passes are tiles of consecutive kx (coalesced).
 #pragma once
+#include <type_traits>
 #include <utility>
 
 #include "apm_internal.cuh"
@@ -534,10 +535,7 @@ __device__ __forceinline__ void stage_fwd_tab_inv(int L, int step, int lg, const
         if constexpr (R2 == 1) Dft<T, -1, R1>::run(v);
         else DftC<T, -1, R1, R2>::run(v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T t = tabf(j + r * nb);
-            v[r] = mk<T>(v[r].x * t, v[r].y * t);
-        }
+        for (int r = 0; r < R; ++r) v[r] = tabf.apply(j + r * nb, v[r]);
         if constexpr (R2 == 1) Dft<T, 1, R1>::run(v);
         else DftC<T, 1, R1, R2>::run(v);
 #pragma unroll
@@ -577,6 +575,29 @@ template <typename T> struct TabCol {
     const T* __restrict__ p;   // at (|ky|, kx)
     int zst, L;
     __device__ T operator()(int kz) const { return p[(kz <= L / 2 ? kz : L - kz) * zst]; }
+    __device__ C<T> apply(int kz, C<T> v) const {
+        const T t = (*this)(kz);
+        return mk<T>(v.x * t, v.y * t);
+    }
+};
+
+// Spectral gradient component comp (1 x, 2 y, 3 z): v -> -i D T v with
+// D = k_comp, 0 on the Nyquist mode of an even length (the table is even, the
+// factor odd, so the product keeps the Hermitian symmetry of a real field).
+// dline: D of the column's kx (comp 1) or ky (comp 2); dz: 2 pi / (M2 delta).
+template <typename T> struct TabGrad {
+    TabCol<T> tab;
+    int comp;
+    T dline, dz;
+    __device__ C<T> apply(int kz, C<T> v) const {
+        T d = dline;
+        if (comp == 3) {
+            const int L = tab.L;
+            d = 2 * kz == L ? T(0) : dz * (T)(kz <= L / 2 ? kz : kz - L);
+        }
+        const T s = tab(kz) * d;
+        return mk<T>(v.y * s, -v.x * s);
+    }
 };
 
 template <typename T, int AX, int MODE, int NT>
@@ -584,7 +605,8 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
                                                      const Chunk* __restrict__ chunks,
                                                      const C<T>* __restrict__ tw_arena,
                                                      const T* __restrict__ tab,
-                                                     C<T>* __restrict__ wsA, C<T>* __restrict__ wsB) {
+                                                     C<T>* __restrict__ wsA, C<T>* __restrict__ wsB,
+                                                     int comp) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
     const int Hx = g.Hx;
@@ -625,14 +647,28 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     } else if (MODE == 2) {
         stages_io<T, 1, NT, false, false>(pl, 0, pl.nst - 1, lg, tw, in, out, cur, nxt, tx, line);
     } else {
-        // phi-hat = T(kappa) rho-hat between the forward and the inverse transform
+        // phi-hat = T(kappa) rho-hat between the forward and the inverse
+        // transform (MODE 1); MODE 3: -i D_comp T(kappa) rho-hat
         const FftPlan1D& ipl = g.iz;
         const int ky = other;
         const int fy = ky <= M1 / 2 ? ky : M1 - ky;
-        TabCol<T> tabf;
-        tabf.p = tab + (g.tab_off + (long long)fy * Hx + kx);
-        tabf.zst = g.Hy2 * Hx;     // the octant table holds < 2^31 entries
-        tabf.L = L;
+        TabCol<T> tabc;
+        tabc.p = tab + (g.tab_off + (long long)fy * Hx + kx);
+        tabc.zst = g.Hy2 * Hx;     // the octant table holds < 2^31 entries
+        tabc.L = L;
+        using Tab = typename std::conditional<MODE == 3, TabGrad<T>, TabCol<T>>::type;
+        Tab tabf;
+        if constexpr (MODE == 3) {
+            tabf.tab = tabc;
+            tabf.comp = comp;
+            tabf.dz = (T)g.dk[2];
+            const int M0 = g.M[0];
+            const int kyc = ky <= M1 / 2 ? ky : ky - M1;
+            tabf.dline = comp == 1 ? (2 * kx == M0 ? T(0) : (T)(g.dk[0] * kx))
+                                   : (comp == 2 ? (2 * ky == M1 ? T(0) : (T)(g.dk[1] * kyc)) : T(0));
+        } else {
+            tabf = tabc;
+        }
         const int n = pl.nst;
         const int R = pl.radix[n - 1];
         if (n == 1) {
@@ -789,7 +825,7 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
                                                     const Chunk* __restrict__ chunks,
                                                     const C<T>* __restrict__ tw_arena,
                                                     const C<T>* __restrict__ wsB,
-                                                    void* const* __restrict__ phis) {
+                                                    void* const* __restrict__ phis, int comp) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
     const int M0 = g.M[0], Hx = g.Hx, np = g.lines[kPassXi], W0 = g.W[0], lg = ilog2(np), es = np + 1;
@@ -807,7 +843,9 @@ __global__ void __launch_bounds__(NT, MinCtas<T>::value * (kFftThreads / NT)) k_
     in.nr0 = 2 * line < nr;
     in.nr1 = 2 * line + 1 < nr;
     XiOut<T> out;
-    out.p = reinterpret_cast<T*>(phis[ch.grid]) + (r_first + 2 * line) * W0;
+    // component comp of a spectral-gradient solve: the comp-th window of W cells
+    out.p = reinterpret_cast<T*>(phis[ch.grid]) + (long long)comp * g.W[0] * g.W[1] * g.W[2] +
+            (r_first + 2 * line) * W0;
     out.W0 = W0;
     out.s0 = g.s0[0];
     out.M0 = M0;

@@ -11,6 +11,8 @@ cudaError_t fft_configure_yi_f32();
 cudaError_t fft_configure_yf_f64();
 cudaError_t fft_configure_z_f64();
 cudaError_t fft_configure_yi_f64();
+cudaError_t fft_configure_zg_f32();
+cudaError_t fft_configure_zg_f64();
 
 // Allows every pass kernel up to kFftSmemLimit of dynamic shared memory
 // (above the 48 KB default).
@@ -24,7 +26,8 @@ cudaError_t fft_configure() {
         if (e != cudaSuccess) return e;
     }
     cudaError_t (*cols[])() = {fft_configure_yf_f32, fft_configure_z_f32, fft_configure_yi_f32,
-                               fft_configure_yf_f64, fft_configure_z_f64, fft_configure_yi_f64};
+                               fft_configure_zg_f32, fft_configure_yf_f64, fft_configure_z_f64,
+                               fft_configure_yi_f64, fft_configure_zg_f64};
     for (auto f : cols) {
         cudaError_t e = f();
         if (e != cudaSuccess) return e;
@@ -49,9 +52,9 @@ template <typename T>
 cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s) {
     if (a.n_chunks <= 0) return cudaSuccess;
     if (a.threads == 128)
-        k_xi<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis);
+        k_xi<T, 128><<<a.n_chunks, 128, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis, a.comp);
     else
-        k_xi<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis);
+        k_xi<T, 256><<<a.n_chunks, 256, a.smem, s>>>(a.g, a.chunks, (const C<T>*)a.tw, (const C<T>*)a.wsB, phis, a.comp);
     return cudaGetLastError();
 }
 

@@ -34,21 +34,32 @@ __device__ double shat(double eta) {
 // sinc(pi f) = sin(pi f) / (pi f)
 __device__ double sinc_pi(double f) { return f == 0.0 ? 1.0 : sinpi(f) / (kPi * f); }
 
+// Gradient operator at the centred mode kc = f M of an M grid (apm_gradient):
+// two-point sin(k delta)/delta, four-point sin(k delta)(4 - cos(k delta))/(3 delta)
+// (the symbol of the (8, -1)/12 stencil), spectral k with 0 on the Nyquist
+// mode of an even M.  The factor -i common to all is left out.
+__device__ double grad_symbol(int grad, int kc, int M, double delta) {
+    const double f = (double)kc / (double)M;
+    if (grad == APM_GRAD_FD2) return sinpi(2.0 * f) / delta;
+    if (grad == APM_GRAD_FD4) return sinpi(2.0 * f) * (4.0 - cospi(2.0 * f)) / (3.0 * delta);
+    return 2 * kc == M ? 0.0 : 2.0 * kPi * f / delta;
+}
+
 // Optimal influence function (Sec. 2.2 Eq. influence) at integer mode kap of an
 // M grid with cell delta, TSC assignment (Eq. assignment read as U^2 =
-// prod sinc^6, alias sum Eq. assignment2), two-point FD gradient
-// D_j = sin(k_j delta)/delta, Brillouin zones n in [-1,1]^3 (Eq. brillouin), and
-// reference force S(a_lev)^2/k^2 minus, on refined levels, S(a_par)^2/k^2
-// (Eq. reference).  Continuum units (potential per unit density).
+// prod sinc^6, alias sum Eq. assignment2), gradient D = grad_symbol, Brillouin
+// zones n in [-1,1]^3 (Eq. brillouin), and reference force S(a_lev)^2/k^2
+// minus, on refined levels, S(a_par)^2/k^2 (Eq. reference).  Continuum units
+// (potential per unit density).
 __device__ double green_opt(const int kap[3], const int M[3], double delta, double a_lev,
-                            double a_par, bool use_parent) {
+                            double a_par, bool use_parent, int grad) {
     double f[3], k[3], D[3];
     double alias = 1.0, D2 = 0.0;
     for (int j = 0; j < 3; ++j) {
         int kc = kap[j] > M[j] / 2 ? kap[j] - M[j] : kap[j];
         f[j] = (double)kc / (double)M[j];
         k[j] = 2.0 * kPi * f[j] / delta;
-        D[j] = sinpi(2.0 * f[j]) / delta;
+        D[j] = grad_symbol(grad, kc, M[j], delta);
         double s = sinpi(f[j]);
         double s2 = s * s;
         alias *= 1.0 - s2 + (2.0 / 15.0) * s2 * s2;
@@ -80,6 +91,7 @@ __device__ double green_opt(const int kap[3], const int M[3], double delta, doub
     return -4.0 * kPi * num / (D2 * alias * alias);
 }
 
+// modes where every operator's gradient vanishes identically (reading R5)
 __device__ bool fd_degenerate(const int kap[3], const int M[3]) {
     for (int j = 0; j < 3; ++j)
         if (!(kap[j] == 0 || 2 * kap[j] == M[j])) return false;
@@ -98,7 +110,7 @@ __device__ void oct_index(long long i, const Oct& o, int kap[3]) {
 }
 
 // kind 0 (refined level) and kind 1 (periodic root) tables
-__global__ void k_green_opt(int kind, Oct o, double delta, double a_lev, double a_par,
+__global__ void k_green_opt(int kind, Oct o, double delta, double a_lev, double a_par, int grad,
                             double* __restrict__ out) {
     long long total = (long long)o.H[0] * o.H[1] * o.H[2];
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -112,9 +124,9 @@ __global__ void k_green_opt(int kind, Oct o, double delta, double a_lev, double 
         if (zero)
             v = -4.0 * kPi * (a_par * a_par - a_lev * a_lev) / 30.0 / vol;  // k -> 0 limit
         else if (!fd_degenerate(kap, o.M))
-            v = green_opt(kap, o.M, delta, a_lev, a_par, true) / vol;
+            v = green_opt(kap, o.M, delta, a_lev, a_par, true, grad) / vol;
     } else {
-        if (!zero && !fd_degenerate(kap, o.M)) v = green_opt(kap, o.M, delta, a_lev, 0.0, false) / vol;
+        if (!zero && !fd_degenerate(kap, o.M)) v = green_opt(kap, o.M, delta, a_lev, 0.0, false, grad) / vol;
     }
     out[i] = v;
 }
@@ -178,7 +190,7 @@ __global__ void k_even_dft_axis(Oct o, int axis, const double* __restrict__ in,
 
 // adds the k-space optimal correction G_opt - (-4 pi S^2/k^2) on non-degenerate
 // modes kappa != 0 (isolated root, optional)
-__global__ void k_iso_correction(Oct o, double delta, double a, double* __restrict__ io) {
+__global__ void k_iso_correction(Oct o, double delta, double a, int grad, double* __restrict__ io) {
     long long total = (long long)o.H[0] * o.H[1] * o.H[2];
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= total) return;
@@ -193,7 +205,7 @@ __global__ void k_iso_correction(Oct o, double delta, double a, double* __restri
     double s = shat(sqrt(kk) * a * 0.5);
     double cont = -4.0 * kPi * s * s / kk;
     double vol = (delta * delta) * delta;
-    io[i] += (green_opt(kap, o.M, delta, a, 0.0, false) - cont) / vol;
+    io[i] += (green_opt(kap, o.M, delta, a, 0.0, false, grad) - cont) / vol;
 }
 
 __global__ void k_twiddles(double2* __restrict__ tw64, float2* __restrict__ tw32, int L) {
@@ -226,7 +238,7 @@ cudaError_t launch_to_f32(const double* in, float* out, long long n, cudaStream_
 }
 
 cudaError_t launch_green_table(int kind, const int M[3], double delta, double a_lev, double a_par,
-                               int correction, double* out, double* scratch, cudaStream_t s) {
+                               int correction, int grad, double* out, double* scratch, cudaStream_t s) {
     Oct o;
     for (int j = 0; j < 3; ++j) {
         o.M[j] = M[j];
@@ -235,7 +247,7 @@ cudaError_t launch_green_table(int kind, const int M[3], double delta, double a_
     long long total = (long long)o.H[0] * o.H[1] * o.H[2];
     const int T = 128;
     if (kind == 0 || kind == 1) {
-        k_green_opt<<<blocks_for(total, T), T, 0, s>>>(kind, o, delta, a_lev, a_par, out);
+        k_green_opt<<<blocks_for(total, T), T, 0, s>>>(kind, o, delta, a_lev, a_par, grad, out);
         return cudaGetLastError();
     }
     // isolated root: transform of the real-space kernel, axis by axis
@@ -245,7 +257,7 @@ cudaError_t launch_green_table(int kind, const int M[3], double delta, double a_
     k_even_dft_axis<<<blocks_for(total, T), T, 0, s>>>(o, 2, out, scratch);
     cudaError_t e = cudaMemcpyAsync(out, scratch, total * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
-    if (correction) k_iso_correction<<<blocks_for(total, T), T, 0, s>>>(o, delta, a_lev, out);
+    if (correction) k_iso_correction<<<blocks_for(total, T), T, 0, s>>>(o, delta, a_lev, grad, out);
     return cudaGetLastError();
 }
 

@@ -45,10 +45,13 @@ class Solver:
     """One APM context on one GPU with a static grid hierarchy.
 
     grids: sequence of (level, parent, start(3), dims(3)); grid 0 is the root.
+    gradient: "fd2" (two-point difference), "fd4" (four-point) or "spectral"
+    (D = -ik), the operator the accelerations and the influence function use.
     """
 
     def __init__(self, grids, periodic=False, precision="fp32", mass_frac_bits=52,
-                 root_correction=True, a_over_dx=3.4, pad_factor=0.65, box=1.0, device=None):
+                 root_correction=True, a_over_dx=3.4, pad_factor=0.65, box=1.0, device=None,
+                 gradient="fd2"):
         L = lib()
         cfg = ApmConfig()
         L.apm_config_default(ctypes.byref(cfg))
@@ -59,6 +62,8 @@ class Solver:
         cfg.precision = _lib.APM_FP64 if precision == "fp64" else _lib.APM_FP32
         cfg.mass_frac_bits = int(mass_frac_bits)
         cfg.root_correction = 1 if root_correction else 0
+        cfg.gradient = _lib.GRADIENTS[gradient]
+        self.gradient = gradient
         dev = torch.cuda.current_device() if device is None else int(device)
         cfg.device = dev
         self.device = torch.device("cuda", dev)
@@ -88,7 +93,7 @@ class Solver:
             self.info.append(dict(level=gi.level, border=gi.border, gmf=tuple(gi.gmf),
                                   fft=tuple(gi.fft), phi_short=tuple(gi.phi_short),
                                   field=tuple(gi.field), level_index=gi.level_index,
-                                  delta=gi.delta))
+                                  delta=gi.delta, comps=gi.phi_short_comps))
         self.level_grids = [[i for i, g in enumerate(self.grids) if g[0] == lev]
                             for lev in range(self.n_levels)]
 
@@ -105,12 +110,16 @@ class Solver:
 
     # ------------------------------------------------------------------ buffers
     def alloc_level(self, level):
-        """Output buffers of one level: gmf (int64), phi_short, phi, acc ([3, ...])."""
+        """Output buffers of one level: gmf (int64), phi_short ([4, ...] with the
+        spectral gradient), phi, acc ([3, ...])."""
         out = dict(gmf=[], phis=[], phi=[], acc=[])
         for gi in self.level_grids[level]:
             inf = self.info[gi]
             out["gmf"].append(torch.empty(inf["gmf"][::-1], dtype=torch.int64, device=self.device))
-            out["phis"].append(torch.empty(inf["phi_short"][::-1], dtype=self.dtype, device=self.device))
+            shape = inf["phi_short"][::-1]
+            if inf["comps"] > 1:
+                shape = (inf["comps"],) + shape
+            out["phis"].append(torch.empty(shape, dtype=self.dtype, device=self.device))
             out["phi"].append(torch.empty(inf["field"][::-1], dtype=self.dtype, device=self.device))
             out["acc"].append(torch.empty((3,) + inf["field"][::-1], dtype=self.dtype, device=self.device))
         return out

@@ -38,6 +38,7 @@ def test_defaults_are_the_papers(L):
     L.apm_config_default(ctypes.byref(c))
     assert c.a_over_dx == 3.4 and c.refine == 2 and c.pad_factor == 0.65   # Sec. 2.2
     assert c.box == 1.0 and c.root_bc == 0 and c.mass_frac_bits == 52 and c.device == -1
+    assert c.gradient == 0                                                  # two-point difference
     assert L.apm_version().startswith(b"apm-gb300")
     for code in range(10):
         assert len(L.apm_status_string(code)) >= 2
@@ -50,7 +51,7 @@ def test_create_rejects_bad_config_before_touching_cuda(L):
     L.apm_config_default(ctypes.byref(c))
     ctx = ctypes.c_void_p()
     bad = [("box", -1.0), ("mass_frac_bits", 63), ("mass_frac_bits", 0), ("root_bc", 5),
-           ("precision", 7), ("refine", 1)]
+           ("precision", 7), ("refine", 1), ("gradient", 3), ("gradient", -1)]
     for field, value in bad:
         cc = ApmConfig()
         ctypes.pointer(cc)[0] = c
