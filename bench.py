@@ -301,9 +301,9 @@ def run_apm(args):
     w = workload(args.workload)
     levels = list(range(1 + max(g.level for g in w.grids))) if w.solve_levels is None else w.solve_levels
 
-    def make(precision):
+    def make(precision, gradient="fd2"):
         s = Solver(w.grids, periodic=w.periodic, precision=precision,
-                   mass_frac_bits=w.mass_frac_bits, device=local)
+                   mass_frac_bits=w.mass_frac_bits, device=local, gradient=gradient)
         return s, s.alloc_all()
 
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in w.particles.items()}
@@ -411,6 +411,43 @@ def run_apm(args):
                 "fp32_speedup": ms64 / ms, "fp32_rel_l2_vs_fp64": {"phi_finest": e_phi, "pacc": e_pacc}}
         s64.close()
 
+    # ---------------- the other gradient operators (Sec. 2.2), FP32, same workload
+    gradients = None
+    if not args.no_gradients:
+        gradients = {}
+        for grad in ("fd4", "spectral"):
+            sv, bv = make("fp32", grad)
+            pv = torch.zeros((3, n), dtype=torch.float32, device=dev)
+
+            def stepv():
+                sv.step(P, w.half_dt, bv, pv, gas=gas, levels=levels)
+
+            if not args.no_tune:
+                sv.autotune(P, w.half_dt, bv, gas=gas, levels=levels)
+            for _ in range(args.warmup):
+                stepv()
+            sv.sync_status()
+            gv = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gv):
+                stepv()
+            gv.replay()
+            torch.cuda.synchronize()
+            sv.sync_status()
+            msv = timed(gv.replay, args.steps)
+            sv.profile(True)
+            for _ in range(args.steps):
+                stepv()
+            pv_prof = sv.profile_read()
+            sv.profile(False)
+            sv.sync_status()
+            gradients[grad] = {
+                "value": job_rate(ranks, cells, msv), "ms_per_step": msv, "time_vs_fd2": msv / ms,
+                "kernel_ms_per_step": {k: v[1] / args.steps for k, v in pv_prof.items() if v[0]},
+                "launches_per_step": sum(v[0] for v in pv_prof.values()) / args.steps}
+            del gv
+            sv.close()
+            del bv, pv
+
     # ---------------- cuFFT comparison (context only: cuFFT is not on the product path)
     cufft = None
     if not args.no_cufft:
@@ -470,6 +507,7 @@ def run_apm(args):
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "fp64": fp64,
+        "gradients": gradients,
         "cufft_compare": cufft,
         "clocks": clk,
     }
@@ -492,6 +530,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
+    ap.add_argument("--no-gradients", action="store_true",
+                    help="skip timing the four-point and spectral gradient operators")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
