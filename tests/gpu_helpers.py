@@ -24,13 +24,15 @@ def rel_l2(a, b):
 
 
 def run_gpu(grids, particles, half_dt, gas=None, periodic=False, precision="fp64",
-            mass_frac_bits=52, root_correction=True, levels=None, batched=True, gradient="fd2"):
+            mass_frac_bits=52, root_correction=True, levels=None, batched=True, gradient="fd2",
+            pad_factor=0.65, a_over_dx=3.4):
     import torch
 
     from paper_1410_0010_gb300.solver import Solver
     dev = torch.device("cuda", 0)
     s = Solver(grids, periodic=periodic, precision=precision, mass_frac_bits=mass_frac_bits,
-               root_correction=root_correction, device=0, gradient=gradient)
+               root_correction=root_correction, device=0, gradient=gradient, pad_factor=pad_factor,
+               a_over_dx=a_over_dx)
     tp = {k: torch.as_tensor(np.ascontiguousarray(v, dtype=np.float64), device=dev)
           for k, v in particles.items()}
     tg = None
@@ -54,10 +56,11 @@ def run_gpu(grids, particles, half_dt, gas=None, periodic=False, precision="fp64
 
 
 def run_oracle(grids, particles, half_dt, gas=None, periodic=False, mass_frac_bits=52,
-               root_correction=True, gradient="fd2"):
+               root_correction=True, gradient="fd2", pad_factor=0.65, a_over_dx=3.4):
     import oracle
     cfg = oracle.Config(periodic=periodic, mass_frac_bits=mass_frac_bits,
-                        root_correction=root_correction, gradient=gradient)
+                        root_correction=root_correction, gradient=gradient, pad_factor=pad_factor,
+                        a_over_dx=a_over_dx)
     return oracle.apm_step(cfg, [oracle.Grid(*g) for g in grids], particles, half_dt, gas=gas)
 
 

@@ -117,6 +117,25 @@ def test_borders_past_an_isolated_root(precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("pad_factor,a_over_dx", [(0.3, 3.4), (0.15, 2.5), (1.0, 5.0)])
+def test_padding_and_softening_parameters(precision, pad_factor, a_over_dx):
+    """The accuracy studies' parameters: border B = ceil(pad 2 a/delta) from 2 to
+    10 cells (down to fewer than the window's 2 extra cells) and a/delta from
+    2.5 to 5, on an isolated root with a child and a grandchild."""
+    grids = [GridDesc(0, -1, (0, 0, 0), (32, 32, 32)),
+             GridDesc(1, 0, (22, 20, 24), (20, 22, 18)),
+             GridDesc(2, 1, (58, 54, 60), (12, 14, 10))]
+    rng = np.random.default_rng(17)
+    parts = W.concat_particles(_random_particles(rng, 600, 0.1, 0.9, vscale=0.2),
+                               _random_particles(rng, 300, 0.4, 0.6, vscale=0.2))
+    gas = [None, rng.random((18, 22, 20)) + 0.2, None]
+    ref = run_oracle(grids, parts, 1e-3, gas=gas, pad_factor=pad_factor, a_over_dx=a_over_dx)
+    gpu = run_gpu(grids, parts, 1e-3, gas=gas, precision=precision, pad_factor=pad_factor,
+                  a_over_dx=a_over_dx)
+    compare(gpu, ref, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_all_level_calls_equal_per_level_calls_bitwise(precision):
     """apm_deposit_all / apm_interp_all against apm_deposit / apm_interp level by
     level on a three-level periodic hierarchy with gas and particles everywhere
