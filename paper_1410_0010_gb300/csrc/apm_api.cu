@@ -707,15 +707,9 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             const GridDev& g = L.hg[k];
             const long long grows = (long long)g.G[1] * g.G[2];
             for (long long t = 0; t < (grows + g.rows_gas - 1) / g.rows_gas; ++t) gas.push_back({k, (int)t});
-            if (cfg.gradient == APM_GRAD_FD2) {   // k_accel: 2x2x2 blocks
-                const long long nblocks = (long long)g.acc_nb[0] * g.acc_nb[1] * g.acc_nb[2];
-                for (long long t = 0; t < (nblocks + kAccBlocksPerCta - 1) / kAccBlocksPerCta; ++t)
-                    acc.push_back({k, (int)t});
-            } else {                              // k_accel_cells: output cells
-                const long long ncell = (long long)(g.N[0] + 2) * (g.N[1] + 2) * (g.N[2] + 2);
-                for (long long t = 0; t < (ncell + kCellsPerCta - 1) / kCellsPerCta; ++t)
-                    acc.push_back({k, (int)t});
-            }
+            const long long nblocks = (long long)g.acc_nb[0] * g.acc_nb[1] * g.acc_nb[2];
+            for (long long t = 0; t < (nblocks + kAccBlocksPerCta - 1) / kAccBlocksPerCta; ++t)
+                acc.push_back({k, (int)t});
         }
         for (int q = 0; q < kFftPasses; ++q) {
             if ((st = build_pass(c, L, q, f64 ? kFftBudgetF64 : kFftBudgetF32, kFftThreads, f64, L.pass[q])) != APM_OK)
@@ -1106,9 +1100,9 @@ apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,
                                   (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s);
     else
         e = c->cfg.precision == APM_FP64
-            ? launch_accel_cells<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+            ? launch_accel_var<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
                                          (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, grad, s)
-            : launch_accel_cells<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+            : launch_accel_var<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
                                         (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, grad, s);
     return cuda_status(e);
 }

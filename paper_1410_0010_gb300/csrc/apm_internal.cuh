@@ -455,12 +455,10 @@ cudaError_t launch_fft_zgrad(const FftArgs& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
 
-// accelerations + parent carry, one thread per output cell, for the four-point
-// and spectral gradients (the two-point one runs launch_accel); chunks hold
-// kCellsPerCta output cells of one grid each
-constexpr int kCellsPerCta = 1024;
+// accelerations + parent carry for the four-point and spectral gradients (the
+// two-point one runs launch_accel), on launch_accel's block work list
 template <typename T>
-cudaError_t launch_accel_cells(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
+cudaError_t launch_accel_var(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
                                const void* const* pphi, const void* const* pacc, void* const* phi,
                                void* const* acc, const Chunk* chunks, int n_chunks, int grad,
                                cudaStream_t s);

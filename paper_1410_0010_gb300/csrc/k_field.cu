@@ -456,98 +456,120 @@ __global__ void __launch_bounds__(kIntThreads, APM_INT_MIN_CTAS) k_interp_levels
     interp_from<T>(L, L.g[own_g], reinterpret_cast<const T*>(accs[own_l][own_g]), X, p, P.n, out);
 }
 
-// Four-point and spectral gradients (Sec. 2.2; apm_gradient), one thread per
-// output cell c in [-1, N]^3, kCellsPerCta cells of one grid per CTA:
+// Four-point and spectral gradients (Sec. 2.2; apm_gradient), on the 2x2x2
+// blocks of k_accel (same work list, same parent interpolation):
 //   phi(c)   = phis(c) + I(parent phi)(c)
-//   acc_j(c) = A_j(c) + I(parent acc_j)(c), with
+//   acc_j(c) = A_j(c) + I(parent acc_j)(c),        c in [-1, N]^3, with
 //   A_j = -(8 (phis(c+e_j) - phis(c-e_j)) - (phis(c+2e_j) - phis(c-2e_j))) / (12 delta)
 //         (four-point; phis spans [-3, N+3)), or the solve's spectral component
 //         j + 1 (phis: four windows of [-2, N+2)).
-// I is trilinear from the parent cell centres: level cell i lies at parent
-// coordinate (i - 1/2)/2, i.e. 1/4 (odd i) or 3/4 (even i) above the centre of
-// parent cell (i - 1) >> 1; the corner weights ((wx wy) wz) are exact.
+// Output cell e (index 0..E-1) is level cell e - 1 and phis cell e - 1 + h.
 template <typename T, int GRAD>
-__global__ void __launch_bounds__(256) k_accel_cells(LevelDev L, const GridDev* __restrict__ pgrids,
-                                                     const void* const* __restrict__ phis_p,
-                                                     const void* const* __restrict__ pphi_p,
-                                                     const void* const* __restrict__ pacc_p,
-                                                     void* const* __restrict__ phi_p,
-                                                     void* const* __restrict__ acc_p,
-                                                     const Chunk* __restrict__ chunks) {
+__global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel_var(
+    LevelDev L, const GridDev* __restrict__ pgrids, const void* const* __restrict__ phis_p,
+    const void* const* __restrict__ pphi_p, const void* const* __restrict__ pacc_p,
+    void* const* __restrict__ phi_p, void* const* __restrict__ acc_p, const Chunk* __restrict__ chunks) {
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = L.g[ch.grid];
-    const int E0 = g.N[0] + 2, E1 = g.N[1] + 2;
-    const long long ncell = (long long)E0 * E1 * (g.N[2] + 2);
+    const int E0 = g.N[0] + 2, E1 = g.N[1] + 2, E2 = g.N[2] + 2;
+    const unsigned ncell = (unsigned)E0 * E1 * E2;
     const int h = g.h;
-    const long long W0 = g.W[0], W01 = (long long)g.W[0] * g.W[1];
-    const long long nw = W01 * g.W[2];
+    const unsigned W0 = g.W[0], W01 = (unsigned)g.W[0] * g.W[1];
+    const unsigned nw = W01 * (unsigned)g.W[2];
+    const int nbx = g.acc_nb[0], nby = g.acc_nb[1];
+    const int nbrows = nby * g.acc_nb[2];
     const T* __restrict__ phis = reinterpret_cast<const T*>(phis_p[ch.grid]);
     T* __restrict__ phi = reinterpret_cast<T*>(phi_p[ch.grid]);
     T* __restrict__ acc = reinterpret_cast<T*>(acc_p[ch.grid]);
     const bool carry = pphi_p != nullptr && g.parent >= 0;
     const T* __restrict__ pphi = carry ? reinterpret_cast<const T*>(pphi_p[g.parent]) : nullptr;
     const T* __restrict__ pacc = carry ? reinterpret_cast<const T*>(pacc_p[g.parent]) : nullptr;
-    long long P0 = 0, P01 = 0, pn = 0;
+    int P0 = 0;
+    unsigned P01 = 0, pn = 0;
     long long ps[3] = {0, 0, 0};
     if (carry) {
         const GridDev& p = pgrids[g.parent];
         P0 = p.N[0] + 2;
-        P01 = P0 * (p.N[1] + 2);
+        P01 = (unsigned)P0 * (p.N[1] + 2);
         pn = P01 * (p.N[2] + 2);
         ps[0] = p.start[0]; ps[1] = p.start[1]; ps[2] = p.start[2];
     }
     const T inv12d = (T)g.inv12d;
-    const long long first = (long long)ch.tile * kCellsPerCta;
-    const long long last = min(first + (long long)kCellsPerCta, ncell);
-    for (long long o = first + threadIdx.x; o < last; o += blockDim.x) {
-        const int e[3] = {(int)(o % E0) - 1, (int)((o / E0) % E1) - 1, (int)(o / ((long long)E0 * E1)) - 1};
-        const long long c = (e[0] + h) + W0 * (e[1] + h) + W01 * (e[2] + h);
-        T p0 = phis[c];
-        T a[3];
-        if constexpr (GRAD == APM_GRAD_FD4) {
-            const long long st[3] = {1, W0, W01};
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const T d1 = phis[c + st[j]] - phis[c - st[j]];
-                const T d2 = phis[c + 2 * st[j]] - phis[c - 2 * st[j]];
-                a[j] = -((T)8 * d1 - d2) * inv12d;
+    const unsigned st[3] = {1u, W0, W01};
+    const long long nblocks = (long long)nbx * nbrows;
+    const long long f0 = (long long)ch.tile * kAccBlocksPerCta;
+    const int count = (int)min((long long)kAccBlocksPerCta, nblocks - f0);
+    int last = -1;
+    int ey0 = 0, ez0 = 0;
+    unsigned prow = 0;
+    for (FlatWalk it(f0, count, nbx); it.ok(); it.next()) {
+        if (it.r != last) {
+            last = it.r;
+            const int by = it.r % nby, bz = it.r / nby;
+            ey0 = 2 * by - g.acc_sh[1];
+            ez0 = 2 * bz - g.acc_sh[2];
+            if (carry) {
+                const long long ky = ((g.start[1] + ey0 - 1) - 1) >> 1;
+                const long long kz = ((g.start[2] + ez0 - 1) - 1) >> 1;
+                prow = (unsigned)(ky - ps[1] + 1) * (unsigned)P0 + (unsigned)(kz - ps[2] + 1) * P01;
             }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) a[j] = phis[(j + 1) * nw + c];
         }
+        const int ex0 = 2 * it.x - g.acc_sh[0];
+        unsigned pbase = 0;
         if (carry) {
-            long long base = 0;
-            T w[3][2];
-            const long long pst[3] = {1, P0, P01};
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const long long i = g.start[j] + e[j];
-                const T f = (i & 1) ? (T)0.25 : (T)0.75;
-                w[j][0] = (T)1 - f;
-                w[j][1] = f;
-                base += (((i - 1) >> 1) - ps[j] + 1) * pst[j];
-            }
-            T ip = 0, ia[3] = {0, 0, 0};
-#pragma unroll
-            for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 2; ++dx) {
-                        const T wt = (w[0][dx] * w[1][dy]) * w[2][dz];
-                        const long long q = base + dx + dy * P0 + dz * P01;
-                        ip += wt * pphi[q];
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) ia[j] += wt * pacc[j * pn + q];
-                    }
-            p0 += ip;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) a[j] += ia[j];
+            const long long kx = ((g.start[0] + ex0 - 1) - 1) >> 1;
+            pbase = prow + (unsigned)(kx - ps[0] + 1);
         }
-        phi[o] = p0;
+        bool wr[2][2][2];
+        unsigned o[2][2][2], c0[2][2][2];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) acc[j * ncell + o] = a[j];
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int ex = ex0 + a, ey = ey0 + b, ez = ez0 + c;
+                    wr[c][b][a] = ex >= 0 && ex < E0 && ey >= 0 && ey < E1 && ez >= 0 && ez < E2;
+                    o[c][b][a] = (unsigned)ex + (unsigned)E0 * ((unsigned)ey + (unsigned)E1 * (unsigned)ez);
+                    c0[c][b][a] = (unsigned)(ex - 1 + h) + W0 * (unsigned)(ey - 1 + h) + W01 * (unsigned)(ez - 1 + h);
+                }
+        T out[2][2][2], q[2][2][2];
+        if (carry) {
+            load_parent<T>(pphi, pbase, P0, P01, q);
+            lerp_block<T>(q, out);
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+                    if (wr[c][b][a]) phi[o[c][b][a]] = phis[c0[c][b][a]] + (carry ? out[c][b][a] : T(0));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (carry) {
+                load_parent<T>(pacc + j * pn, pbase, P0, P01, q);
+                lerp_block<T>(q, out);
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        if (!wr[c][b][a]) continue;
+                        const unsigned ci = c0[c][b][a];
+                        T v;
+                        if constexpr (GRAD == APM_GRAD_FD4) {
+                            const T d1 = phis[ci + st[j]] - phis[ci - st[j]];
+                            const T d2 = phis[ci + 2 * st[j]] - phis[ci - 2 * st[j]];
+                            v = -((T)8 * d1 - d2) * inv12d;
+                        } else {
+                            v = phis[(j + 1) * nw + ci];
+                        }
+                        acc[j * ncell + o[c][b][a]] = v + (carry ? out[c][b][a] : T(0));
+                    }
+        }
     }
 }
 
@@ -564,16 +586,17 @@ cudaError_t launch_accel(const LevelDev& L, const GridDev* parent_grids, const v
 }
 
 template <typename T>
-cudaError_t launch_accel_cells(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
+cudaError_t launch_accel_var(const LevelDev& L, const GridDev* parent_grids, const void* const* phis,
                                const void* const* pphi, const void* const* pacc, void* const* phi,
                                void* const* acc, const Chunk* chunks, int n_chunks, int grad,
                                cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
     if (grad == APM_GRAD_FD4)
-        k_accel_cells<T, APM_GRAD_FD4><<<n_chunks, 256, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc, chunks);
+        k_accel_var<T, APM_GRAD_FD4><<<n_chunks, kAccThreads, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc,
+                                                                      chunks);
     else
-        k_accel_cells<T, APM_GRAD_SPECTRAL><<<n_chunks, 256, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi, acc,
-                                                                     chunks);
+        k_accel_var<T, APM_GRAD_SPECTRAL><<<n_chunks, kAccThreads, 0, s>>>(L, parent_grids, phis, pphi, pacc, phi,
+                                                                           acc, chunks);
     return cudaGetLastError();
 }
 
@@ -602,10 +625,10 @@ template cudaError_t launch_accel<float>(const LevelDev&, const GridDev*, const 
 template cudaError_t launch_accel<double>(const LevelDev&, const GridDev*, const void* const*,
                                           const void* const*, const void* const*, void* const*,
                                           void* const*, const Chunk*, int, cudaStream_t);
-template cudaError_t launch_accel_cells<float>(const LevelDev&, const GridDev*, const void* const*,
+template cudaError_t launch_accel_var<float>(const LevelDev&, const GridDev*, const void* const*,
                                                const void* const*, const void* const*, void* const*,
                                                void* const*, const Chunk*, int, int, cudaStream_t);
-template cudaError_t launch_accel_cells<double>(const LevelDev&, const GridDev*, const void* const*,
+template cudaError_t launch_accel_var<double>(const LevelDev&, const GridDev*, const void* const*,
                                                 const void* const*, const void* const*, void* const*,
                                                 void* const*, const Chunk*, int, int, cudaStream_t);
 template cudaError_t launch_interp<float>(const LevelDev&, const LevelDev*, const Particles&, double,
