@@ -181,6 +181,59 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
+def ncu_label(name):
+    """bench.py's kernel label of an ncu kernel name (the column passes by their
+    template arguments <T, axis, mode, threads>), or None."""
+    import re
+    m = re.search(r"k_([a-z_]+)(<[^>]*>)?\(", name)
+    if not m:
+        return None
+    base, targs = m.group(1), m.group(2) or ""
+    if base == "col":
+        a = [t.strip() for t in targs.strip("<>").split(",")]
+        return {("1", "0"): "fft_y_fwd", ("2", "1"): "fft_z_green", ("1", "2"): "fft_y_inv",
+                ("2", "3"): "fft_z_green"}.get((a[1], a[2])) if len(a) >= 3 else None
+    return {"gas_init": "gas_init", "deposit_levels": "tsc_deposit", "xf": "fft_x_fwd", "xi": "fft_x_inv",
+            "accel": "accel_carry", "interp_levels": "tsc_interp"}.get(base)
+
+
+def write_traffic(csv_path, small="c5s", full="c5", scale=8):
+    """profiles/traffic.json from an ncu --csv capture of one step of the `small`
+    workload (dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over
+    the step's launches of each kernel), with the per-launch figures scaled by
+    `scale` for the `full` workload and the sha256 of the current sources."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    H = rows[hdr]
+    ki, mi, vi, ui, ii = (H.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
+    unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per = {}
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi or not r[mi].startswith("dram__bytes_"):
+            continue
+        label = ncu_label(r[ki])
+        if label is None:
+            continue
+        d = per.setdefault(label, {})
+        d[int(r[ii])] = d.get(int(r[ii]), 0.0) + float(r[vi].replace(",", "")) * unit.get(r[ui], 1)
+    ws, wf = workload(small).name, workload(full).name
+    out = {}
+    for label, launches in sorted(per.items()):
+        mean = sum(launches.values()) / len(launches)
+        out[f"{ws}:{label}"] = int(round(mean))
+        out[f"{wf}:{label}"] = int(round(mean * scale))
+    doc = {"source_sha256": kernel_source_hash(),
+           "note": ("dram__bytes_read.sum + dram__bytes_write.sum per launch (mean over the launches of one "
+                    f"step), captured on {ws} and scaled x{scale} to {wf} ({scale}x the cells, grids and "
+                    f"particles per launch); the {ws} values are kept as measured"),
+           "per_launch_bytes": out}
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(path, "w") as f:
+        json.dump(doc, f, indent=1)
+    return path
+
+
 # ----------------------------------------------------------------------------
 # oracle sample (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------
@@ -530,9 +583,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
+    ap.add_argument("--write-traffic", metavar="CSV",
+                    help="write profiles/traffic.json from an ncu --csv capture of one c5s step, then exit")
     ap.add_argument("--no-gradients", action="store_true",
                     help="skip timing the four-point and spectral gradient operators")
     args = ap.parse_args()
+    if args.write_traffic:
+        print(write_traffic(args.write_traffic))
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
