@@ -311,3 +311,82 @@ class Solver:
             return
         for lev in levs:
             self.interp(lev, bufs[lev]["acc"], P, half_dt, pacc, stream)
+
+
+class StepPipeline:
+    """End-to-end solves from pinned host particles to host accelerations, with
+    the copies overlapped: two device particle/acceleration buffer sets, each
+    with its own captured solve (CUDA graph), and a copy stream that uploads
+    step k+1's particles and downloads step k-1's accelerations while step k
+    solves.  Every step still copies all of its inputs in and its result out.
+
+    solver, bufs: a Solver and its alloc_all() buffers (shared by both sets);
+    host: dict of pinned float64 host arrays (PARTICLE_KEYS); the rest as for
+    Solver.step.  run(steps, inputs=None, outputs=None): inputs(k) -> host dict
+    of step k (default: `host` every step); outputs(k) -> pinned host (3, n)
+    tensor of the solver's precision that receives step k's accelerations
+    (default: two alternating buffers)."""
+
+    def __init__(self, solver, bufs, host, half_dt, gas=None, levels=None):
+        self.s = solver
+        self.host = host
+        dev = solver.device
+        self.n = int(host["x"].numel())
+        self.sets = []
+        for _ in range(2):
+            P = Particles({k: torch.empty_like(host[k], device=dev) for k in PARTICLE_KEYS})
+            pacc = torch.zeros((3, self.n), dtype=solver.dtype, device=dev)
+            self.sets.append((P, pacc))
+        self.hout = [torch.empty((3, self.n), dtype=solver.dtype).pin_memory() for _ in range(2)]
+        self.copy = torch.cuda.Stream(device=dev)
+        self.graphs = []
+        for P, pacc in self.sets:
+            for k in PARTICLE_KEYS:
+                P.t[k].copy_(host[k])
+            solver.step(P, half_dt, bufs, pacc, gas=gas, levels=levels)     # warm, outside capture
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                solver.step(P, half_dt, bufs, pacc, gas=gas, levels=levels)
+            self.graphs.append(g)
+        torch.cuda.synchronize(dev)
+        solver.sync_status()
+
+    def bytes_per_step(self):
+        h2d = sum(self.host[k].numel() * self.host[k].element_size() for k in PARTICLE_KEYS)
+        return h2d, self.hout[0].numel() * self.hout[0].element_size()
+
+    def run(self, steps, inputs=None, outputs=None):
+        comp = torch.cuda.current_stream(self.s.device)
+        cp = self.copy
+        ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_out = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def upload(k):
+            P = self.sets[k % 2][0]
+            src = self.host if inputs is None else inputs(k)
+            with torch.cuda.stream(cp):
+                for key in PARTICLE_KEYS:
+                    P.t[key].copy_(src[key], non_blocking=True)
+                ev_in[k % 2].record(cp)
+
+        cp.wait_stream(comp)
+        if steps > 0:
+            upload(0)
+        for k in range(steps):
+            b = k % 2
+            comp.wait_event(ev_in[b])
+            if k >= 2:
+                comp.wait_event(ev_out[b])         # step k-2's download of this set is done
+            self.graphs[b].replay()
+            ev_done[b].record(comp)
+            if k + 1 < steps:
+                if k >= 1:
+                    cp.wait_event(ev_done[1 - b])      # set 1-b is free once step k-1 has solved
+                upload(k + 1)
+            with torch.cuda.stream(cp):
+                cp.wait_event(ev_done[b])
+                dst = self.hout[b] if outputs is None else outputs(k)
+                dst.copy_(self.sets[b][1], non_blocking=True)
+                ev_out[b].record(cp)
+        comp.wait_stream(cp)
