@@ -53,7 +53,9 @@ typedef enum {
     APM_E_OUT_OF_BOX = 6,  /* particle outside an isolated root (folded to its edge) */
     APM_E_TIMEOUT = 7,     /* a bounded device wait ran out */
     APM_E_UNSUPPORTED = 8, /* valid request this build does not implement */
-    APM_E_STATE = 9        /* call out of order (e.g. no hierarchy set) */
+    APM_E_STATE = 9,       /* call out of order (e.g. no hierarchy set) */
+    APM_E_BOUNDS = 10      /* a checked device access was out of range (only in
+                              libraries built with -DAPM_BOUNDS_CHECK) */
 } apm_status;
 
 typedef enum { APM_FP32 = 0, APM_FP64 = 1 } apm_precision;

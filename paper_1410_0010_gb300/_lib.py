@@ -3,14 +3,15 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libapm.so")
+# APM_LIB selects another build of the library (the bounds-checked one)
+LIB_PATH = os.environ.get("APM_LIB") or os.path.join(HERE, "_build", "libapm.so")
 
 c_i32, c_i64, c_dbl, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
 APM_OK = 0
 STATUS_NAMES = {0: "APM_OK", 1: "APM_E_INVALID", 2: "APM_E_NESTING", 3: "APM_E_NOMEM",
                 4: "APM_E_CUDA", 5: "APM_E_OVERFLOW", 6: "APM_E_OUT_OF_BOX", 7: "APM_E_TIMEOUT",
-                8: "APM_E_UNSUPPORTED", 9: "APM_E_STATE"}
+                8: "APM_E_UNSUPPORTED", 9: "APM_E_STATE", 10: "APM_E_BOUNDS"}
 APM_FP32, APM_FP64 = 0, 1
 APM_BC_ISOLATED, APM_BC_PERIODIC = 0, 1
 APM_GRAD_FD2, APM_GRAD_FD4, APM_GRAD_SPECTRAL = 0, 1, 2

@@ -15,6 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libapm.so")
+# the bounds-checked debug library (-DAPM_BOUNDS_CHECK), loaded with APM_LIB
+BOUNDS_DIR = os.path.join(HERE, "_build_bounds")
 
 # (source, object, extra flags): k_fft_col.cu is compiled once per precision
 # and column pass
@@ -42,17 +44,19 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile the stale translation units and link libapm.so.  Extra nvcc
-    flags come from `extra` and the APM_NVCC_FLAGS environment variable."""
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, extra=(), out_dir=OUT_DIR):
+    """Compile the stale translation units and link libapm.so in `out_dir`.
+    Extra nvcc flags come from `extra` and the APM_NVCC_FLAGS environment
+    variable."""
+    lib_path = os.path.join(out_dir, "libapm.so")
+    os.makedirs(out_dir, exist_ok=True)
     extra = list(extra) + os.environ.get("APM_NVCC_FLAGS", "").split()
     headers = [os.path.join(CSRC, h) for h in sorted(os.listdir(CSRC)) if h.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "apm.h"))
     objs, jobs = [], []
     for src, oname, flags in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(OUT_DIR, oname)
+        obj = os.path.join(out_dir, oname)
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
             cmd = [nvcc(), *ARCH, *COMMON, *PER_FILE.get(src, []), *flags, *extra, "-c", path, "-o", obj]
@@ -70,14 +74,23 @@ def build(force=False, verbose=False, extra=()):
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + ".tmp"
         run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
+
+
+def build_bounds_checked(force=False, verbose=False):
+    """The debug library: every data- or hierarchy-dependent global index is
+    tested before use (APM_BOUNDS_CHECK; apm_sync_status reports APM_E_BOUNDS)."""
+    return build(force=force, verbose=verbose, extra=["-DAPM_BOUNDS_CHECK"], out_dir=BOUNDS_DIR)
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+    if "--bounds-check" in sys.argv:
+        print(build_bounds_checked(force="--force" in sys.argv, verbose=True))
+    else:
+        print(build(force="--force" in sys.argv, verbose=True,
+                    extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))

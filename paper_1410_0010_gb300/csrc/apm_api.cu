@@ -9,11 +9,23 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "apm_internal.cuh"
 
 using namespace apm;
 
 namespace {
+
+// NVTX range for the lifetime of the object: every API call and every kernel
+// launch appears by name on a timeline tool's NVTX row (nvtx3 is header-only;
+// with no tool attached each call returns at once)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 constexpr int kRoles = 11;
 enum Role { R_GMF = 0, R_GAS, R_PGAS, R_GMF_IN, R_PHIS, R_PHIS_IN, R_PPHI, R_PACC, R_PHI, R_ACC, R_ACC_IN };
@@ -384,7 +396,8 @@ struct Trace {
     apm_ctx* c;
     int pair = -1;
     cudaStream_t s;
-    Trace(apm_ctx* ctx, int k, cudaStream_t st) : c(ctx), s(st) {
+    Range range;
+    Trace(apm_ctx* ctx, int k, cudaStream_t st) : c(ctx), s(st), range(kKernelNames[k]) {
         Profiler& P = c->prof;
         if (!P.on || P.used * 2 + 1 >= (int)P.ev.size()) return;
         pair = P.used++;
@@ -451,6 +464,7 @@ const char* apm_status_string(apm_status s) {
         case APM_E_TIMEOUT: return "device wait ran out";
         case APM_E_UNSUPPORTED: return "unsupported request";
         case APM_E_STATE: return "call out of order";
+        case APM_E_BOUNDS: return "device access out of range (bounds-checked build)";
     }
     return "unknown status";
 }
@@ -529,6 +543,7 @@ apm_status apm_get_grid_info(const apm_ctx* c, int32_t grid, apm_grid_info* out)
 }
 
 apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
+    Range nvtx_range("apm_set_hierarchy");
     if (!c || !grids) return APM_E_INVALID;
     apm_status st = validate(c->cfg, grids, n);
     if (st != APM_OK) return st;
@@ -745,6 +760,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
         D.span = (long long)N0 << kPosBits;
         D.box = cfg.box;
         D.periodic = periodic ? 1 : 0;
+        D.status = c->d_status;
         if (L.level > 0) {
             std::vector<std::pair<std::array<long long, 3>, std::array<long long, 3>>> dep, own;
             long long lo[3] = {1LL << 62, 1LL << 62, 1LL << 62}, hi[3] = {-(1LL << 62), -(1LL << 62), -(1LL << 62)};
@@ -834,6 +850,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
 apm_status apm_deposit(apm_ctx* c, int32_t level, const apm_particles* particles, double half_dt,
                        const double* const* gas, const double* const* parent_gas,
                        int64_t* const* gmf, void* stream) {
+    Range nvtx_range("apm_deposit");
     if (!c) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (level < 0 || level >= (int)c->levels.size() || !gmf || !particles_ok(particles))
@@ -871,6 +888,7 @@ apm_status apm_deposit(apm_ctx* c, int32_t level, const apm_particles* particles
 
 apm_status apm_deposit_all(apm_ctx* c, const apm_particles* particles, double half_dt,
                            const double* const* gas, int64_t* const* gmf, void* stream) {
+    Range nvtx_range("apm_deposit_all");
     if (!c) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (!gmf || !particles_ok(particles)) return APM_E_INVALID;
@@ -917,6 +935,7 @@ apm_status apm_deposit_all(apm_ctx* c, const apm_particles* particles, double ha
 
 apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
                            void* const* phi_short, void* stream) {
+    Range nvtx_range("apm_solve_level");
     if (!c) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (level < 0 || level >= (int)c->levels.size() || !gmf || !phi_short) return APM_E_INVALID;
@@ -947,6 +966,7 @@ apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
 
 apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
                               void* const* phi_short, void* stream) {
+    Range nvtx_range("apm_autotune_level");
     if (!c) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (level < 0 || level >= (int)c->levels.size() || !gmf || !phi_short) return APM_E_INVALID;
@@ -1069,6 +1089,7 @@ apm_status apm_set_fft_shapes(apm_ctx* c, int32_t level, const apm_fft_shapes* s
 apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,
                      const void* const* parent_phi, const void* const* parent_acc, void* const* phi,
                      void* const* acc, void* stream) {
+    Range nvtx_range("apm_accel");
     if (!c) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (level < 0 || level >= (int)c->levels.size() || !phi_short || !phi || !acc) return APM_E_INVALID;
@@ -1109,6 +1130,7 @@ apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,
 
 apm_status apm_interp(apm_ctx* c, int32_t level, const void* const* acc,
                       const apm_particles* particles, double half_dt, void* acc_out, void* stream) {
+    Range nvtx_range("apm_interp");
     if (!c) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (level < 0 || level >= (int)c->levels.size() || !acc || !particles_ok(particles) ||
@@ -1130,6 +1152,7 @@ apm_status apm_interp(apm_ctx* c, int32_t level, const void* const* acc,
 
 apm_status apm_interp_all(apm_ctx* c, const void* const* acc, const apm_particles* particles,
                           double half_dt, void* acc_out, void* stream) {
+    Range nvtx_range("apm_interp_all");
     if (!c) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (!acc || !particles_ok(particles) || (!acc_out && particles->n > 0)) return APM_E_INVALID;
@@ -1158,6 +1181,7 @@ apm_status apm_interp_all(apm_ctx* c, const void* const* acc, const apm_particle
 
 apm_status apm_kick_drift(apm_ctx* c, int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                           double* vz, const void* acc, double dt, void* stream) {
+    Range nvtx_range("apm_kick_drift");
     if (!c) return APM_E_INVALID;
     if (n < 0 || (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !acc))) return APM_E_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1217,6 +1241,7 @@ apm_status apm_profile_read(apm_ctx* c, int32_t kernel, int64_t* launches, doubl
 }
 
 apm_status apm_sync_status(apm_ctx* c, void* stream) {
+    Range nvtx_range("apm_sync_status");
     if (!c) return APM_E_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaStreamSynchronize(s) != cudaSuccess) return APM_E_CUDA;
@@ -1227,6 +1252,7 @@ apm_status apm_sync_status(apm_ctx* c, void* stream) {
     if (h & kStOverflow) return APM_E_OVERFLOW;
     if (h & kStOutOfBox) return APM_E_OUT_OF_BOX;
     if (h & kStTimeout) return APM_E_TIMEOUT;
+    if (h & kStBounds) return APM_E_BOUNDS;
     return APM_OK;
 }
 

@@ -57,6 +57,23 @@ constexpr int kMaxFft = 1024;       // longest supported transform
 constexpr unsigned kStOverflow = 1u;
 constexpr unsigned kStOutOfBox = 2u;
 constexpr unsigned kStTimeout = 4u;
+constexpr unsigned kStBounds = 8u;
+
+// Bounds-checked builds (-DAPM_BOUNDS_CHECK): the kernels test each global
+// index whose value depends on the data or the hierarchy before using it; an
+// index outside [0, n) sets the status word's bounds bit (apm_sync_status:
+// APM_E_BOUNDS) and the access is skipped.  Release builds compile the tests
+// out.  Nothing here asserts or traps.
+#ifdef APM_BOUNDS_CHECK
+__device__ __forceinline__ bool in_bounds(long long i, long long n, unsigned* status) {
+    if (i >= 0 && i < n) return true;
+    if (status) atomicOr(status, kStBounds);
+    return false;
+}
+#define APM_IN_BOUNDS(i, n, status) ::apm::in_bounds((long long)(i), (long long)(n), (status))
+#else
+#define APM_IN_BOUNDS(i, n, status) true
+#endif
 
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
@@ -247,6 +264,7 @@ struct LevelDev {
     double box;
     int periodic;
     int pos_exp;           // delta0 = 2^(31 - pos_exp) when delta0_pow2: X = rint(x 2^pos_exp)
+    unsigned* status;      // the context's device status word (bounds-checked builds)
 };
 
 // Fixed-point TSC (shared by the deposit and the interpolation).  A drifted

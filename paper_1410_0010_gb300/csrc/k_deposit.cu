@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
             if (px >= 0 && px < p->N[0] && py >= 0 && py < p->N[1] && pz >= 0 && pz < p->N[2])
                 rho = par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
         }
-        row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
+        if (APM_IN_BOUNDS((long long)r * G0 + x, g.cells_gmf, L.status))
+            row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
     }
 }
 
@@ -135,12 +136,14 @@ __device__ __forceinline__ void scatter_charges(const LevelDev& L, int64_t* cons
                     long long v = (long long)mul63<SMALL>(mxy[a], w[2][c]);
                     v = M < 0 ? -v : v;
                     others += v;
-                    if (ok && cx[a] >= 0) add_charge(out, row + (unsigned)cx[a], v);
+                    if (ok && cx[a] >= 0 && APM_IN_BOUNDS(row + (unsigned)cx[a], g.cells_gmf, status))
+                        add_charge(out, row + (unsigned)cx[a], v);
                 }
             }
         }
-        if (cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0)
-            add_charge(out, (unsigned)cx[1] + G0 * (unsigned)cy[1] + G01 * (unsigned)cz[1], M - others);
+        const unsigned ci = (unsigned)cx[1] + G0 * (unsigned)cy[1] + G01 * (unsigned)cz[1];
+        if (cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0 && APM_IN_BOUNDS(ci, g.cells_gmf, status))
+            add_charge(out, ci, M - others);
     }
 }
 

@@ -161,6 +161,8 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel(Lev
         if (carry) {
             const long long kx = ((g.start[0] + ex0 - 1) - 1) >> 1;
             pbase = prow + (unsigned)(kx - ps[0] + 1);
+            // the block's 8 parent cells: pbase .. pbase + 1 + P0 + P01
+            if (!APM_IN_BOUNDS((long long)pbase + 1 + P0 + P01, pn, L.status)) continue;
         }
         // output cells: (ex0 + a, ey0 + b, ez0 + c); the pair a = 0, 1 is one
         // aligned pair store when both are inside and ex0 is even
@@ -366,6 +368,9 @@ __device__ __forceinline__ void interp_from(const LevelDev& L, const GridDev& g,
     const bool fold = g.mode == 1;
     int lc[3];
     for (int j = 0; j < 3; ++j) lc[j] = (int)((X[j] >> L.frac_bits) - g.start[j]);
+    // the owner's interior holds the particle's cell (fold: the root's box)
+    for (int j = 0; j < 3; ++j)
+        if (!APM_IN_BOUNDS(fold ? min(max(lc[j], 0), g.N[j] - 1) : lc[j], g.N[j], L.status)) return;
     T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -519,6 +524,7 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel_var
         if (carry) {
             const long long kx = ((g.start[0] + ex0 - 1) - 1) >> 1;
             pbase = prow + (unsigned)(kx - ps[0] + 1);
+            if (!APM_IN_BOUNDS((long long)pbase + 1 + P0 + P01, pn, L.status)) continue;
         }
         bool wr[2][2][2];
         unsigned o[2][2][2], c0[2][2][2];

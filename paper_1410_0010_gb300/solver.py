@@ -191,9 +191,12 @@ class Solver:
 
     def autotune(self, particles, half_dt, bufs, gas=None, levels=None, cache=None, stream=None):
         """Picks the FFT pass shapes of every level: from the JSON file `cache`
-        when it holds this GPU, precision and level shape; otherwise by one step
-        whose solves run the library's autotuner (apm_autotune_level), after
-        which the file is updated.  Returns {level: shapes}."""
+        (default: the APM_TUNE_CACHE environment variable, if set) when it holds
+        this GPU, precision and level shape; otherwise by one step whose solves
+        run the library's autotuner (apm_autotune_level), after which the file
+        is updated.  Returns {level: shapes}."""
+        if cache is None:
+            cache = os.environ.get("APM_TUNE_CACHE") or None
         levs = list(range(self.n_levels) if levels is None else levels)
         table = {}
         if cache and os.path.exists(cache):

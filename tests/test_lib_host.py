@@ -40,7 +40,7 @@ def test_defaults_are_the_papers(L):
     assert c.box == 1.0 and c.root_bc == 0 and c.mass_frac_bits == 52 and c.device == -1
     assert c.gradient == 0                                                  # two-point difference
     assert L.apm_version().startswith(b"apm-gb300")
-    for code in range(10):
+    for code in range(11):
         assert len(L.apm_status_string(code)) >= 2
     assert L.apm_status_string(99) == b"unknown status"
 
