@@ -501,6 +501,12 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel_var
     }
     const T inv12d = (T)g.inv12d;
     const unsigned st[3] = {1u, W0, W01};
+    // two-element accesses need even row lengths and pointers aligned to two elements
+    using V2 = typename Cplx<T>::type;
+    const size_t amask = 2 * sizeof(T) - 1;
+    const bool vout = !(E0 & 1) && !(ncell & 1) && !(reinterpret_cast<size_t>(phi) & amask) &&
+                      !(reinterpret_cast<size_t>(acc) & amask);
+    const bool vin = !(W0 & 1) && !(W01 & 1) && !(nw & 1) && !(reinterpret_cast<size_t>(phis) & amask);
     const long long nblocks = (long long)nbx * nbrows;
     const long long f0 = (long long)ch.tile * kAccBlocksPerCta;
     const int count = (int)min((long long)kAccBlocksPerCta, nblocks - f0);
@@ -539,18 +545,51 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel_var
                     o[c][b][a] = (unsigned)ex + (unsigned)E0 * ((unsigned)ey + (unsigned)E1 * (unsigned)ez);
                     c0[c][b][a] = (unsigned)(ex - 1 + h) + W0 * (unsigned)(ey - 1 + h) + W01 * (unsigned)(ez - 1 + h);
                 }
+        // a row pair (a = 0, 1) with both cells written moves as two-element
+        // loads and stores where aligned; other pairs cell by cell
+        const bool pst = vout && !(ex0 & 1);               // o[.][.][0] even
+        const bool pld = vin && !(c0[0][0][0] & 1);        // c0[.][.][0] even (W0, W01 even)
         T out[2][2][2], q[2][2][2];
         if (carry) {
             load_parent<T>(pphi, pbase, P0, P01, q);
             lerp_block<T>(q, out);
         }
+        auto put = [&](T* __restrict__ f, unsigned i, int c, int b, T v0, T v1) {
+            if (pst && wr[c][b][0] && wr[c][b][1]) {
+                *reinterpret_cast<V2*>(f + i) = mk2(v0, v1);
+            } else {
+                if (wr[c][b][0]) f[i] = v0;
+                if (wr[c][b][1]) f[i + 1] = v1;
+            }
+        };
+        auto ld2 = [&](const T* __restrict__ f, unsigned i, T& v0, T& v1) {
+            if (pld) {
+                const V2 u = *reinterpret_cast<const V2*>(f + i);
+                v0 = u.x;
+                v1 = u.y;
+            } else {
+                v0 = f[i];
+                v1 = f[i + 1];
+            }
+        };
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-                    if (wr[c][b][a]) phi[o[c][b][a]] = phis[c0[c][b][a]] + (carry ? out[c][b][a] : T(0));
+            for (int b = 0; b < 2; ++b) {
+                const unsigned ci = c0[c][b][0];
+                T v0 = 0, v1 = 0;
+                if (wr[c][b][0] && wr[c][b][1]) {
+                    ld2(phis, ci, v0, v1);
+                } else {
+                    if (wr[c][b][0]) v0 = phis[ci];
+                    if (wr[c][b][1]) v1 = phis[ci + 1];
+                }
+                if (carry) {
+                    v0 += out[c][b][0];
+                    v1 += out[c][b][1];
+                }
+                put(phi, o[c][b][0], c, b, v0, v1);
+            }
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             if (carry) {
@@ -560,21 +599,51 @@ __global__ void __launch_bounds__(kAccThreads, AccMinCtas<T>::value) k_accel_var
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
-                for (int b = 0; b < 2; ++b)
-#pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        if (!wr[c][b][a]) continue;
-                        const unsigned ci = c0[c][b][a];
-                        T v;
+                for (int b = 0; b < 2; ++b) {
+                    const unsigned ci = c0[c][b][0];
+                    T v[2] = {0, 0};
+                    if (wr[c][b][0] && wr[c][b][1]) {
                         if constexpr (GRAD == APM_GRAD_FD4) {
-                            const T d1 = phis[ci + st[j]] - phis[ci - st[j]];
-                            const T d2 = phis[ci + 2 * st[j]] - phis[ci - 2 * st[j]];
-                            v = -((T)8 * d1 - d2) * inv12d;
+                            if (j == 0) {   // x: cells ci-2 .. ci+3
+                                T m2, m1, p0, p1, p2, p3;
+                                ld2(phis, ci - 2, m2, m1);
+                                ld2(phis, ci, p0, p1);
+                                ld2(phis, ci + 2, p2, p3);
+                                v[0] = -((T)8 * (p1 - m1) - (p2 - m2)) * inv12d;
+                                v[1] = -((T)8 * (p2 - p0) - (p3 - m1)) * inv12d;
+                            } else {
+                                T a1[2], b1[2], a2[2], b2[2];
+                                ld2(phis, ci + st[j], a1[0], a1[1]);
+                                ld2(phis, ci - st[j], b1[0], b1[1]);
+                                ld2(phis, ci + 2 * st[j], a2[0], a2[1]);
+                                ld2(phis, ci - 2 * st[j], b2[0], b2[1]);
+#pragma unroll
+                                for (int a = 0; a < 2; ++a)
+                                    v[a] = -((T)8 * (a1[a] - b1[a]) - (a2[a] - b2[a])) * inv12d;
+                            }
                         } else {
-                            v = phis[(j + 1) * nw + ci];
+                            ld2(phis, (j + 1) * nw + ci, v[0], v[1]);
                         }
-                        acc[j * ncell + o[c][b][a]] = v + (carry ? out[c][b][a] : T(0));
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) {
+                            if (!wr[c][b][a]) continue;
+                            const unsigned cc = ci + a;
+                            if constexpr (GRAD == APM_GRAD_FD4) {
+                                const T d1 = phis[cc + st[j]] - phis[cc - st[j]];
+                                const T d2 = phis[cc + 2 * st[j]] - phis[cc - 2 * st[j]];
+                                v[a] = -((T)8 * d1 - d2) * inv12d;
+                            } else {
+                                v[a] = phis[(j + 1) * nw + cc];
+                            }
+                        }
                     }
+                    if (carry) {
+                        v[0] += out[c][b][0];
+                        v[1] += out[c][b][1];
+                    }
+                    put(acc + j * ncell, o[c][b][0], c, b, v[0], v[1]);
+                }
         }
     }
 }
