@@ -263,7 +263,8 @@ typedef struct {
 /* Autotuner: solves `level` like apm_solve_level (same arguments and outputs)
  * while timing every candidate shape of each FFT pass in turn (budgets
  * 512..8192 (FP32) or 256..4096 (FP64) by powers of two, 128 or 256 threads;
- * the mean of two launches after a warm one, CUDA events on `stream`), and
+ * the fastest of five timed launches after a warm one, CUDA events on
+ * `stream`), and
  * keeps the fastest shape per pass for the context's later calls.  phi_short
  * holds the level's potential on return.  Synchronises `stream` and the
  * device several times: APM_E_STATE while `stream` is being captured. */
