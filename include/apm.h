@@ -52,7 +52,7 @@ typedef enum {
     APM_E_OVERFLOW = 5,    /* |m 2^F| >= 2^62 for some particle (it was skipped) */
     APM_E_OUT_OF_BOX = 6,  /* particle outside an isolated root (folded to its edge) */
     APM_E_TIMEOUT = 7,     /* a bounded device wait ran out */
-    APM_E_UNSUPPORTED = 8, /* valid request this build does not implement */
+    APM_E_UNSUPPORTED = 8, /* valid request the library does not implement */
     APM_E_STATE = 9,       /* call out of order (e.g. no hierarchy set) */
     APM_E_BOUNDS = 10      /* a checked device access was out of range (only in
                               libraries built with -DAPM_BOUNDS_CHECK) */
