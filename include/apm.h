@@ -68,7 +68,9 @@ typedef enum { APM_BC_ISOLATED = 0, APM_BC_PERIODIC = 1 } apm_bc;
  *                    A_j(c) = -(phi(c+1) - phi(c-1)) / (2 delta)
  *  APM_GRAD_FD4      four-point difference,
  *                    D_j = (8 sin(k_j delta) - sin(2 k_j delta)) / (6 delta);
- *                    A_j(c) = -(8 (phi(c+1) - phi(c-1)) - (phi(c+2) - phi(c-2))) / (12 delta)
+ *                    A_j(c) = -(8 (phi(c+1) - phi(c-1)) - (phi(c+2) - phi(c-2))) / (12 delta);
+ *                    an isolated root then needs an even FFT length >= 2 N0 + 2,
+ *                    so N0 <= 511 (APM_E_UNSUPPORTED above)
  *  APM_GRAD_SPECTRAL D_j = k_j (0 on the Nyquist mode of an even M_j); the
  *                    short-range accelerations are transformed back from
  *                    -i D_j T rho-hat, one inverse transform per component. */
