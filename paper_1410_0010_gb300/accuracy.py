@@ -160,10 +160,9 @@ def force_decomposition(root=32, bins=16, device=0, precision="fp64"):
     s, bufs, _ = _solve(grids, P, 1, device, precision)
     edges = np.logspace(math.log10(0.5 / (root * 8)), math.log10(0.5), bins + 1)
     table = {"r": np.sqrt(edges[:-1] * edges[1:]).tolist(), "newton": [], "total_ratio": [], "levels": [],
-             "a": []}
+             "a": [], "delta": []}
     total_sum = np.zeros(bins)
     total_cnt = np.zeros(bins)
-    covered = []
     for lev in range(s.n_levels):
         g = s.grids[s.level_grids[lev][0]]
         b = bufs[lev]
@@ -199,11 +198,10 @@ def force_decomposition(root=32, bins=16, device=0, precision="fp64"):
             total_cnt[k] += selt.sum()
         table["levels"].append(mean_own)
         table["a"].append(3.4 * float(d))
-        covered.append(float(d))
+        table["delta"].append(float(d))
     s.close()
     table["total_ratio"] = [float(total_sum[k] / total_cnt[k]) if total_cnt[k] else None for k in range(bins)]
     table["newton"] = [1.0 / rr ** 2 for rr in table["r"]]
-    table["delta"] = covered
     return table
 
 
