@@ -41,6 +41,18 @@ class Workload:
         return int(sum(int(np.prod(g.dims)) for g in self.grids if lv is None or g.level in lv))
 
 
+
+# workload key -> name (the names the benchmark reports and keys its DRAM
+# traffic file by)
+NAMES = {
+    "c1": "isolated_root32_p4096",
+    "c2": "two_level_iso64",
+    "c3": "periodic128_3lev_plummer1M",
+    "c4": "batched512_level",
+    "c5": "cosmo512_2lev_zeldovich16M",
+    "c5s": "cosmo256_2lev_zeldovich2M",
+}
+
 def _particles(x, y, z, vx=None, vy=None, vz=None, m=None):
     n = len(x)
     z0 = np.zeros(n)
@@ -114,7 +126,7 @@ def config_isolated_root32(seed=1):
     n = 4096
     pos = rng.random((3, n))
     grids = [GridDesc(0, -1, (0, 0, 0), (32, 32, 32))]
-    return Workload("isolated_root32_p4096", False, grids,
+    return Workload(NAMES["c1"], False, grids,
                     _particles(pos[0], pos[1], pos[2], m=np.full(n, 1.0 / n)),
                     notes="uniform positions, m = 1/4096, no drift")
 
@@ -149,7 +161,7 @@ def config_two_level(seed=2):
     gas_r = _gaussian(xx, yy, zz, sigma)
     restr = gas_c.reshape(32, 2, 32, 2, 32, 2).mean(axis=(1, 3, 5))
     gas_r[16:48, 16:48, 16:48] = restr
-    return Workload("two_level_iso64", False, grids, parts, gas=[gas_r, gas_c],
+    return Workload(NAMES["c2"], False, grids, parts, gas=[gas_r, gas_c],
                     half_dt=1.5e-3, notes="Gaussian gas, two particles, half-step drift")
 
 
@@ -196,7 +208,7 @@ def config_plummer(seed=3, n=1 << 20, levels=3, child_n=64, root_n=128):
         pc = _densest_cell(cells, np.array(par.start), np.array(par.start) + np.array(par.dims))
         st = _centred_child(pc, child_n, np.array(par.start), np.array(par.dims))
         grids.append(GridDesc(lev, lev - 1, st, (child_n,) * 3))
-    return Workload("periodic128_3lev_plummer1M", True, grids, parts, half_dt=1e-3,
+    return Workload(NAMES["c3"], True, grids, parts, half_dt=1e-3,
                     notes="Plummer sphere, scale radius 4 root cells")
 
 
@@ -233,7 +245,7 @@ def config_batched_level(seed=4, n_grids=512, root_n=512):
         ms.append(np.full(npart, mass / npart))
     parts = _particles(np.concatenate(xs), np.concatenate(ys), np.concatenate(zs),
                        m=np.concatenate(ms))
-    return Workload("batched512_level", False, grids, parts, gas=gas, solve_levels=[1],
+    return Workload(NAMES["c4"], False, grids, parts, gas=gas, solve_levels=[1],
                     mass_frac_bits=60,
                     notes="short-range level solve only; the root is the container")
 
@@ -324,7 +336,7 @@ def config_cosmo512(seed=5, root_n=512, lattice=256, n_sub=64, sub_n=128):
         best = int(np.argmax(cnt))
         st = _centred_child(ctr[:, best], sub_n, pst, pdm)
         grids.append(GridDesc(2, gi, st, (sub_n,) * 3))
-    return Workload("cosmo512_2lev_zeldovich16M", True, grids, parts, half_dt=5e-4,
+    return Workload(NAMES["c5"], True, grids, parts, half_dt=5e-4,
                     notes="Zel'dovich lattice, P(k) ~ k^-2, v = 10 psi")
 
 
@@ -333,7 +345,7 @@ def config_cosmo_small(seed=6):
     128^3 = 2,097,152 Zel'dovich particles, two levels of 8 subgrids of 128^3
     (inputs still larger than the 129 MB L2: 134 MB root mass field + particles)."""
     w = config_cosmo512(seed=seed, root_n=256, lattice=128, n_sub=8, sub_n=128)
-    w.name = "cosmo256_2lev_zeldovich2M"
+    w.name = NAMES["c5s"]
     return w
 
 

@@ -217,7 +217,8 @@ def write_traffic(csv_path, small="c5s", full="c5", scale=8):
             continue
         d = per.setdefault(label, {})
         d[int(r[ii])] = d.get(int(r[ii]), 0.0) + float(r[vi].replace(",", "")) * unit.get(r[ui], 1)
-    ws, wf = workload(small).name, workload(full).name
+    import apm_inputs as W
+    ws, wf = W.NAMES[small], W.NAMES[full]
     out = {}
     for label, launches in sorted(per.items()):
         mean = sum(launches.values()) / len(launches)

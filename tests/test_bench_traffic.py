@@ -1,0 +1,80 @@
+"""bench.py's DRAM-traffic file from an ncu --csv capture (host logic): kernel
+names map to the bench's labels (the column passes by their template
+arguments), bytes are summed per launch over read and write, averaged per
+kernel, scaled to the full workload, and stamped with the sources' hash."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_kernel_names_map_to_labels():
+    b = _bench()
+    col = "void unnamed>::k_col<float, {}, {}, 256>(const GridDev *, const Chunk *, int)"
+    assert b.ncu_label(col.format(1, 0)) == "fft_y_fwd"
+    assert b.ncu_label(col.format(2, 1)) == "fft_z_green"
+    assert b.ncu_label(col.format(1, 2)) == "fft_y_inv"
+    assert b.ncu_label("void unnamed>::k_xf<float, 128>(const GridDev *)") == "fft_x_fwd"
+    assert b.ncu_label("void unnamed>::k_xi<double, 256>(const GridDev *)") == "fft_x_inv"
+    assert b.ncu_label("unnamed>::k_gas_init(LevelDev, const GridDev *)") == "gas_init"
+    assert b.ncu_label("unnamed>::k_deposit_levels(const LevelDev *, int)") == "tsc_deposit"
+    assert b.ncu_label("void unnamed>::k_accel<float>(LevelDev, const GridDev *)") == "accel_carry"
+    assert b.ncu_label("void unnamed>::k_interp_levels<float>(const LevelDev *, int)") == "tsc_interp"
+    assert b.ncu_label("void at::native::vectorized_elementwise_kernel<4>(int)") is None
+
+
+def test_write_traffic_averages_scales_and_stamps(tmp_path, monkeypatch):
+    b = _bench()
+    head = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+            '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
+    rows = []
+
+    def add(i, name, metric, unit, value):
+        rows.append(f'"{i}","1","python","h","{name}","1","7","(256, 1, 1)","(8, 1, 1)","0","10.3","m",'
+                    f'"{metric}","{unit}","{value}"')
+    acc = "void unnamed>::k_accel<float>(LevelDev, const GridDev *)"
+    add(0, acc, "dram__bytes_read.sum", "Mbyte", "100")
+    add(0, acc, "dram__bytes_write.sum", "Mbyte", "200")
+    add(0, acc, "gpu__time_duration.sum", "usecond", "50")
+    add(1, acc, "dram__bytes_read.sum", "Mbyte", "120")
+    add(1, acc, "dram__bytes_write.sum", "Kbyte", "180,000")
+    add(2, "unnamed>::k_gas_init(LevelDev)", "dram__bytes_write.sum", "byte", "1000")
+    csv_path = tmp_path / "t.csv"
+    csv_path.write_text("==PROF== noise\n" + head + "\n" + "\n".join(rows) + "\n")
+    written = {}
+
+    real_open = open
+
+    def fake_open(path, mode="r", *a, **k):
+        if str(path).endswith(os.path.join("profiles", "traffic.json")) and "w" in mode:
+            class W:
+                def __enter__(self_):
+                    return self_
+
+                def __exit__(self_, *e):
+                    return False
+
+                def write(self_, s):
+                    written.setdefault("s", "")
+                    written["s"] += s
+            return W()
+        return real_open(path, mode, *a, **k)
+
+    monkeypatch.setattr("builtins.open", fake_open)
+    b.write_traffic(str(csv_path))
+    doc = json.loads(written["s"])
+    import apm_inputs as W
+    small, full = W.NAMES["c5s"], W.NAMES["c5"]
+    assert W.config_isolated_root32().name == W.NAMES["c1"]
+    per = doc["per_launch_bytes"]
+    assert per[f"{small}:accel_carry"] == 300_000_000          # (300 MB + 300 MB) / 2 launches
+    assert per[f"{full}:accel_carry"] == 8 * 300_000_000
+    assert per[f"{small}:gas_init"] == 1000
+    assert doc["source_sha256"] == b.kernel_source_hash()
