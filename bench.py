@@ -102,7 +102,11 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
     """Bytes per step per kernel, summed over the solved levels.
 
     csz / rsz: bytes of one complex / real value of the precision; batched:
-    the deposit and the interpolation read the particles once for all levels."""
+    the deposit and the interpolation read the particles once for all levels.
+    The spectral gradient runs the z, y-inverse and x-inverse passes once per
+    component (phi, A_x, A_y, A_z), each reading its input again; its
+    acceleration kernel reads phi and the three components on the output
+    cells instead of differencing."""
     out = {k: 0 for k in ("gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green",
                           "fft_y_inv", "fft_x_inv", "accel_carry", "tsc_interp")}
     n = w.n_particles
@@ -117,12 +121,16 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
             out["tsc_deposit"] += 8 * cg                      # the accumulated field
             out["fft_x_fwd"] += 8 * cg + csz * G[1] * G[2] * Hx
             out["fft_y_fwd"] += csz * G[1] * G[2] * Hx + csz * G[2] * M[1] * Hx
-            out["fft_z_green"] += (csz * G[2] * M[1] * Hx + csz * Wd[2] * M[1] * Hx
-                                   + rsz * Hx * (M[1] // 2 + 1) * (M[2] // 2 + 1))
-            out["fft_y_inv"] += csz * Wd[2] * M[1] * Hx + csz * Wd[2] * Wd[1] * Hx
-            out["fft_x_inv"] += csz * Wd[2] * Wd[1] * Hx + rsz * Wd[0] * Wd[1] * Wd[2]
+            comps = inf.get("comps", 1)
+            out["fft_z_green"] += comps * (csz * G[2] * M[1] * Hx + csz * Wd[2] * M[1] * Hx
+                                           + rsz * Hx * (M[1] // 2 + 1) * (M[2] // 2 + 1))
+            out["fft_y_inv"] += comps * (csz * Wd[2] * M[1] * Hx + csz * Wd[2] * Wd[1] * Hx)
+            out["fft_x_inv"] += comps * (csz * Wd[2] * Wd[1] * Hx + rsz * Wd[0] * Wd[1] * Wd[2])
             ec = F[0] * F[1] * F[2]
-            out["accel_carry"] += rsz * Wd[0] * Wd[1] * Wd[2] + 4 * rsz * ec
+            if comps > 1:
+                out["accel_carry"] += 4 * rsz * ec + 4 * rsz * ec
+            else:
+                out["accel_carry"] += rsz * Wd[0] * Wd[1] * Wd[2] + 4 * rsz * ec
             out["tsc_interp"] += 3 * rsz * ec
         if not batched:
             out["tsc_deposit"] += 56 * n      # x, y, z, vx, vy, vz, m per level
@@ -355,7 +363,7 @@ def run_apm(args):
     w = workload(args.workload)
     levels = list(range(1 + max(g.level for g in w.grids))) if w.solve_levels is None else w.solve_levels
 
-    def make(precision, gradient="fd2"):
+    def make(precision, gradient=args.gradient):
         s = Solver(w.grids, periodic=w.periodic, precision=precision,
                    mass_frac_bits=w.mass_frac_bits, device=local, gradient=gradient)
         return s, s.alloc_all()
@@ -477,7 +485,7 @@ def run_apm(args):
     gradients = None
     if not args.no_gradients:
         gradients = {}
-        for grad in ("fd4", "spectral"):
+        for grad in [g for g in ("fd2", "fd4", "spectral") if g != args.gradient]:
             sv, bv = make("fp32", grad)
             pv = torch.zeros((3, n), dtype=torch.float32, device=dev)
 
@@ -503,7 +511,7 @@ def run_apm(args):
             sv.profile(False)
             sv.sync_status()
             gradients[grad] = {
-                "value": job_rate(ranks, cells, msv), "ms_per_step": msv, "time_vs_fd2": msv / ms,
+                "value": job_rate(ranks, cells, msv), "ms_per_step": msv, "time_vs_main": msv / ms,
                 "kernel_ms_per_step": {k: v[1] / args.steps for k, v in pv_prof.items() if v[0]},
                 "launches_per_step": sum(v[0] for v in pv_prof.values()) / args.steps}
             del gv
@@ -512,7 +520,7 @@ def run_apm(args):
 
     # ---------------- cuFFT comparison (context only: cuFFT is not on the product path)
     cufft = None
-    if not args.no_cufft:
+    if not args.no_cufft and args.gradient == "fd2":     # cuFFT does one convolution, like the two-point path
         cufft = cufft_convolution_ms(s32, levels, dev, args.steps, timed)
         ours = sum(prof[k][1] for k in ("fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv")
                    if k in prof) / max(args.steps, 1)
@@ -538,8 +546,9 @@ def run_apm(args):
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
-        # counters taken on other kernel sources do not describe these kernels
-        if tj.get("source_sha256") == kernel_source_hash():
+        # counters taken on other kernel sources (or on the two-point path when
+        # another operator runs) do not describe these kernels
+        if tj.get("source_sha256") == kernel_source_hash() and args.gradient == "fd2":
             traffic = tj.get("per_launch_bytes", {}).get(f"{w.name}:{top}")
     roofline = {"bound": "hbm", "kernel": top, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_source": peak_src, "traffic": traffic}
@@ -559,7 +568,7 @@ def run_apm(args):
         "config": {"workload": w.name, "levels": levels, "grids": len(w.grids),
                    "interior_cells": cells, "particles": n, "periodic": w.periodic,
                    "l2": "inputs larger than L2 (no flush)", "cuda_graph": used_graph,
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", "gradient": args.gradient,
                    "fft_shapes": shapes32},
         "particles_per_s": job_rate(ranks, n, ms) * 1e6,
         "roofline": roofline,
@@ -595,8 +604,10 @@ def main():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
     ap.add_argument("--write-traffic", metavar="CSV",
                     help="write profiles/traffic.json from an ncu --csv capture of one c5s step, then exit")
+    ap.add_argument("--gradient", choices=["fd2", "fd4", "spectral"], default="fd2",
+                    help="the gradient operator of the measured solve (default: the two-point difference)")
     ap.add_argument("--no-gradients", action="store_true",
-                    help="skip timing the four-point and spectral gradient operators")
+                    help="skip timing the other gradient operators")
     args = ap.parse_args()
     if args.write_traffic:
         print(write_traffic(args.write_traffic))
