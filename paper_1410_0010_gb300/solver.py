@@ -239,15 +239,28 @@ class Solver:
                                    t["vx"].data_ptr(), t["vy"].data_ptr(), t["vz"].data_ptr(),
                                    acc.data_ptr(), float(dt), _stream_handle(stream)), "apm_kick_drift")
 
-    def evolve(self, particles, dt, steps, bufs, pacc, gas=None, callback=None, stream=None):
+    def evolve(self, particles, dt, steps, bufs, pacc, gas=None, callback=None, stream=None,
+               graph=False):
         """`steps` timesteps without subcycling: each solves the hierarchy at
         the half-step drifted positions (half_dt = dt / 2) and applies
         apm_kick_drift.  callback(k, particles, pacc), if given, runs after
-        step k (k = 1 .. steps)."""
+        step k (k = 1 .. steps).  graph: after the first step (eager), one
+        step is captured as a CUDA graph and replayed for the others, which
+        removes the per-launch host cost (the same launches, the same
+        results)."""
         P = particles if isinstance(particles, Particles) else Particles(particles)
+        g = None
         for k in range(1, steps + 1):
-            self.step(P, 0.5 * dt, bufs, pacc, gas=gas, stream=stream)
-            self.kick_drift(P, pacc, dt, stream)
+            if g is not None:
+                g.replay()
+            else:
+                self.step(P, 0.5 * dt, bufs, pacc, gas=gas, stream=stream)
+                self.kick_drift(P, pacc, dt, stream)
+                if graph and k < steps:
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g):
+                        self.step(P, 0.5 * dt, bufs, pacc, gas=gas)
+                        self.kick_drift(P, pacc, dt)
             if callback is not None:
                 callback(k, P, pacc)
 
