@@ -481,6 +481,34 @@ def run_apm(args):
                 "fp32_speedup": ms64 / ms, "fp32_rel_l2_vs_fp64": {"phi_finest": e_phi, "pacc": e_pacc}}
         s64.close()
 
+    # ---------------- one evolution timestep (solve at half_dt = dt/2, then the
+    # kick-drift), graph-captured, on a copy of the particles (the kick moves
+    # them); the kick-drift alone against its algorithmic bytes: six FP64
+    # arrays read and written and the accelerations read, per particle
+    evolution = None
+    if not args.no_evolution:
+        Pe = Particles({k: v.clone() for k, v in dparts.items()})
+        dt = 2.0 * w.half_dt
+        pe = torch.zeros((3, n), dtype=torch.float32, device=dev)
+        s32.step(Pe, w.half_dt, b32, pe, gas=gas, levels=levels)
+        s32.kick_drift(Pe, pe, dt)
+        ge = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(ge):
+            s32.step(Pe, w.half_dt, b32, pe, gas=gas, levels=levels)
+            s32.kick_drift(Pe, pe, dt)
+        ge.replay()
+        torch.cuda.synchronize()
+        s32.sync_status()
+        ms_evo = timed(ge.replay, args.steps)
+        ms_kick = timed(lambda: s32.kick_drift(Pe, pe, dt), max(args.steps, 10))
+        s32.sync_status()
+        kick_bytes = (12 * 8 + 3 * 4) * n
+        evolution = {"ms_per_step": ms_evo, "steps_per_s": 1e3 / ms_evo,
+                     "kick_drift": {"ms_per_launch": ms_kick, "bytes_per_launch": kick_bytes,
+                                    "GBps": kick_bytes / (ms_kick * 1e-3) / 1e9,
+                                    "frac": kick_bytes / (ms_kick * 1e-3) / 1e9 / peaks()[0]}}
+        del ge, Pe, pe
+
     # ---------------- the other gradient operators (Sec. 2.2), FP32, same workload
     gradients = None
     if not args.no_gradients:
@@ -580,6 +608,7 @@ def run_apm(args):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "fp64": fp64,
         "gradients": gradients,
+        "evolution": evolution,
         "cufft_compare": cufft,
         "clocks": clk,
     }
@@ -604,6 +633,7 @@ def main():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
     ap.add_argument("--write-traffic", metavar="CSV",
                     help="write profiles/traffic.json from an ncu --csv capture of one c5s step, then exit")
+    ap.add_argument("--no-evolution", action="store_true", help="skip timing the evolution timestep")
     ap.add_argument("--gradient", choices=["fd2", "fd4", "spectral"], default="fd2",
                     help="the gradient operator of the measured solve (default: the two-point difference)")
     ap.add_argument("--no-gradients", action="store_true",

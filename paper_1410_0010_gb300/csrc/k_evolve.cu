@@ -16,17 +16,23 @@ __global__ void __launch_bounds__(256) k_kick_drift(long long n, double* __restr
                                                     const T* __restrict__ acc, double dt) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= n) return;
-    double* pos[3] = {x, y, z};
-    double* vel[3] = {vx, vy, vz};
+    // all nine loads first (the arrays are distinct), then the updates
+    const double v[3] = {vx[p], vy[p], vz[p]};
+    const double q[3] = {x[p], y[p], z[p]};
+    const double a[3] = {(double)acc[p], (double)acc[n + p], (double)acc[2 * n + p]};
+    double vn[3], qn[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const double v = vel[j][p];
-        const double a = (double)acc[j * n + p];
-        const double vn = __dadd_rn(v, __dmul_rn(a, dt));
-        const double vm = __dmul_rn(__dadd_rn(v, vn), 0.5);
-        pos[j][p] = __dadd_rn(pos[j][p], __dmul_rn(vm, dt));
-        vel[j][p] = vn;
+        vn[j] = __dadd_rn(v[j], __dmul_rn(a[j], dt));
+        const double vm = __dmul_rn(__dadd_rn(v[j], vn[j]), 0.5);
+        qn[j] = __dadd_rn(q[j], __dmul_rn(vm, dt));
     }
+    x[p] = qn[0];
+    y[p] = qn[1];
+    z[p] = qn[2];
+    vx[p] = vn[0];
+    vy[p] = vn[1];
+    vz[p] = vn[2];
 }
 
 }  // namespace
