@@ -78,3 +78,41 @@ def test_write_traffic_averages_scales_and_stamps(tmp_path, monkeypatch):
     assert per[f"{full}:accel_carry"] == 8 * 300_000_000
     assert per[f"{small}:gas_init"] == 1000
     assert doc["source_sha256"] == b.kernel_source_hash()
+
+
+def test_algorithmic_bytes_per_operator():
+    """bench.py's algorithmic bytes for one refined grid: the spectral path
+    counts its z, y-inverse and x-inverse passes four times and reads four
+    windows in the acceleration kernel; the four-point one differences a
+    wider window."""
+    import types
+
+    import numpy as np
+    b = _bench()
+    N, B = 8, 5
+    G = (N + 2 * B,) * 3
+    M = (30, 30, 30)
+    E = (N + 2,) * 3
+
+    def solver(h, comps):
+        W = (N + 2 * h,) * 3
+        info = [dict(gmf=G, fft=M, phi_short=W, field=E, comps=comps)]
+        return types.SimpleNamespace(level_grids=[[0]], info=info, n_levels=1), W
+    w = types.SimpleNamespace(n_particles=0, gas=None, grids=[types.SimpleNamespace(dims=(N, N, N))])
+    csz, rsz = 8, 4
+    Hx = M[0] // 2 + 1
+    s2, W2 = solver(2, 1)
+    s4, W4 = solver(3, 1)
+    ss, Ws = solver(2, 4)
+    a2 = b.algorithmic_bytes(s2, w, [0], csz, rsz, True)
+    a4 = b.algorithmic_bytes(s4, w, [0], csz, rsz, True)
+    asp = b.algorithmic_bytes(ss, w, [0], csz, rsz, True)
+    ec = int(np.prod(E))
+    assert a2["accel_carry"] == rsz * int(np.prod(W2)) + 4 * rsz * ec
+    assert a4["accel_carry"] == rsz * int(np.prod(W4)) + 4 * rsz * ec
+    assert asp["accel_carry"] == 8 * rsz * ec
+    for k in ("fft_z_green", "fft_y_inv", "fft_x_inv"):
+        assert asp[k] == 4 * a2[k], k
+    for k in ("gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd"):
+        assert asp[k] == a2[k] == a4[k], k
+    assert a2["fft_x_fwd"] == 8 * int(np.prod(G)) + csz * G[1] * G[2] * Hx
