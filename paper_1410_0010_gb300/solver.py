@@ -23,6 +23,21 @@ def _ptr(t):
     return None if t is None else t.data_ptr()
 
 
+def check_field(t, shape, dtype, device, name):
+    """The C ABI sees only a pointer: a tensor handed to it must have this
+    exact shape and dtype, be contiguous and live on the context's device."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the context on {device}")
+
+
 class Particles:
     """Device particle arrays (float64, contiguous) and their C view."""
 
@@ -147,6 +162,7 @@ class Solver:
     def interp_all(self, acc, particles, half_dt, out, stream=None):
         """apm_interp_all: acc is a list over the hierarchy's grids."""
         P = particles if isinstance(particles, Particles) else Particles(particles)
+        check_field(out, (3, P.n), self.dtype, self.device, "particle accelerations")
         check(lib().apm_interp_all(self._ctx, ptr_array([_ptr(t) for t in acc]), ctypes.byref(P.c),
                                    float(half_dt), out.data_ptr(), _stream_handle(stream)),
               "apm_interp_all")
@@ -234,6 +250,9 @@ class Solver:
         """apm_kick_drift: one leapfrog step in place, acc (3, n) evaluated at
         the half-step drifted positions (step with half_dt = dt / 2)."""
         P = particles if isinstance(particles, Particles) else Particles(particles)
+        check_field(acc, (3, P.n), self.dtype, self.device, "accelerations")
+        for k in ("x", "y", "z", "vx", "vy", "vz"):
+            check_field(P.t[k], (P.n,), torch.float64, self.device, f"particle array {k}")
         t = P.t
         check(lib().apm_kick_drift(self._ctx, P.n, t["x"].data_ptr(), t["y"].data_ptr(), t["z"].data_ptr(),
                                    t["vx"].data_ptr(), t["vy"].data_ptr(), t["vz"].data_ptr(),
@@ -294,6 +313,14 @@ class Solver:
         (apm_deposit_all / apm_interp_all, bit-identical to the per-level calls)
         when all levels are stepped."""
         P = particles if isinstance(particles, Particles) else Particles(particles)
+        if pacc is not None:
+            check_field(pacc, (3, P.n), self.dtype, self.device, "particle accelerations")
+        if gas is not None:
+            if len(gas) != len(self.grids):
+                raise ValueError(f"gas has {len(gas)} entries, the hierarchy {len(self.grids)} grids")
+            for gi, g in enumerate(gas):
+                if g is not None:
+                    check_field(g, tuple(self.grids[gi][3])[::-1], torch.float64, self.device, f"gas of grid {gi}")
         levs = range(self.n_levels) if levels is None else levels
         whole = batched and (levels is None or list(levels) == list(range(self.n_levels)))
         if whole:   # every level: one pass over the particles (apm_deposit_all)

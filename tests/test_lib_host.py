@@ -146,3 +146,21 @@ def test_package_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not found"):
         _lib.lib()
+
+
+def test_binding_checks_tensors_before_the_c_abi():
+    import torch
+
+    from paper_1410_0010_gb300.solver import check_field
+    ok = torch.zeros((3, 5), dtype=torch.float32)
+    check_field(ok, (3, 5), torch.float32, None, "acc")
+    with pytest.raises(ValueError, match="shape"):
+        check_field(ok, (3, 6), torch.float32, None, "acc")
+    with pytest.raises(ValueError, match="dtype"):
+        check_field(ok, (3, 5), torch.float64, None, "acc")
+    with pytest.raises(ValueError, match="contiguous"):
+        check_field(torch.zeros((5, 3)).t(), (3, 5), torch.float32, None, "acc")
+    with pytest.raises(ValueError, match="context"):
+        check_field(ok, (3, 5), torch.float32, torch.device("cuda", 0), "acc")
+    with pytest.raises(TypeError):
+        check_field([0.0], (1,), torch.float32, None, "acc")
