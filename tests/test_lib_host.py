@@ -164,3 +164,64 @@ def test_binding_checks_tensors_before_the_c_abi():
         check_field(ok, (3, 5), torch.float32, torch.device("cuda", 0), "acc")
     with pytest.raises(TypeError):
         check_field([0.0], (1,), torch.float32, None, "acc")
+
+
+def _rules_hold(descs, periodic, B=5):
+    """The nesting rules of apm_set_hierarchy written out (reading R9): a root
+    first; every other grid's parent one level up; levels contiguous; the
+    parent cells that a child's GMF border (floor((start - B) / 2) ..
+    floor((start + N + B - 1) / 2)) and the carry of its cells [-1, N] read lie
+    in the parent's interior, except that a level-1 border may leave an
+    isolated root; sibling interiors disjoint."""
+    import math
+    root = descs[0]
+    if root[0] != 0 or root[1] != -1 or any(root[2]) or len(set(root[3])) != 1:
+        return False
+    levels = set()
+    for i, (lev, par, st, dm) in enumerate(descs):
+        if i == 0:
+            continue
+        if lev < 1 or not (0 <= par < len(descs)) or par == i or descs[par][0] != lev - 1:
+            return False
+        levels.add(lev)
+        p = descs[par]
+        past_root = par == 0 and not periodic
+        for j in range(3):
+            lo_b, hi_b = (st[j] - B) // 2, (st[j] + dm[j] + B - 1) // 2
+            lo_c = math.floor((st[j] - 1 + 0.5) / 2 - 0.5)
+            hi_c = math.floor((st[j] + dm[j] + 0.5) / 2 - 0.5) + 1
+            lo, hi = (lo_c, hi_c) if past_root else (min(lo_b, lo_c), max(hi_b, hi_c))
+            if lo < p[2][j] or hi >= p[2][j] + p[3][j]:
+                return False
+    if levels and levels != set(range(1, max(levels) + 1)):
+        return False
+    for i in range(1, len(descs)):
+        for k in range(i + 1, len(descs)):
+            a, b = descs[i], descs[k]
+            if a[0] == b[0] and all(a[2][j] < b[2][j] + b[3][j] and b[2][j] < a[2][j] + a[3][j]
+                                    for j in range(3)):
+                return False
+    return True
+
+
+def test_validation_agrees_with_the_rules_on_random_hierarchies(L):
+    import random
+    rnd = random.Random(12)
+    agree = {True: 0, False: 0}
+    for t in range(600):
+        n0 = rnd.choice([16, 20, 24])
+        descs = [(0, -1, (0, 0, 0), (n0, n0, n0))]
+        for lev in range(1, rnd.randint(1, 3)):
+            parents = [i for i, d in enumerate(descs) if d[0] == lev - 1]
+            for _ in range(rnd.randint(1, 2)):
+                par = rnd.choice(parents)
+                p = descs[par]
+                st = tuple(2 * p[2][j] + rnd.randint(-2, 2 * p[3][j]) for j in range(3))
+                dm = tuple(rnd.randint(2, 2 * p[3][j]) for j in range(3))
+                descs.append((lev, par, st, dm))
+        periodic = rnd.random() < 0.5
+        want = _rules_hold(descs, periodic)
+        got = _validate(L, descs, periodic=periodic)
+        assert (got == 0) == want, (descs, periodic, got)
+        agree[want] += 1
+    assert agree[True] > 50 and agree[False] > 50, agree
