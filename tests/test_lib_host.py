@@ -208,20 +208,33 @@ def test_validation_agrees_with_the_rules_on_random_hierarchies(L):
     import random
     rnd = random.Random(12)
     agree = {True: 0, False: 0}
+    nested = 0
     for t in range(600):
         n0 = rnd.choice([16, 20, 24])
         descs = [(0, -1, (0, 0, 0), (n0, n0, n0))]
-        for lev in range(1, rnd.randint(1, 3)):
+        for lev in range(1, rnd.randint(2, 4)):
             parents = [i for i, d in enumerate(descs) if d[0] == lev - 1]
-            for _ in range(rnd.randint(1, 2)):
+            for _ in range(1 if rnd.random() < 0.75 else 2):
                 par = rnd.choice(parents)
                 p = descs[par]
-                st = tuple(2 * p[2][j] + rnd.randint(-2, 2 * p[3][j]) for j in range(3))
-                dm = tuple(rnd.randint(2, 2 * p[3][j]) for j in range(3))
-                descs.append((lev, par, st, dm))
+                st, dm = [], []
+                near = rnd.random() < 0.8
+                for j in range(3):
+                    lo, hi = 2 * p[2][j], 2 * (p[2][j] + p[3][j])
+                    if near:                    # near the legal range: margins of 5 to 8 cells,
+                        m = lambda: rnd.randint(5, 8) if rnd.random() < 0.9 else rnd.randint(2, 4)
+                        s0 = lo + m()             # now and then 2 to 4 (the border leaves the parent)
+                        e0 = max(s0 + 2, hi - m())
+                    else:                       # anywhere around the parent
+                        s0 = lo + rnd.randint(-2, hi - lo)
+                        e0 = s0 + rnd.randint(2, hi - lo)
+                    st.append(s0)
+                    dm.append(e0 - s0)
+                descs.append((lev, par, tuple(st), tuple(dm)))
         periodic = rnd.random() < 0.5
         want = _rules_hold(descs, periodic)
         got = _validate(L, descs, periodic=periodic)
         assert (got == 0) == want, (descs, periodic, got)
         agree[want] += 1
-    assert agree[True] > 50 and agree[False] > 50, agree
+        nested += want and len(descs) > 1
+    assert agree[False] > 100 and nested > 100, (agree, nested)
