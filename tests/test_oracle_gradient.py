@@ -176,3 +176,48 @@ def test_fd4_isolated_root_window_sees_unwrapped_offsets(oracle_mod):
             want += mass[tuple(s)] * oracle_mod.psi(np.linalg.norm(off) * d / a) / a
         got = phis[c[2] + h, c[1] + h, c[0] + h]
         assert got == pytest.approx(want, rel=1e-12), c
+
+
+@pytest.mark.parametrize("M", [(12, 10, 9), (16, 15, 14)])
+def test_spectral_solve_equals_numpy_fft_route(oracle_mod, M):
+    """orc_solve_spectral against numpy's FFT on a random mass field: the mass
+    on the M grid, its transform times the table, times -i k_j (0 on an even
+    M's Nyquist mode) for A_j, transformed back and windowed.  Pins the
+    spectral solve's transforms, product, sign and window on every mode."""
+    import ctypes
+    rng = np.random.default_rng(7)
+    G = (M[0] - 3, M[1] - 2, M[2] - 4)
+    W = (M[0] + 2, M[1] - 1, M[2] + 1)          # longer than M on x and z: wraps
+    s0 = (M[0] - 2, 3, M[2] - 1)
+    F = 40
+    delta = 1.0 / 16
+    gmf = rng.integers(-2 ** 40, 2 ** 40, size=G[::-1], dtype=np.int64)
+    H = tuple(m // 2 + 1 for m in M)
+    T = rng.normal(size=H[::-1])                 # any table even in every kappa_j
+    out = np.zeros((4,) + W[::-1])
+    lib = oracle_mod.lib()
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    lib.orc_solve_spectral(P(gmf), P(np.array(G, dtype=np.int64)), F, P(np.array(M, dtype=np.int64)),
+                           P(np.array(s0, dtype=np.int64)), P(np.array(W, dtype=np.int64)), P(T), delta,
+                           P(out), 1)
+    mass = np.zeros(M[::-1])
+    mass[:G[2], :G[1], :G[0]] = np.ldexp(gmf.astype(float), -F)
+    rho = np.fft.fftn(mass)
+    idx = [np.minimum(np.arange(m), m - np.arange(m)) for m in M]
+    Tf = T[np.ix_(idx[2], idx[1], idx[0])]
+    phi_hat = Tf * rho
+    comps = [phi_hat]
+    for j in range(3):
+        m = M[j]
+        kc = np.where(np.arange(m) <= m // 2, np.arange(m), np.arange(m) - m)
+        k = 2 * np.pi * kc / (m * delta)
+        if m % 2 == 0:
+            k[m // 2] = 0.0
+        shape = [1, 1, 1]
+        shape[2 - j] = m
+        comps.append(-1j * k.reshape(shape) * phi_hat)
+    for c, spec in enumerate(comps):
+        field = np.fft.ifftn(spec).real
+        sel = np.ix_(*[(s0[a] + np.arange(W[a])) % M[a] for a in (2, 1, 0)])
+        want = field[sel]
+        assert np.allclose(out[c], want, rtol=0, atol=1e-12 * np.abs(want).max()), c
