@@ -7,9 +7,15 @@ the FD accelerations with the parent carry, then the TSC interpolation to all
 particles.  Default workload: periodic 512^3 root + 2 levels of 64 subgrids of
 128^3, 16,777,216 Zel'dovich particles (the largest single-GPU configuration).
 
-Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
-a bounded sample of the same workload instead.
+Prints ONE JSON line (rank 0): the step's throughput and per-kernel bandwidth,
+the dominant kernel's roofline (with its ncu DRAM traffic when the sources
+match the capture), the end-to-end step through StepPipeline, the FP64 path,
+the other gradient operators, one evolution timestep and the kick-drift, the
+cuFFT comparison and the CPU oracle on a sample.  `--impl reference` times the
+FP64 CPU oracle on a bounded sample of the same workload instead;
+`--write-traffic CSV` writes profiles/traffic.json from an ncu capture.
 Run: python bench.py [--gpus N --steps K --warmup W] [--workload c5|c4|c3]
+     [--gradient fd2|fd4|spectral]
 """
 import argparse
 import json
