@@ -10,11 +10,14 @@ particles.  Default workload: periodic 512^3 root + 2 levels of 64 subgrids of
 Prints ONE JSON line (rank 0): the step's throughput and per-kernel bandwidth,
 the dominant kernel's roofline (with its ncu DRAM traffic when the sources
 match the capture), the end-to-end step through StepPipeline, the FP64 path,
-the other gradient operators, one evolution timestep and the kick-drift, the
-cuFFT comparison and the CPU oracle on a sample.  `--impl reference` times the
+the plain per-grid path (the same kernels launched grid by grid, FP64 and
+FP32) and the batched FP32 step's speed-up over it, the FFT passes' combined
+fraction of HBM peak, the other gradient operators, one evolution timestep and
+the kick-drift, the cuFFT comparison, and the CPU oracle on a sample together
+with each GPU path's error against it.  `--impl reference` times the
 FP64 CPU oracle on a bounded sample of the same workload instead;
 `--write-traffic CSV` writes profiles/traffic.json from an ncu capture.
-Run: python bench.py [--gpus N --steps K --warmup W] [--workload c5|c4|c3]
+Run: python bench.py [--gpus N --steps K --warmup W] [--workload c5|c4|c3|c2|c1]
      [--gradient fd2|fd4|spectral]
 """
 import argparse
@@ -252,26 +255,37 @@ def write_traffic(csv_path, small="c5s", full="c5", scale=8):
 # ----------------------------------------------------------------------------
 # oracle sample (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample(w, n_grids=2):
-    """The first n_grids refined grids of the workload solved by the FP64 CPU oracle:
-    TSC deposit of every particle touching each GMF, naive-DFT convolution on its
-    M grid, FD accelerations (the parent carry is omitted: zero parent fields).
-    Returns (interior cells, seconds, description)."""
+def sample_grids(w, n_grids=2):
+    """The grids the oracle sample solves: the first n_grids refined grids of the
+    solved levels, or the root when no refined level is solved."""
+    ids = [i for i, g in enumerate(w.grids)
+           if g.level >= 1 and (w.solve_levels is None or g.level in w.solve_levels)][:n_grids]
+    return ids or [0]
+
+
+def oracle_sample(w, n_grids=2, outputs=None):
+    """The sampled grids of the workload (sample_grids) solved by the FP64 CPU
+    oracle: TSC deposit of every particle touching each GMF (with the grid's
+    gas), naive-DFT convolution on its M grid, FD accelerations (the parent
+    carry is omitted: zero parent fields).  Returns (interior cells, seconds,
+    description); with outputs={} it also fills outputs[gi] = (phi_short, acc)."""
     import oracle
     cfg = oracle.Config(periodic=w.periodic, mass_frac_bits=w.mass_frac_bits)
     grids = [oracle.Grid(*g) for g in w.grids]
-    ids = [i for i, g in enumerate(w.grids) if g.level >= 1][:n_grids]
+    ids = sample_grids(w, n_grids)
     oracle.lib()
     t0 = time.perf_counter()
     for gi in ids:
         gas = None if w.gas is None else w.gas[gi]
         gmf, _ = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt, gas=gas)
         phis = oracle.solve(cfg, grids, gi, gmf)
-        oracle.accel(cfg, grids, gi, phis)
+        _, acc = oracle.accel(cfg, grids, gi, phis)
+        if outputs is not None:
+            outputs[gi] = (phis, acc)
     dt = time.perf_counter() - t0
     cells = int(sum(np.prod(w.grids[gi].dims) for gi in ids))
     plans = [oracle.plan_grid(cfg, grids, gi).M for gi in ids]
-    desc = (f"oracle solve of {len(ids)} refined subgrids {[tuple(w.grids[gi].dims) for gi in ids]} "
+    desc = (f"oracle solve of {len(ids)} grid(s) {[tuple(w.grids[gi].dims) for gi in ids]} "
             f"(M={plans}): deposit of all {w.n_particles} particles, naive-DFT convolution, "
             f"FD accelerations")
     return cells, dt, desc
@@ -326,6 +340,38 @@ def job_rate(ranks, units, ms):
     """Whole-job throughput in millions of units per second: the units all ranks
     processed over the slowest rank's time (ms, the max over ranks)."""
     return ranks.sum(units) / (ms / 1e3) / 1e6
+
+
+def snapshot(solver, bufs, ids):
+    """Host copies of the sampled grids' phi_short and accelerations."""
+    out = {}
+    for gi in ids:
+        lev, k = solver.info[gi]["level"], solver.info[gi]["level_index"]
+        out[gi] = (bufs[lev]["phis"][k].double().cpu().numpy(), bufs[lev]["acc"][k].double().cpu().numpy())
+    return out
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def errors_vs_oracle(snap, ref, carried):
+    """Relative L2 of the GPU outputs against the oracle's on the sampled grids:
+    phi_short always; the accelerations only on grids whose step added no
+    parent carry (the oracle sample omits it)."""
+    e_phi = max(rel_l2(snap[gi][0], ref[gi][0]) for gi in ref)
+    acc = [rel_l2(snap[gi][1], ref[gi][1]) for gi in ref if not carried(gi)]
+    return {"phi_short": e_phi, "acc": max(acc) if acc else None}
+
+
+def fft_pass_summary(prof, ab, steps, hbm):
+    """The five FFT passes together: algorithmic bytes over their summed device
+    time per step, and that bandwidth as a fraction of the HBM peak."""
+    names = ("fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv")
+    ms = sum(prof[k][1] for k in names if k in prof) / max(steps, 1)
+    byts = sum(ab[k] for k in names)
+    gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else None
+    return {"ms_per_step": ms, "bytes_per_step": byts, "GBps": gbs, "frac": gbs / hbm if gbs else None}
 
 
 def run_reference(args):
@@ -429,6 +475,8 @@ def run_apm(args):
     ms = timed(run, args.steps)
     clk = clocks.stop()
     s32.sync_status()
+    ids = sample_grids(w)
+    snap32 = snapshot(s32, b32, ids)
 
     # per-kernel device times (tracing on, eager, same workload)
     s32.profile(True)
@@ -485,7 +533,53 @@ def run_apm(args):
                           for a, b in zip(phi32, b64[-1]["phi"])))
         fp64 = {"value": job_rate(ranks, cells, ms64), "ms_per_step": ms64,
                 "fp32_speedup": ms64 / ms, "fp32_rel_l2_vs_fp64": {"phi_finest": e_phi, "pacc": e_pacc}}
+        snap64 = snapshot(s64, b64, ids)
         s64.close()
+        del b64, pacc64
+
+    # ---------------- the plain per-grid path: the same kernels launched grid
+    # by grid (apm_set_grid_batching(0)) for the level solve and the
+    # accelerations, FP64 and FP32, graph-captured like the main step;
+    # the batched FP32 step's speed-up over it at the accuracy reported
+    per_grid = None
+    if not args.no_per_grid:
+        per_grid = {"launch": "one launch sequence per grid for apm_solve_level and apm_accel; "
+                              "deposit and interpolation one pass over the particles for all levels"}
+        for prec in ("fp64", "fp32"):
+            sp, bp = make(prec)
+            sp.set_grid_batching(False)
+            pp = torch.zeros((3, n), dtype=sp.dtype, device=dev)
+
+            def stepp():
+                sp.step(P, w.half_dt, bp, pp, gas=gas, levels=levels)
+
+            if not args.no_tune:
+                sp.autotune(P, w.half_dt, bp, gas=gas, levels=levels)
+            stepp()
+            sp.sync_status()
+            gp = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gp):
+                stepp()
+            gp.replay()
+            torch.cuda.synchronize()
+            sp.sync_status()
+            msp = timed(gp.replay, max(1, args.steps // 2))
+            ms_eager = timed(stepp, 1)
+            ref = pacc if prec == "fp32" else None
+            per_grid[prec] = {"ms_per_step": msp, "value": job_rate(ranks, cells, msp),
+                              "eager_ms_per_step": ms_eager,
+                              "launches_per_step": None,
+                              "equal_to_batched": bool(torch.equal(pp, ref)) if ref is not None else None}
+            sp.profile(True)
+            stepp()
+            lp = sp.profile_read()
+            sp.profile(False)
+            per_grid[prec]["launches_per_step"] = sum(v[0] for v in lp.values())
+            del gp
+            sp.close()
+            del bp, pp
+        per_grid["batched_fp32_speedup_vs_per_grid_fp64"] = per_grid["fp64"]["ms_per_step"] / ms
+        per_grid["batched_fp32_speedup_vs_per_grid_fp32"] = per_grid["fp32"]["ms_per_step"] / ms
 
     # ---------------- one evolution timestep (solve at half_dt = dt/2, then the
     # kick-drift), graph-captured, on a copy of the particles (the kick moves
@@ -519,8 +613,13 @@ def run_apm(args):
     gradients = None
     if not args.no_gradients:
         gradients = {}
+        from paper_1410_0010_gb300._lib import ApmError
         for grad in [g for g in ("fd2", "fd4", "spectral") if g != args.gradient]:
-            sv, bv = make("fp32", grad)
+            try:
+                sv, bv = make("fp32", grad)
+            except ApmError as exc:      # e.g. the four-point root limit (N0 <= 511, isolated)
+                gradients[grad] = {"unsupported": str(exc)}
+                continue
             pv = torch.zeros((3, n), dtype=torch.float32, device=dev)
 
             def stepv():
@@ -573,6 +672,7 @@ def run_apm(args):
         kernels[name] = {"launches_per_step": cnt / args.steps, "ms_per_launch": per_launch_ms,
                          "share": tot / sum(v[1] for v in prof.values()),
                          "GBps": bytes_per_launch / (per_launch_ms * 1e-3) / 1e9}
+    fft_passes = fft_pass_summary(prof, ab, args.steps, hbm)
     top = max(kernels, key=lambda k: kernels[k]["share"])
     ach = kernels[top]["GBps"]
     traffic = None
@@ -589,10 +689,20 @@ def run_apm(args):
 
     # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
     cpu = None
+    err_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        c, dt, desc = oracle_sample(w)
+        ref = {}
+        c, dt, desc = oracle_sample(w, outputs=ref)
         cpu = {"value": c / dt / 1e6, "unit": "Mcells/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": desc, "seconds": dt}
+
+        def carried(gi):
+            lev = s32.info[gi]["level"]
+            return lev > 0 and (lev - 1) in levels
+
+        err_oracle = {"grids": ids, "fp32": errors_vs_oracle(snap32, ref, carried),
+                      "fp64": errors_vs_oracle(snap64, ref, carried) if fp64 is not None else None,
+                      "tolerance": {"fp32": {"phi_short": 2e-5, "acc": 1e-4}, "fp64": 1e-12}}
 
     value = job_rate(ranks, cells, ms)
     line = {
@@ -613,6 +723,9 @@ def run_apm(args):
                 "pipelined": True, "serial_ms_per_step": e2e_serial_ms},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "fp64": fp64,
+        "per_grid": per_grid,
+        "fft_passes": fft_passes,
+        "rel_l2_vs_oracle": err_oracle,
         "gradients": gradients,
         "evolution": evolution,
         "cufft_compare": cufft,
@@ -632,9 +745,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["apm", "reference"], default="apm")
-    ap.add_argument("--workload", choices=["c3", "c4", "c5", "c5s"], default="c5")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "c5s"], default="c5")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-per-grid", action="store_true",
+                    help="skip timing the plain per-grid launch path (FP64 and FP32)")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
     ap.add_argument("--write-traffic", metavar="CSV",

@@ -247,6 +247,16 @@ apm_status apm_accel(apm_ctx* ctx, int32_t level, const void* const* phi_short,
                      const void* const* parent_phi, const void* const* parent_acc,
                      void* const* phi, void* const* acc, void* stream);
 
+/* Launch granularity of apm_solve_level and apm_accel.  batched = 1 (the
+ * default): each FFT pass, and the acceleration kernel, is one launch over
+ * every grid of the level.  batched = 0: one launch sequence per grid, grid
+ * after grid, which is how the paper's implementation runs the level (Sec. 2.2:
+ * one FFT convolution per grid); kept as the plain per-grid baseline the
+ * batched launches are measured against.  Every grid runs the same kernels on
+ * the same work items either way, so the results are bit-identical.
+ * APM_E_INVALID for a value other than 0 or 1. */
+apm_status apm_set_grid_batching(apm_ctx* ctx, int32_t batched);
+
 /* Launch shapes of the five FFT passes of one level (x forward, y forward, z
  * with the table, y inverse, x inverse), in that order.  budget[p] is the
  * number of complex elements one shared-memory buffer of a pass CTA aims at:
@@ -329,14 +339,18 @@ int32_t apm_kernel_count(void);
 const char* apm_kernel_name(int32_t kernel);
 
 /* Potential of one periodic root grid without allocating anything.
- * The paper has no counterpart: this is a convenience for callers that cannot
- * call cudaMalloc (code running where the CUDA runtime may not allocate, such
- * as host callbacks or graph-capture regions, or programs whose memory pool
- * owns the whole device).  It needs no context: it computes what apm_solve_level
- * computes for a periodic root of n^3 cells (box side `box`, smoothing
- * a = a_over_dx * box / n), in FP32, with every intermediate (twiddles, the
- * Green's table, the FFT spectra) kept in one fixed 24 MiB device array that
- * each GPU loading the library holds until the process exits.
+ * The paper has no counterpart.  Some callers cannot call cudaMalloc:
+ * applications that give the whole device to their own memory pool at
+ * start-up (a library allocating behind their back would fail, or break the
+ * pool's accounting), and loops that must not stall on the device-wide
+ * synchronisation cudaFree implies.  This entry point needs no context and
+ * allocates nothing; it computes what apm_solve_level computes for a periodic
+ * root of n^3 cells (box side `box`, smoothing a = a_over_dx * box / n) with
+ * the two-point-difference optimal Green's function (APM_GRAD_FD2) and the
+ * FP32 path's default FFT stages (radices up to 16), in FP32, with every
+ * intermediate (twiddles, the Green's table, the FFT spectra, a status word)
+ * kept in one fixed 24 MiB device array that each GPU loading the library
+ * holds until the process exits.
  *  gmf       : device, n^3 int64 cell masses * 2^mass_frac_bits (x fastest)
  *  phi_short : device, (n+4)^3 floats, cells [-2, n+2) (periodic wrap)
  * n must be {2,3,5,7}-smooth with 4 <= n <= 128; larger or non-smooth n return
@@ -344,9 +358,13 @@ const char* apm_kernel_name(int32_t kernel);
  * The first call on a device looks up the array's device address and sets the
  * FFT kernels' shared-memory limit (host-side set-up, once per device, with that
  * device current); make that first call before any stream capture.
- * All calls share the one array: each call rebuilds everything it reads, but
+ * All calls share the one array, which keeps the last call's contents: each
+ * call rebuilds everything it reads and clears its status word first, but
  * calls whose work overlaps on the GPU (different streams, or different host
- * threads) race on it and must be serialised by the caller. */
+ * threads) race on it and must be serialised by the caller.
+ * There is no status reader: if the x-forward pass's bounded wait for its row
+ * copy runs out (about a second; not expected in normal operation), the whole
+ * phi_short window is filled with NaN instead of a partial result. */
 apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a_over_dx,
                                       int32_t mass_frac_bits, const int64_t* gmf,
                                       float* phi_short, void* stream);

@@ -67,6 +67,7 @@ SIGNATURES = {
                            c_dbl, c_void_p, c_void_p]),
     "apm_autotune_level": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p),
                                    ctypes.POINTER(c_void_p), c_void_p]),
+    "apm_set_grid_batching": (c_i32, [c_void_p, c_i32]),
     "apm_get_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
     "apm_set_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
     "apm_kick_drift": (c_i32, [c_void_p, c_i64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

@@ -56,6 +56,7 @@ struct PassPlan {
     int n = 0;
     size_t smem = 0;
     std::vector<int> lines;          // per grid of the level
+    std::vector<int> first;          // per grid: its first chunk (grid k: [first[k], first[k+1]))
 };
 
 struct Level {
@@ -68,6 +69,7 @@ struct Level {
     PassPlan pass[kFftPasses];
     Chunk* d_gas = nullptr; int n_gas = 0;
     Chunk* d_acc = nullptr; int n_acc = 0;
+    std::vector<int> acc_first;      // per grid: its first acceleration chunk (ng + 1 entries)
     // pointer tables (device) + pinned mirrors + last uploaded values
     int cap = 0;
     void** d_ptr = nullptr;          // kRoles * cap
@@ -98,6 +100,7 @@ struct apm_ctx {
     LevelDev* d_levels = nullptr;    // every level's LevelDev (the all-level kernels)
     void** d_tabs = nullptr;         // [role][level]: each level's device pointer table of the role
     Profiler prof;
+    bool batched = true;             // apm_set_grid_batching
 };
 
 namespace {
@@ -296,8 +299,10 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
     const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
     std::vector<Chunk> list;
     P.lines.assign(L.hg.size(), 0);
+    P.first.assign(L.hg.size() + 1, 0);
     P.smem = 0;
     for (int k = 0; k < (int)L.hg.size(); ++k) {
+        P.first[k] = (int)list.size();
         const GridDev& g = L.hg[k];
         const int len = (q == kPassXf || q == kPassXi) ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
         int lines = fft_pass_lines(q, len, budget, f64);
@@ -316,6 +321,7 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
                 for (int kt = 0; kt < nkt; ++kt) list.push_back({k, (kt << kColOtherBits) | o});
         }
     }
+    P.first[L.hg.size()] = (int)list.size();
     P.budget = budget;
     P.threads = threads;
     P.n = (int)list.size();
@@ -332,8 +338,9 @@ void apply_pass(Level& L, int q) {
 // comp: with the spectral gradient, the component (0 phi, 1-3 A_x..A_z) of
 // the z, y-inverse and x-inverse passes; the y inverse then writes wsC, so
 // the y-forward output in wsB stays for the next component's z pass.
+// grid >= 0: only that grid's chunks (one grid's launch of the pass)
 cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void** d_gmf, void** d_phis,
-                     cudaStream_t s, int comp = 0) {
+                     cudaStream_t s, int comp = 0, int grid = -1) {
     const bool f64 = c->cfg.precision == APM_FP64;
     FftArgs a;
     a.g = L.d_grids;
@@ -342,8 +349,8 @@ cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void*
     a.wsA = c->wsA;
     a.wsB = c->wsB;
     a.F = c->cfg.mass_frac_bits;
-    a.chunks = P.d;
-    a.n_chunks = P.n;
+    a.chunks = grid < 0 ? P.d : P.d + P.first[grid];
+    a.n_chunks = grid < 0 ? P.n : P.first[grid + 1] - P.first[grid];
     a.smem = P.smem;
     a.threads = P.threads;
     a.status = c->d_status;
@@ -718,7 +725,9 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
         const int ng = (int)L.grids.size();
         if ((st = upload(c, &L.d_grids, L.hg)) != APM_OK) return st;
         std::vector<Chunk> gas, acc;
+        L.acc_first.assign(ng + 1, 0);
         for (int k = 0; k < ng; ++k) {
+            L.acc_first[k] = (int)acc.size();
             const GridDev& g = L.hg[k];
             const long long grows = (long long)g.G[1] * g.G[2];
             for (long long t = 0; t < (grows + g.rows_gas - 1) / g.rows_gas; ++t) gas.push_back({k, (int)t});
@@ -726,6 +735,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
             for (long long t = 0; t < (nblocks + kAccBlocksPerCta - 1) / kAccBlocksPerCta; ++t)
                 acc.push_back({k, (int)t});
         }
+        L.acc_first[ng] = (int)acc.size();
         for (int q = 0; q < kFftPasses; ++q) {
             if ((st = build_pass(c, L, q, f64 ? kFftBudgetF64 : kFftBudgetF32, kFftThreads, f64, L.pass[q])) != APM_OK)
                 return st;
@@ -950,17 +960,28 @@ apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
     if ((st = set_ptrs(c, L, R_PHIS, (const void* const*)phi_short, ng, &d_phis, s)) != APM_OK) return st;
     const Kern kind[kFftPasses] = {K_XF, K_YF, K_Z, K_YI, K_XI};
     const int ncomp = c->cfg.gradient == APM_GRAD_SPECTRAL ? 4 : 1;
-    for (int q = 0; q < kFftPasses; ++q) {
-        Trace t(c, kind[q], s);
-        if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) return APM_E_CUDA;
-    }
-    // the spectral gradient's acceleration components: z (table times
-    // -i D_comp), y inverse and x inverse again on the kept forward transform
-    for (int comp = 1; comp < ncomp; ++comp)
-        for (int q = kPassZ; q < kFftPasses; ++q) {
+    // batched: each pass is one launch over every grid of the level; otherwise
+    // one launch sequence per grid, grid after grid
+    const int g_first = c->batched ? -1 : 0, g_last = c->batched ? -1 : ng - 1;
+    for (int gk = g_first; gk <= g_last; ++gk) {
+        for (int q = 0; q < kFftPasses; ++q) {
             Trace t(c, kind[q], s);
-            if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, comp) != cudaSuccess) return APM_E_CUDA;
+            if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, 0, gk) != cudaSuccess) return APM_E_CUDA;
         }
+        // the spectral gradient's acceleration components: z (table times
+        // -i D_comp), y inverse and x inverse again on the kept forward transform
+        for (int comp = 1; comp < ncomp; ++comp)
+            for (int q = kPassZ; q < kFftPasses; ++q) {
+                Trace t(c, kind[q], s);
+                if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, comp, gk) != cudaSuccess) return APM_E_CUDA;
+            }
+    }
+    return APM_OK;
+}
+
+apm_status apm_set_grid_batching(apm_ctx* c, int32_t batched) {
+    if (!c || (batched != 0 && batched != 1)) return APM_E_INVALID;
+    c->batched = batched == 1;
     return APM_OK;
 }
 
@@ -1116,22 +1137,29 @@ apm_status apm_accel(apm_ctx* c, int32_t level, const void* const* phi_short,
         if ((st = set_ptrs(c, L, R_PACC, parent_acc, np, &d_pacc, s)) != APM_OK) return st;
         pgrids = P.d_grids;
     }
-    Trace t(c, K_ACCEL, s);
     const int grad = c->cfg.gradient;
-    cudaError_t e;
-    if (grad == APM_GRAD_FD2)
-        e = c->cfg.precision == APM_FP64
-            ? launch_accel<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                                   (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s)
-            : launch_accel<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                                  (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, s);
-    else
-        e = c->cfg.precision == APM_FP64
-            ? launch_accel_var<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                                         (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, grad, s)
-            : launch_accel_var<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
-                                        (const void* const*)d_pacc, d_phi, d_acc, L.d_acc, L.n_acc, grad, s);
-    return cuda_status(e);
+    // batched: one launch over every grid; otherwise one launch per grid
+    const int g_first = c->batched ? -1 : 0, g_last = c->batched ? -1 : ng - 1;
+    for (int gk = g_first; gk <= g_last; ++gk) {
+        const Chunk* ch = gk < 0 ? L.d_acc : L.d_acc + L.acc_first[gk];
+        const int nch = gk < 0 ? L.n_acc : L.acc_first[gk + 1] - L.acc_first[gk];
+        Trace t(c, K_ACCEL, s);
+        cudaError_t e;
+        if (grad == APM_GRAD_FD2)
+            e = c->cfg.precision == APM_FP64
+                ? launch_accel<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                       (const void* const*)d_pacc, d_phi, d_acc, ch, nch, s)
+                : launch_accel<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                      (const void* const*)d_pacc, d_phi, d_acc, ch, nch, s);
+        else
+            e = c->cfg.precision == APM_FP64
+                ? launch_accel_var<double>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                             (const void* const*)d_pacc, d_phi, d_acc, ch, nch, grad, s)
+                : launch_accel_var<float>(L.dev, pgrids, (const void* const*)d_phis, (const void* const*)d_pphi,
+                                            (const void* const*)d_pacc, d_phi, d_acc, ch, nch, grad, s);
+        if (e != cudaSuccess) return APM_E_CUDA;
+    }
+    return APM_OK;
 }
 
 apm_status apm_interp(apm_ctx* c, int32_t level, const void* const* acc,

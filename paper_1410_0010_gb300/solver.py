@@ -186,6 +186,12 @@ class Solver:
                                        ptr_array([_ptr(t) for t in phis]), _stream_handle(stream)),
               "apm_autotune_level")
 
+    def set_grid_batching(self, batched):
+        """True (default): one launch per FFT pass (and for the accelerations)
+        over all grids of a level; False: one launch sequence per grid, the
+        plain per-grid baseline.  Results are bit-identical."""
+        check(lib().apm_set_grid_batching(self._ctx, 1 if batched else 0), "apm_set_grid_batching")
+
     def fft_shapes(self, level):
         sh = ApmFftShapes()
         check(lib().apm_get_fft_shapes(self._ctx, level, ctypes.byref(sh)), "apm_get_fft_shapes")

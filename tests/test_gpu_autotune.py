@@ -105,3 +105,38 @@ def test_cache_file_roundtrip(tmp_path):
     again = s2.autotune(P2, 1e-3, bufs2, cache=cache)
     assert again == first
     s2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("gradient", ["fd2", "spectral"])
+def test_per_grid_launches_give_identical_bits(precision, gradient):
+    """apm_set_grid_batching(0): the level solve and the accelerations run one
+    launch sequence per grid (the plain per-grid path) and must reproduce the
+    batched launches bit for bit."""
+    import torch
+
+    from paper_1410_0010_gb300.solver import Solver
+    s, P = _setup(precision)
+    s.close()
+    s = Solver(GRIDS, periodic=False, precision=precision, device=0, gradient=gradient)
+    bufs = s.alloc_all()
+    pacc = torch.zeros((3, P.n), dtype=s.dtype, device="cuda")
+    s.step(P, 1e-3, bufs, pacc)
+    ref, ref_pacc = _fields(bufs), pacc.clone()
+    s.set_grid_batching(False)
+    for b in bufs:
+        for t in b["phis"] + b["acc"]:
+            t.fill_(float("nan"))
+    pacc.fill_(float("nan"))
+    s.profile(True)
+    s.step(P, 1e-3, bufs, pacc)
+    prof = s.profile_read()
+    s.profile(False)
+    s.sync_status()
+    assert _same(_fields(bufs), ref)
+    assert torch.equal(pacc, ref_pacc)
+    # three refined grids: three x-forward launches on level 1, one on the root
+    assert prof["fft_x_fwd"][0] == 4
+    assert prof["accel_carry"][0] == 4
+    s.set_grid_batching(True)
+    s.close()
