@@ -1,15 +1,15 @@
 // apm_noalloc.cu -- apm_solve_periodic_noalloc: the potential solve of one
 // periodic root grid that allocates no memory at all.
 //
-// Some callers cannot call cudaMalloc: code that runs where the CUDA runtime
-// may not allocate (host callbacks enqueued with cudaLaunchHostFunc, regions
-// being captured into a CUDA graph with plain allocations), or applications
-// that hand the whole device to their own memory pool and must not see the
-// library grow its footprint.  This entry point needs no context and no
-// allocation: every intermediate it uses (twiddles, the Green's table, grid
-// descriptors and the two spectrum buffers of the FFT passes) lives in one
-// fixed, file-scope device array, kScratchBytes large, that every GPU which
-// loads the library holds until the process exits.
+// Some callers cannot call cudaMalloc: applications that give the whole device
+// to their own memory pool at start-up, so that a library allocating behind
+// their back would fail or break the pool's accounting, and loops that must
+// not stall on the device-wide synchronisation cudaFree implies.  This entry
+// point needs no context and no allocation: every intermediate it uses
+// (twiddles, the Green's table, grid descriptors, a status word and the two
+// spectrum buffers of the FFT passes) lives in one fixed, file-scope device
+// array, kScratchBytes large, that every GPU which loads the library holds
+// until the process exits.
 #include <algorithm>
 #include <cstring>
 
@@ -33,19 +33,31 @@ void* g_scratch_addr[kMaxDevices] = {};
 // {grid 0, tile i} into the scratch
 // row chunks {0, i}; column chunks {0, (kt << kColOtherBits) | other} for
 // i = other * nkt + kt
+// (and clears the status word the x-forward pass's bounded wait reports to)
 __global__ void k_noalloc_setup(GridDev g, GridDev* dst, Chunk* chunks, Chunk* cchunks, int n, int nkt,
-                                const int64_t** in_tab, const int64_t* in, void** out_tab, void* out) {
+                                const int64_t** in_tab, const int64_t* in, void** out_tab, void* out,
+                                unsigned* status) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *dst = g;
         *in_tab = in;
         *out_tab = out;
+        *status = 0u;
     }
     if (i < n) {
         chunks[i] = Chunk{0, i};
         const int other = i / nkt, kt = i - other * nkt;
         cchunks[i] = Chunk{0, (kt << kColOtherBits) | other};
     }
+}
+
+// There is no status reader for this entry point, so a wait that ran out must
+// show in the output itself: if the status word is set, the whole window is
+// overwritten with NaN.  One CTA; it reads one word and returns when it is 0.
+__global__ void k_noalloc_finish(const unsigned* status, float* out, long long count) {
+    if (*status == 0u) return;
+    const float nan = __int_as_float(0x7fc00000);
+    for (long long i = threadIdx.x; i < count; i += blockDim.x) out[i] = nan;
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -112,6 +124,8 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     size_t off = 0;
     GridDev* d_g = reinterpret_cast<GridDev*>(base + off);
     off = align256(off + sizeof(GridDev));
+    unsigned* d_status = reinterpret_cast<unsigned*>(base + off);
+    off = align256(off + sizeof(unsigned));
     Chunk* d_chunks = reinterpret_cast<Chunk*>(base + off);
     off = align256(off + kMaxChunks * sizeof(Chunk));
     Chunk* d_cchunks = reinterpret_cast<Chunk*>(base + off);
@@ -149,9 +163,10 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     const int64_t** d_in = reinterpret_cast<const int64_t**>(d_chunks + (kMaxChunks - 2));
     void** d_out = reinterpret_cast<void**>(d_chunks + (kMaxChunks - 1));
 
-    // every call rebuilds what it reads: nothing depends on the previous call
+    // every call rebuilds what it reads (and clears the status word): nothing
+    // depends on the previous call
     k_noalloc_setup<<<(n_max + 255) / 256, 256, 0, s>>>(g, d_g, d_chunks, d_cchunks, n_max, nky, d_in, gmf,
-                                                        d_out, phi_short);
+                                                        d_out, phi_short, d_status);
     if (cudaGetLastError() != cudaSuccess) return APM_E_CUDA;
     if (launch_twiddles(tw64, tw32, n, s) != cudaSuccess) return APM_E_CUDA;
     const int M[3] = {n, n, n};
@@ -168,7 +183,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     a.wsB = wsB;
     a.F = mass_frac_bits;
     a.threads = kFftThreads;
-    a.status = nullptr;   // a wait that runs out leaves the output unfinished, unreported
+    a.status = d_status;  // read by k_noalloc_finish after the last pass
     const size_t smem_rows = fft_pass_smem(kPassXf, n, g.lines[kPassXf], sizeof(float2), n);
     const size_t smem_cols = fft_pass_smem(kPassYf, n, g.lines[kPassYf], sizeof(float2));
     a.n_chunks = n_xf;
@@ -186,5 +201,7 @@ extern "C" apm_status apm_solve_periodic_noalloc(int32_t n, double box, double a
     a.n_chunks = n_xi;
     a.smem = smem_rows;
     if (launch_fft_xi<float>(a, d_out, s) != cudaSuccess) return APM_E_CUDA;
+    k_noalloc_finish<<<1, 256, 0, s>>>(d_status, phi_short, (long long)(n + 4) * (n + 4) * (n + 4));
+    if (cudaGetLastError() != cudaSuccess) return APM_E_CUDA;
     return APM_OK;
 }
