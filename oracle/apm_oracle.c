@@ -230,9 +230,61 @@ static int degenerate(const int64_t kap[3], const int64_t M[3]) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Textbook FFT of one line (used instead of the naive sum when the oracle's  */
+/* transform mode is 1): recursive decimation-in-time Cooley-Tukey.  A length */
+/* n = p m with p its smallest prime factor is split into the p subsequences  */
+/* x[r + p j] (j < m), each transformed recursively, and combined as          */
+/*   X[k + q m] = sum_r w_n^(r (k + q m)) Y_r[k],  k < m, q < p,             */
+/* with w_n = exp(sign 2 pi i / n).  Every root is taken from the table of    */
+/* the full line length L (w_n^t = w_L^(t L/n)) at the exact integer index    */
+/* (t L/n) mod L.  x: input at stride `stride`; y: output (n values); t:      */
+/* scratch (n values).                                                        */
+/* ------------------------------------------------------------------------ */
+static int64_t smallest_prime_factor(int64_t n) {
+    for (int64_t p = 2; p * p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+static void fft_rec(const double* xr, const double* xi, int64_t stride, int64_t n, double* yr, double* yi,
+                    double* tr, double* ti, int64_t L, const double* wr, const double* wi) {
+    if (n == 1) {
+        yr[0] = xr[0];
+        yi[0] = xi[0];
+        return;
+    }
+    int64_t p = smallest_prime_factor(n), m = n / p;
+    /* sub-transforms Y_r into t[r m .. r m + m), with y[r m ..] as their scratch */
+    for (int64_t r = 0; r < p; ++r)
+        fft_rec(xr + r * stride, xi + r * stride, stride * p, m, tr + r * m, ti + r * m, yr + r * m,
+                yi + r * m, L, wr, wi);
+    int64_t scale = L / n;
+    for (int64_t q = 0; q < p; ++q)
+        for (int64_t k = 0; k < m; ++k) {
+            int64_t kk = k + q * m;
+            double sr = 0.0, si = 0.0;
+            for (int64_t r = 0; r < p; ++r) {
+                int64_t t = ((r * kk) % n) * scale;   /* exact index of w_n^(r kk) in the L table */
+                double ar = tr[r * m + k], ai = ti[r * m + k];
+                sr += ar * wr[t] - ai * wi[t];
+                si += ar * wi[t] + ai * wr[t];
+            }
+            yr[kk] = sr;
+            yi[kk] = si;
+        }
+}
+
+/* transform of the oracle's separable 3-D routines: 0 the naive sum (default), */
+/* 1 the textbook FFT above; both compute the same unnormalised DFT            */
+static int orc_transform_mode = 0;
+void orc_set_transform(int mode) { orc_transform_mode = mode; }
+int orc_get_transform(void) { return orc_transform_mode; }
+
+/* ------------------------------------------------------------------------ */
 /* Separable naive DFT of a complex M0 x M1 x M2 array (x fastest):           */
 /* out[kappa] = sum_j in[j] exp(sign 2 pi i kappa j / M), twiddles indexed by */
-/* the exact integer (kappa*j) mod M.  No normalisation.                      */
+/* the exact integer (kappa*j) mod M.  No normalisation.  With transform      */
+/* mode 1 each line goes through fft_rec instead (same result, O(M log M)).   */
 /* ------------------------------------------------------------------------ */
 static void dft_axis(double* re, double* im, const int64_t M[3], int axis, int sign) {
     int64_t L = M[axis];
@@ -246,10 +298,15 @@ static void dft_axis(double* re, double* im, const int64_t M[3], int axis, int s
         wr[t] = cos(2.0 * ORC_PI * (double)t / (double)L);
         wi[t] = (double)sign * sin(2.0 * ORC_PI * (double)t / (double)L);
     }
+    const int fft = orc_transform_mode == 1;
 #pragma omp parallel
     {
         double* lr = (double*)malloc(sizeof(double) * L);
         double* li = (double*)malloc(sizeof(double) * L);
+        double* yr = (double*)malloc(sizeof(double) * L);
+        double* yi = (double*)malloc(sizeof(double) * L);
+        double* sr_ = (double*)malloc(sizeof(double) * L);
+        double* si_ = (double*)malloc(sizeof(double) * L);
 #pragma omp for schedule(static)
         for (int64_t line = 0; line < nlines; ++line) {
             /* base index of this line: decompose line into the other two axes */
@@ -258,6 +315,14 @@ static void dft_axis(double* re, double* im, const int64_t M[3], int axis, int s
             for (int64_t j = 0; j < L; ++j) {
                 lr[j] = re[base + j * stride];
                 li[j] = im[base + j * stride];
+            }
+            if (fft) {
+                fft_rec(lr, li, 1, L, yr, yi, sr_, si_, L, wr, wi);
+                for (int64_t kk = 0; kk < L; ++kk) {
+                    re[base + kk * stride] = yr[kk];
+                    im[base + kk * stride] = yi[kk];
+                }
+                continue;
             }
             for (int64_t kk = 0; kk < L; ++kk) {
                 double sr = 0.0, si = 0.0;
@@ -272,6 +337,10 @@ static void dft_axis(double* re, double* im, const int64_t M[3], int axis, int s
         }
         free(lr);
         free(li);
+        free(yr);
+        free(yi);
+        free(sr_);
+        free(si_);
     }
     free(wr);
     free(wi);

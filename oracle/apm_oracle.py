@@ -47,6 +47,10 @@ def lib():
         L.orc_grad_d.argtypes = [ci, i64, i64, d]
         L.orc_dft3.restype = None
         L.orc_dft3.argtypes = [P, P, P, ci, ci]
+        L.orc_set_transform.restype = None
+        L.orc_set_transform.argtypes = [ci]
+        L.orc_get_transform.restype = ci
+        L.orc_get_transform.argtypes = []
         L.orc_green_table.restype = None
         L.orc_green_table.argtypes = [ci, P, d, d, d, ci, ci, P, ci]
         L.orc_drift.restype = d
@@ -123,6 +127,16 @@ def green_opt(kappa, M, delta, a_lev, a_par, use_parent, gradient="fd2"):
     m = _i64(M)
     return lib().orc_green_opt(_p(k), _p(m), float(delta), float(a_lev), float(a_par),
                                int(use_parent), GRADIENTS[gradient])
+
+
+def set_transform(mode):
+    """The transform of every separable 3-D DFT in the oracle: "dft" (the naive
+    sum, default) or "fft" (the textbook mixed-radix FFT, the same unnormalised
+    DFT in O(M log M), for the benchmark-size grids).  Returns the previous
+    mode."""
+    prev = "fft" if lib().orc_get_transform() == 1 else "dft"
+    lib().orc_set_transform(1 if mode == "fft" else 0)
+    return prev
 
 
 def dft3(re, im, sign):

@@ -6,11 +6,18 @@
 * 512 batched subgrids of one level with gas: every grid on the GPU, a sample
   of grids (GMF bit-exact, potential, accelerations) against the oracle, for
   every gradient operator;
+  The sampled grids' particle accelerations against the oracle's
+  interpolation of its own accelerations;
 * periodic 512^3 root + 2 x 64 subgrids of 128^3, 16.8M particles: root GMF
-  bit-exact against the oracle's full deposit; the root potential mode by mode
-  (DFT of the GPU output at sampled modes against T(kappa) DFT(mass)(kappa) with
-  the oracle's Green's function); two 128^3 subgrids solved fully by the oracle;
-  FD, parent carry and particle interpolation on samples.
+  bit-exact against the oracle's full deposit; the whole 512^3 root potential,
+  element by element, against the oracle's solve in its textbook-FFT mode; the
+  root potential mode by mode; two 128^3 subgrids solved fully by the oracle;
+  the chain root -> level 1 -> level 2 through the oracle's own carry on the
+  level-2 grid holding the most particles, its level-1 parent and that
+  parent's 64^3 footprint on the root, with the particle accelerations they
+  own; FD, parent carry and particle interpolation on samples;
+* the periodic 128^3 + three levels hierarchy in FP64 against the oracle at
+  the FP64 tolerance.
 """
 import numpy as np
 import pytest
@@ -21,12 +28,34 @@ from gpu_helpers import TOL, compare, rel_l2, run_gpu, run_oracle
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-@pytest.mark.parametrize("gradient", ["fd2", "fd4", "spectral"])
-def test_plummer_periodic_three_levels_full(gradient):
+@pytest.fixture(scope="module")
+def plummer():
     w = W.config_plummer()
-    ref = run_oracle(w.grids, w.particles, w.half_dt, periodic=True, gradient=gradient)
+    return w, {}
+
+
+def _plummer_ref(plummer, gradient):
+    w, cache = plummer
+    if gradient not in cache:
+        cache[gradient] = run_oracle(w.grids, w.particles, w.half_dt, periodic=True, gradient=gradient)
+    return cache[gradient]
+
+
+@pytest.mark.parametrize("gradient", ["fd2", "fd4", "spectral"])
+def test_plummer_periodic_three_levels_full(plummer, gradient):
+    w, _ = plummer
+    ref = _plummer_ref(plummer, gradient)
     gpu = run_gpu(w.grids, w.particles, w.half_dt, periodic=True, precision="fp32", gradient=gradient)
     compare(gpu, ref, "fp32")
+
+
+def test_plummer_periodic_three_levels_full_fp64(plummer):
+    """The FP64 GPU path at a benchmark size: every grid's GMF bit-exact and
+    every field and particle acceleration within 1e-12 of the oracle."""
+    w, _ = plummer
+    ref = _plummer_ref(plummer, "fd2")
+    gpu = run_gpu(w.grids, w.particles, w.half_dt, periodic=True, precision="fp64")
+    compare(gpu, ref, "fp64")
 
 
 @pytest.mark.parametrize("gradient", ["fd2", "spectral"])
@@ -44,6 +73,7 @@ def test_batched_level_sampled_grids(gradient):
     grids = [oracle.Grid(*g) for g in w.grids]
     rng = np.random.default_rng(40)
     sample = sorted(rng.choice(np.arange(1, len(grids)), size=6, replace=False).tolist())
+    own = oracle.owners(cfg, grids, w.particles, w.half_dt) if gradient == "fd2" else None
     for gi in sample:
         gmf, st = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt, gas=w.gas[gi])
         assert np.array_equal(gpu["gmf"][gi], gmf), gi
@@ -56,6 +86,16 @@ def test_batched_level_sampled_grids(gradient):
         phi, acc = oracle.accel(cfg, grids, gi, phis)
         assert rel_l2(gpu["phi"][gi], phi) <= TOL["fp32"]["phi"], gi
         assert rel_l2(gpu["acc"][gi], acc) <= TOL["fp32"]["acc"], gi
+        if gradient != "fd2":
+            continue
+        # the particles this grid owns: the oracle's interpolation of its own
+        # accelerations against the GPU's particle accelerations
+        sel = own == gi
+        assert sel.sum() >= 2000, gi
+        parts = {k: v[sel] for k, v in w.particles.items()}
+        out = np.zeros((3, int(sel.sum())))
+        oracle.interp(cfg, grids, gi, acc, parts, w.half_dt, own[sel], out)
+        assert rel_l2(gpu["pacc"][:, sel], out) <= TOL["fp32"]["pacc"], gi
 
 
 def test_four_point_isolated_root_over_511_cells_is_refused():
@@ -87,7 +127,26 @@ def cosmo():
     s.step(P, w.half_dt, bufs, pacc)
     s.sync_status()
     l1 = s.level_grids[1][:2]
+    # the chain: the level-2 grid whose interior holds the most particles (the
+    # workload's own positions), and its level-1 parent
+    pos = np.stack([w.particles[k] for k in ("x", "y", "z")])
+    l2_ids = s.level_grids[2]
+    counts = []
+    for gi in l2_ids:
+        _, _, start, dims = w.grids[gi]
+        d2 = 1.0 / (w.grids[0].dims[0] * 4)
+        lo = np.array(start)[:, None] * d2
+        hi = lo + np.array(dims)[:, None] * d2
+        counts.append(int(np.all((pos >= lo) & (pos < hi), axis=0).sum()))
+    g2 = l2_ids[int(np.argmax(counts))]
+    g1 = w.grids[g2][1]
+
+    def grab(lev, gi):
+        k = s.info[gi]["level_index"]
+        return {key: bufs[lev][key][k].cpu().numpy() for key in ("gmf", "phis", "phi", "acc")}
+
     out = dict(w=w, solver=s, root_gmf=bufs[0]["gmf"][0].cpu().numpy(),
+               chain=(g1, g2), chain_l1=grab(1, g1), chain_l2=grab(2, g2),
                root_phis=bufs[0]["phis"][0].cpu().numpy(),
                root_phi=bufs[0]["phi"][0].cpu().numpy(), root_acc=bufs[0]["acc"][0].cpu().numpy(),
                l1_ids=l1, l1={k: {key: bufs[1][key][s.info[gi]["level_index"]].cpu().numpy()
@@ -105,6 +164,77 @@ def test_cosmo_root_mass_field_bit_exact(cosmo):
     gmf, st = oracle.deposit(cfg, [oracle.Grid(*g) for g in w.grids], 0, w.particles, w.half_dt)
     assert st == 0
     assert np.array_equal(cosmo["root_gmf"], gmf)
+
+
+def _root_oracle(cosmo):
+    """The oracle's root potential (textbook-FFT mode) and its own FD fields."""
+    import oracle
+    if "root_ref" not in cosmo:
+        w = cosmo["w"]
+        cfg = oracle.Config(periodic=True, mass_frac_bits=w.mass_frac_bits)
+        grids = [oracle.Grid(*g) for g in w.grids]
+        gmf, st = oracle.deposit(cfg, grids, 0, w.particles, w.half_dt)
+        assert st == 0
+        prev = oracle.set_transform("fft")
+        try:
+            phis = oracle.solve(cfg, grids, 0, gmf)
+        finally:
+            oracle.set_transform(prev)
+        phi, acc = oracle.accel(cfg, grids, 0, phis)
+        cosmo["root_ref"] = (phis, phi, acc)
+    return cosmo["root_ref"]
+
+
+def test_cosmo_root_potential_element_by_element(cosmo):
+    """The whole 512^3 root: phi_short, phi and the accelerations against the
+    oracle's chain (its own deposit, FFT-mode solve and FD), every cell."""
+    phis, phi, acc = _root_oracle(cosmo)
+    assert rel_l2(cosmo["root_phis"], phis) <= TOL["fp32"]["phis"]
+    assert rel_l2(cosmo["root_phi"], phi) <= TOL["fp32"]["phi"]
+    assert rel_l2(cosmo["root_acc"], acc) <= TOL["fp32"]["acc"]
+
+
+def test_cosmo_chain_root_level1_level2(cosmo):
+    """The oracle's whole chain on the level-2 grid holding the most particles,
+    its level-1 parent and that parent's 64^3 footprint on the root: deposit,
+    solve, FD and the carry of the oracle's own parent fields, element by
+    element, then the particle accelerations these grids own."""
+    import oracle
+    w = cosmo["w"]
+    cfg = oracle.Config(periodic=True, mass_frac_bits=w.mass_frac_bits)
+    grids = [oracle.Grid(*g) for g in w.grids]
+    _, phi0, acc0 = _root_oracle(cosmo)
+    g1, g2 = cosmo["chain"]
+    # the parent's footprint on the root: cells [s/2 - 1, (s + N)/2 + 1) of the
+    # root window [-1, N0 + 1)
+    _, _, start1, dims1 = w.grids[g1]
+    sl = tuple(slice(start1[j] // 2, (start1[j] + dims1[j]) // 2 + 2) for j in (2, 1, 0))
+    assert rel_l2(cosmo["root_phi"][sl], phi0[sl]) <= TOL["fp32"]["phi"]
+    assert rel_l2(cosmo["root_acc"][(slice(None),) + sl], acc0[(slice(None),) + sl]) <= TOL["fp32"]["acc"]
+    fields = {}
+    parent = (phi0, acc0)
+    prev = oracle.set_transform("fft")
+    try:
+        for gi, got in ((g1, cosmo["chain_l1"]), (g2, cosmo["chain_l2"])):
+            gmf, st = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt)
+            assert np.array_equal(got["gmf"], gmf), gi
+            phis = oracle.solve(cfg, grids, gi, gmf)
+            phi, acc = oracle.accel(cfg, grids, gi, phis, parent[0], parent[1])
+            assert rel_l2(got["phis"], phis) <= TOL["fp32"]["phis"], gi
+            assert rel_l2(got["phi"], phi) <= TOL["fp32"]["phi"], gi
+            assert rel_l2(got["acc"], acc) <= TOL["fp32"]["acc"], gi
+            fields[gi] = acc
+            parent = (phi, acc)
+    finally:
+        oracle.set_transform(prev)
+    own = oracle.owners(cfg, grids, w.particles, w.half_dt)
+    for gi in (g1, g2):
+        sel = own == gi
+        assert sel.sum() > 1000, gi
+        parts = {k: v[sel] for k, v in w.particles.items()}
+        out = np.zeros((3, int(sel.sum())))
+        oracle.interp(cfg, grids, gi, fields[gi], parts, w.half_dt, own[sel], out)
+        assert rel_l2(cosmo["pacc"][:, sel], out) <= TOL["fp32"]["pacc"], gi
 
 
 def test_cosmo_root_potential_mode_by_mode(cosmo):

@@ -103,3 +103,45 @@ def test_isolated_root_table_is_transform_of_real_space_kernel(oracle_mod):
     ref = np.fft.fftn(g).real
     T = oracle_mod.full_table(cfg, plan)
     assert np.max(np.abs(T - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("shape", [(6, 10, 15), (8, 9, 7), (150, 2, 3), (64, 4, 5), (1, 49, 12), (11, 13, 2)])
+def test_textbook_fft_mode_equals_naive_dft(shape, oracle_mod):
+    oracle = oracle_mod
+    """The oracle's textbook FFT mode (recursive Cooley-Tukey by smallest prime
+    factor) computes the same unnormalised DFT as its naive sum, forward and
+    inverse, on smooth and prime lengths (shape given as (x, y, z))."""
+    rng = np.random.default_rng(sum(shape))
+    re = rng.normal(size=shape[::-1])
+    im = rng.normal(size=shape[::-1])
+    prev = oracle.set_transform("dft")
+    try:
+        for sign in (-1, 1):
+            ar, ai = oracle.dft3(re, im, sign)
+            oracle.set_transform("fft")
+            br, bi = oracle.dft3(re, im, sign)
+            oracle.set_transform("dft")
+            a = ar + 1j * ai
+            b = br + 1j * bi
+            assert np.linalg.norm(b - a) <= 1e-13 * np.linalg.norm(a)
+            ref = np.fft.fftn(re + 1j * im) if sign < 0 else np.fft.ifftn(re + 1j * im) * re.size
+            assert np.linalg.norm(b - ref) <= 1e-13 * np.linalg.norm(ref)
+    finally:
+        oracle.set_transform(prev)
+
+
+def test_textbook_fft_mode_solve_matches_naive_solve(oracle_mod):
+    oracle = oracle_mod
+    """A periodic-root solve through the FFT mode equals the naive-DFT solve."""
+    n = 24
+    cfg = oracle.Config(periodic=True)
+    grids = [oracle.Grid(0, -1, (0, 0, 0), (n, n, n))]
+    gmf = np.random.default_rng(5).integers(0, 1 << 40, size=(n, n, n))
+    prev = oracle.set_transform("dft")
+    try:
+        a = oracle.solve(cfg, grids, 0, gmf)
+        oracle.set_transform("fft")
+        b = oracle.solve(cfg, grids, 0, gmf)
+    finally:
+        oracle.set_transform(prev)
+    assert np.linalg.norm(b - a) <= 1e-13 * np.linalg.norm(a)
