@@ -29,6 +29,7 @@ class Workload:
     half_dt: float = 0.0
     mass_frac_bits: int = 52
     solve_levels: list = None      # levels that are solved (None: all)
+    spatial_order: bool = False    # the particles are stored in spatial order (a lattice)
     notes: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -336,7 +337,7 @@ def config_cosmo512(seed=5, root_n=512, lattice=256, n_sub=64, sub_n=128):
         best = int(np.argmax(cnt))
         st = _centred_child(ctr[:, best], sub_n, pst, pdm)
         grids.append(GridDesc(2, gi, st, (sub_n,) * 3))
-    return Workload(NAMES["c5"], True, grids, parts, half_dt=5e-4,
+    return Workload(NAMES["c5"], True, grids, parts, half_dt=5e-4, spatial_order=True,
                     notes="Zel'dovich lattice, P(k) ~ k^-2, v = 10 psi")
 
 

@@ -257,27 +257,92 @@ apm_status apm_accel(apm_ctx* ctx, int32_t level, const void* const* phi_short,
  * APM_E_INVALID for a value other than 0 or 1. */
 apm_status apm_set_grid_batching(apm_ctx* ctx, int32_t batched);
 
-/* Launch shapes of the five FFT passes of one level (x forward, y forward, z
- * with the table, y inverse, x inverse), in that order.  budget[p] is the
- * number of complex elements one shared-memory buffer of a pass CTA aims at:
- * each grid batches pow2_floor(budget / M) lines per CTA (1..32 row pairs for
- * the x passes, 4..32 kx columns for the y/z passes, 2..32 in FP64), halved
- * while the CTA needs more than 200 KB of shared memory.  threads[p] is the
- * CTA size, 128 or 256.  The defaults are budget 2048
- * (FP32) / 1024 (FP64) and 256 threads.  A shape only regroups whole lines, so
- * it never changes a result, bit for bit.  The paper has no counterpart: this
- * is a property of the GPU launch, not of the method. */
+/* CUDA graphs of call sequences, owned by the context.  The paper has no
+ * counterpart: replaying a recorded launch sequence removes the host cost of
+ * each launch, which is what lets a level of many uneven grids (one work list
+ * per pass, several segments) run as one replayed sequence.
+ * apm_graph_begin starts capturing the work issued to `stream` (a stream the
+ * caller created; the legacy default stream cannot be captured): this
+ * library's calls and anything else the caller enqueues there.
+ * apm_graph_end ends the capture, instantiates it and returns its id;
+ * apm_graph_launch replays it on a stream; apm_graph_destroy frees it.
+ * A replay repeats every captured launch with the same arguments, on the same
+ * device buffers, so their contents at replay time are what it reads.  Make
+ * the sequence's calls once outside capture first (its pointer tables are then
+ * uploaded), and capture no call that synchronises (apm_sync_status,
+ * apm_autotune_level, apm_set_fft_shapes, apm_reserve_order): the capture
+ * then fails and apm_graph_end returns APM_E_STATE.  apm_set_hierarchy and
+ * apm_destroy free every graph.  APM_E_STATE from apm_graph_begin without a
+ * hierarchy or while `stream` is already capturing; APM_E_INVALID for a NULL
+ * stream or an unknown id. */
+apm_status apm_graph_begin(apm_ctx* ctx, void* stream);
+apm_status apm_graph_end(apm_ctx* ctx, void* stream, int32_t* graph_id);
+apm_status apm_graph_launch(apm_ctx* ctx, int32_t graph_id, void* stream);
+apm_status apm_graph_destroy(apm_ctx* ctx, int32_t graph_id);
+
+/* Particle processing order.  The paper has no counterpart: this is a property
+ * of the GPU launch, not of the method.  The interpolation kernels run one
+ * thread per particle; when consecutive particles are far apart in space, a
+ * warp's 27-cell gathers touch as many cache lines as it has particles.
+ * apm_order_particles sorts the particle indices by a root-level bin of their
+ * drifted positions (cubes of 4 or more root cells, at most 128^3 bins; a
+ * counting sort: one pass computing bins and ranks with atomics, a scan of
+ * the bin counts, one scatter), and every later interpolation call
+ * (apm_interp, apm_interp_all) on the same number of particles visits them in
+ * that order.  The deposits keep the caller's order: in bin order neighbouring
+ * threads add into the same cells and their reductions serialise.  The order
+ * never changes a result: each particle is interpolated on its own, so every
+ * output is bit-identical with or without it, and with an order computed
+ * from other positions (after a kick-drift, say) the results stay exact, only
+ * less coherent in memory.
+ *
+ * apm_reserve_order allocates the workspace for up to n_max particles (16 bytes
+ * per particle plus the bin counts; a set-up call that synchronises the
+ * device), or frees it and turns the ordering off for n_max = 0.
+ * apm_set_hierarchy frees it too.  APM_E_STATE without a hierarchy.
+ * apm_order_particles: APM_E_INVALID when no workspace is reserved or n is
+ * above n_max; asynchronous on `stream`. */
+apm_status apm_reserve_order(apm_ctx* ctx, int64_t n_max);
+apm_status apm_order_particles(apm_ctx* ctx, const apm_particles* particles, double half_dt, void* stream);
+
+/* Launch shapes and plan choices of the five FFT passes of one level (x
+ * forward, y forward, z with the table, y inverse, x inverse), in that order.
+ *  budget[p]  the number of complex elements one shared-memory buffer of a
+ *             runtime-planned pass CTA aims at: each grid batches
+ *             pow2_floor(budget / M) lines per CTA (1..32 row pairs for the x
+ *             passes, 4..32 kx columns for the y/z passes, 2..32 in FP64),
+ *             halved while the CTA needs more than 200 KB of shared memory;
+ *  threads[p] the runtime-planned pass's CTA size, 128 or 256;
+ *  plan[p]    0: FP32 grids whose length has a compile-time plan (every
+ *             {2,3,5,7}-smooth length from 36 to 84, and 128, 150, 256, 512)
+ *             run the kernel specialised for it (16 lines per CTA; not the x
+ *             inverse, nor the spectral gradient's z pass); 1: every grid runs
+ *             the runtime-planned kernel;
+ *  max_radix  the largest stage radix of the runtime plans: 16 (FP32
+ *             default; composite radices in registers) or 8 (FP64: always 8);
+ *  packing    0: the grids of a level enter each work list in hierarchy order;
+ *             1: largest transform first.
+ * The defaults are budget 2048 (FP32) / 1024 (FP64), 256 threads, plan 0,
+ * max_radix 16 (FP32) and packing 0.  budget, threads and packing only
+ * regroup or reorder whole lines, so they never change a result, bit for bit;
+ * plan and max_radix change the order of the butterflies' roundings (results
+ * stay within the FP32 parity tolerances).  The paper has no counterpart:
+ * these are properties of the GPU launch, not of the method. */
 typedef struct {
     int32_t budget[5];
     int32_t threads[5];
+    int32_t plan[5];
+    int32_t max_radix;
+    int32_t packing;
 } apm_fft_shapes;
 
 /* Autotuner: solves `level` like apm_solve_level (same arguments and outputs)
  * while timing every candidate shape of each FFT pass in turn (budgets
  * 512..8192 (FP32) or 256..4096 (FP64) by powers of two, 128 or 256 threads;
  * the fastest of five timed launches after a warm one, CUDA events on
- * `stream`), and
- * keeps the fastest shape per pass for the context's later calls.  phi_short
+ * `stream`), then, over the whole level's passes, each pass's plan (FP32),
+ * the packing and the runtime plans' largest radix (FP32), one at a time, and
+ * keeps the fastest choices for the context's later calls.  phi_short
  * holds the level's potential on return.  Synchronises `stream` and the
  * device several times: APM_E_STATE while `stream` is being captured. */
 apm_status apm_autotune_level(apm_ctx* ctx, int32_t level, const int64_t* const* gmf,
@@ -285,7 +350,8 @@ apm_status apm_autotune_level(apm_ctx* ctx, int32_t level, const int64_t* const*
 
 /* The shapes in use for `level`, and setting them (for instance from a cache
  * of earlier autotuner results).  apm_set_fft_shapes synchronises the device;
- * APM_E_INVALID for a budget < 1 or a thread count outside the rule above. */
+ * APM_E_INVALID for a budget < 1, a thread count, plan, packing or max_radix
+ * outside the rules above (FP64: max_radix 8). */
 apm_status apm_get_fft_shapes(const apm_ctx* ctx, int32_t level, apm_fft_shapes* out);
 apm_status apm_set_fft_shapes(apm_ctx* ctx, int32_t level, const apm_fft_shapes* shapes);
 

@@ -40,7 +40,8 @@ class ApmGridInfo(ctypes.Structure):
 
 
 class ApmFftShapes(ctypes.Structure):
-    _fields_ = [("budget", c_i32 * 5), ("threads", c_i32 * 5)]
+    _fields_ = [("budget", c_i32 * 5), ("threads", c_i32 * 5), ("plan", c_i32 * 5),
+                ("max_radix", c_i32), ("packing", c_i32)]
 
 
 # name -> (restype, argtypes); every function declared in include/apm.h
@@ -68,6 +69,12 @@ SIGNATURES = {
     "apm_autotune_level": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p),
                                    ctypes.POINTER(c_void_p), c_void_p]),
     "apm_set_grid_batching": (c_i32, [c_void_p, c_i32]),
+    "apm_reserve_order": (c_i32, [c_void_p, c_i64]),
+    "apm_graph_begin": (c_i32, [c_void_p, c_void_p]),
+    "apm_graph_end": (c_i32, [c_void_p, c_void_p, ctypes.POINTER(c_i32)]),
+    "apm_graph_launch": (c_i32, [c_void_p, c_i32, c_void_p]),
+    "apm_graph_destroy": (c_i32, [c_void_p, c_i32]),
+    "apm_order_particles": (c_i32, [c_void_p, ctypes.POINTER(ApmParticles), c_dbl, c_void_p]),
     "apm_get_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
     "apm_set_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
     "apm_kick_drift": (c_i32, [c_void_p, c_i64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

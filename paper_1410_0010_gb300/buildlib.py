@@ -19,13 +19,14 @@ LIB = os.path.join(OUT_DIR, "libapm.so")
 BOUNDS_DIR = os.path.join(HERE, "_build_bounds")
 
 # (source, object, extra flags): k_fft_col.cu is compiled once per precision
-# and column pass
+# and column pass, k_fft_fast.cu once per pass
 SOURCES = [("apm_api.cu", "apm_api.o", []), ("k_green.cu", "k_green.o", []),
            ("k_deposit.cu", "k_deposit.o", []), ("k_fft_x.cu", "k_fft_x.o", []),
            ("k_field.cu", "k_field.o", []), ("k_evolve.cu", "k_evolve.o", []),
-           ("apm_noalloc.cu", "apm_noalloc.o", [])] + [
+           ("apm_noalloc.cu", "apm_noalloc.o", []), ("k_order.cu", "k_order.o", [])] + [
     ("k_fft_col.cu", f"k_fft_col_{p}_{m}.o", [f"-DAPM_COL_FP64={1 if p == 'f64' else 0}", f"-DAPM_COL_MODE={m}"])
-    for p in ("f32", "f64") for m in (0, 1, 2, 3)]
+    for p in ("f32", "f64") for m in (0, 1, 2, 3)] + [
+    ("k_fft_fast.cu", f"k_fft_fast_{m}.o", [f"-DAPM_FAST_MODE={m}"]) for m in (0, 1, 2, 3)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
           "--expt-relaxed-constexpr"]
@@ -79,6 +80,22 @@ def build(force=False, verbose=False, extra=(), out_dir=OUT_DIR):
         run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, lib_path)
     return lib_path
+
+
+def build_probe(force=False):
+    """The compute-peak probe (csrc/peak_probe.cu), a standalone program that
+    prints the measured FP32/FP64/INT32 and reduction rates as JSON; bench.py
+    --probe-peaks runs it."""
+    src = os.path.join(CSRC, "peak_probe.cu")
+    exe = os.path.join(OUT_DIR, "peak_probe")
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if force or _stale(exe, [src]):
+        r = subprocess.run([nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", exe + ".tmp"],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        os.replace(exe + ".tmp", exe)
+    return exe
 
 
 def build_bounds_checked(force=False, verbose=False):

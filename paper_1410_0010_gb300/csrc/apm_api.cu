@@ -33,10 +33,10 @@ constexpr int kChunkCells = 2048;
 constexpr double kPiHost = 3.141592653589793238462643383279502884;
 
 // kernels, in launch order of one level
-enum Kern { K_GAS = 0, K_DEPOSIT, K_XF, K_YF, K_Z, K_YI, K_XI, K_ACCEL, K_INTERP, K_COUNT };
+enum Kern { K_GAS = 0, K_DEPOSIT, K_XF, K_YF, K_Z, K_YI, K_XI, K_ACCEL, K_INTERP, K_ORDER, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd",
                                            "fft_z_green", "fft_y_inv", "fft_x_inv", "accel_carry",
-                                           "tsc_interp"};
+                                           "tsc_interp", "particle_order"};
 
 struct Profiler {
     bool on = false;
@@ -49,14 +49,23 @@ struct Profiler {
 
 // Launch shape of one FFT pass over a level: the buffer budget that sets each
 // grid's lines per CTA, the threads per CTA, and the resulting work list.
+// One launch of a pass: a contiguous range of the work list whose grids all
+// run the same kernel (fast_L = 0: the runtime-planned kernel; otherwise the
+// FP32 kernel with the compile-time plan of that length).
+struct PassSeg {
+    int first = 0, count = 0;
+    int fast_L = 0;
+    size_t smem = 0;
+};
 struct PassPlan {
     int budget = 0;
     int threads = 0;
     Chunk* d = nullptr;
     int n = 0;
-    size_t smem = 0;
     std::vector<int> lines;          // per grid of the level
-    std::vector<int> first;          // per grid: its first chunk (grid k: [first[k], first[k+1]))
+    std::vector<int> first, count;   // per grid: its chunks [first, first + count)
+    std::vector<int> seg_of;         // per grid: its segment
+    std::vector<PassSeg> seg;
 };
 
 struct Level {
@@ -67,6 +76,12 @@ struct Level {
     LevelDev dev{};
     // CTA work lists: the FFT passes (launch shape per pass), baryons, accelerations
     PassPlan pass[kFftPasses];
+    // autotuned plan choices (apm_fft_shapes): per pass, the compile-time plan
+    // where a length has one (0) or the runtime plan (1); the runtime plans'
+    // largest stage radix; the order grids are packed into each work list
+    int plan[kFftPasses] = {0, 0, 0, 0, 0};
+    int max_radix = 16;
+    int packing = 0;                 // 0 hierarchy order, 1 largest transform first
     Chunk* d_gas = nullptr; int n_gas = 0;
     Chunk* d_acc = nullptr; int n_acc = 0;
     std::vector<int> acc_first;      // per grid: its first acceleration chunk (ng + 1 entries)
@@ -101,6 +116,15 @@ struct apm_ctx {
     void** d_tabs = nullptr;         // [role][level]: each level's device pointer table of the role
     Profiler prof;
     bool batched = true;             // apm_set_grid_batching
+    std::vector<cudaGraphExec_t> graphs;   // apm_graph_end (null: destroyed)
+    // particle processing order (apm_reserve_order / apm_order_particles)
+    struct Order {
+        long long cap = 0;           // particles the workspace holds (0: no ordering)
+        int shift = 0, nb = 0;       // bins: cubes of 2^shift root cells, nb per axis
+        unsigned *count = nullptr, *sums = nullptr, *key = nullptr, *rank = nullptr;
+        int* perm = nullptr;
+        long long n = -1;            // particle count of the current order (-1: none)
+    } order;
 };
 
 namespace {
@@ -149,8 +173,15 @@ void dfree(apm_ctx* c, void* p) {
     if (it != c->dev_allocs.end()) c->dev_allocs.erase(it);
 }
 
+void free_graphs(apm_ctx* c) {
+    for (cudaGraphExec_t g : c->graphs)
+        if (g) cudaGraphExecDestroy(g);
+    c->graphs.clear();
+}
+
 void free_hierarchy(apm_ctx* c) {
     cudaDeviceSynchronize();
+    free_graphs(c);   // they replay launches on the buffers freed below
     for (void* p : c->dev_allocs) cudaFree(p);
     c->dev_allocs.clear();
     for (Level& L : c->levels) {
@@ -164,6 +195,7 @@ void free_hierarchy(apm_ctx* c) {
     c->tw64 = nullptr; c->tw32 = nullptr; c->tab64 = nullptr; c->tab32 = nullptr;
     c->wsA = nullptr; c->wsB = nullptr; c->wsC = nullptr;
     c->d_levels = nullptr; c->d_tabs = nullptr;
+    c->order = apm_ctx::Order();     // its arrays were among dev_allocs
     c->has_hier = false;
 }
 
@@ -189,6 +221,14 @@ long long floor_div(long long a, long long b) {
     long long q = a / b;
     if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
     return q;
+}
+
+// the FP32 column passes use the compile-time plans of fft_fast.cuh where a
+// length has one (APM_FFT_FAST=0 keeps every pass on the runtime-planned
+// kernels, for comparison)
+bool fft_fast_enabled() {
+    const char* v = std::getenv("APM_FFT_FAST");
+    return !(v && std::atoi(v) == 0);
 }
 
 // largest FFT stage radix of the FP32 path (16; APM_FFT_MAX_RADIX overrides it,
@@ -297,31 +337,73 @@ apm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APM_OK : APM_E
 // changes a result.
 apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads, bool f64, PassPlan& P) {
     const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
+    const int ng = (int)L.hg.size();
     std::vector<Chunk> list;
-    P.lines.assign(L.hg.size(), 0);
-    P.first.assign(L.hg.size() + 1, 0);
-    P.smem = 0;
-    for (int k = 0; k < (int)L.hg.size(); ++k) {
-        P.first[k] = (int)list.size();
+    P.lines.assign(ng, 0);
+    P.first.assign(ng, 0);
+    P.count.assign(ng, 0);
+    P.seg_of.assign(ng, 0);
+    P.seg.clear();
+    // the kernel of each grid: a compile-time plan for the FP32 passes of its
+    // length, if there is one (not for the x-inverse pass, whose Stockham
+    // kernel measured faster; not for the spectral gradient's z pass, whose
+    // components share this work list with the runtime-planned kernel, nor for
+    // the x-forward pass while its bulk-copy wait is made to run out)
+    std::vector<int> fast(ng, 0), lens(ng, 0);
+    const bool row = q == kPassXf || q == kPassXi;
+    for (int k = 0; k < ng; ++k) {
         const GridDev& g = L.hg[k];
-        const int len = (q == kPassXf || q == kPassXi) ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
-        int lines = fft_pass_lines(q, len, budget, f64);
-        while (lines > 1 && fft_pass_smem(q, len, lines, csz, g.G[0]) > (size_t)kFftSmemLimit) lines /= 2;
-        P.lines[k] = lines;
-        P.smem = std::max(P.smem, fft_pass_smem(q, len, lines, csz, g.G[0]));
-        if (q == kPassXf || q == kPassXi) {
-            const long long rows = q == kPassXf ? (long long)g.G[1] * g.G[2] : (long long)g.W[1] * g.W[2];
-            const long long n = ((rows + 1) / 2 + lines - 1) / lines;
-            for (long long t = 0; t < n; ++t) list.push_back({k, (int)t});
-        } else {
-            // (kx tile, z | ky | zw) pairs, encoded as (kt << kColOtherBits) | other
-            const int nkt = (g.Hx + lines - 1) / lines;
-            const int n_other = q == kPassYf ? g.G[2] : (q == kPassZ ? g.M[1] : g.W[2]);
-            for (int o = 0; o < n_other; ++o)
-                for (int kt = 0; kt < nkt; ++kt) list.push_back({k, (kt << kColOtherBits) | o});
-        }
+        lens[k] = row ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
+        if (!f64 && q != kPassXi && L.plan[q] == 0 && fft_fast_enabled() && fast_length(lens[k]) &&
+            !(q == kPassZ && c->cfg.gradient == APM_GRAD_SPECTRAL) && !(q == kPassXf && fault_wait()))
+            fast[k] = lens[k];
     }
-    P.first[L.hg.size()] = (int)list.size();
+    std::vector<int> kinds(fast);
+    std::sort(kinds.begin(), kinds.end());
+    kinds.erase(std::unique(kinds.begin(), kinds.end()), kinds.end());
+    // packing: the order of the grids inside each segment's work list
+    std::vector<int> order(ng);
+    for (int k = 0; k < ng; ++k) order[k] = k;
+    if (L.packing == 1) {
+        auto work = [&](int k) { return (long long)L.hg[k].M[0] * L.hg[k].M[1] * L.hg[k].M[2]; };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    }
+    for (int kind : kinds) {
+        PassSeg sg;
+        sg.first = (int)list.size();
+        sg.fast_L = kind;
+        for (int k : order) {
+            if (fast[k] != kind) continue;
+            const GridDev& g = L.hg[k];
+            const int len = lens[k];
+            int lines;
+            if (kind) {
+                lines = row ? kFastNp : kFastTx;
+                sg.smem = row ? fast_row_smem(len) : fast_col_smem(len);
+            } else {
+                lines = fft_pass_lines(q, len, budget, f64);
+                while (lines > 1 && fft_pass_smem(q, len, lines, csz, g.G[0]) > (size_t)kFftSmemLimit) lines /= 2;
+                sg.smem = std::max(sg.smem, fft_pass_smem(q, len, lines, csz, g.G[0]));
+            }
+            P.lines[k] = lines;
+            P.first[k] = (int)list.size();
+            P.seg_of[k] = (int)P.seg.size();
+            if (q == kPassXf || q == kPassXi) {
+                const long long rows = q == kPassXf ? (long long)g.G[1] * g.G[2] : (long long)g.W[1] * g.W[2];
+                const long long n = ((rows + 1) / 2 + lines - 1) / lines;
+                for (long long t = 0; t < n; ++t) list.push_back({k, (int)t});
+            } else {
+                // (kx tile, z | ky | zw) pairs, encoded as (kt << kColOtherBits) | other
+                const int nkt = (g.Hx + lines - 1) / lines;
+                const int n_other = q == kPassYf ? g.G[2] : (q == kPassZ ? g.M[1] : g.W[2]);
+                for (int o = 0; o < n_other; ++o)
+                    for (int kt = 0; kt < nkt; ++kt) list.push_back({k, (kt << kColOtherBits) | o});
+            }
+            P.count[k] = (int)list.size() - P.first[k];
+        }
+        sg.count = (int)list.size() - sg.first;
+        P.seg.push_back(sg);
+    }
     P.budget = budget;
     P.threads = threads;
     P.n = (int)list.size();
@@ -334,13 +416,29 @@ void apply_pass(Level& L, int q) {
     for (size_t k = 0; k < L.hg.size(); ++k) L.hg[k].lines[q] = L.pass[q].lines[k];
 }
 
-// launches FFT pass q of a level with plan P
+// the runtime plans of every grid of the level with stage radices up to r
+// (FP32: 16 or 8; FP64 plans keep radices up to 8)
+bool replan_level(Level& L, int r) {
+    for (GridDev& g : L.hg) {
+        FftPlan1D* pls[3] = {&g.fx, &g.fy, &g.fz};
+        for (int j = 0; j < 3; ++j) {
+            const int off = pls[j]->tw_off;
+            if (!fft_plan(g.M[j], r, pls[j])) return false;
+            pls[j]->tw_off = off;
+        }
+        fft_plan_reversed(g.fy, &g.iy);
+        fft_plan_reversed(g.fz, &g.iz);
+    }
+    L.max_radix = r;
+    return true;
+}
+
+// One launch of pass q over the chunks [first, first + count) of segment sg.
 // comp: with the spectral gradient, the component (0 phi, 1-3 A_x..A_z) of
 // the z, y-inverse and x-inverse passes; the y inverse then writes wsC, so
 // the y-forward output in wsB stays for the next component's z pass.
-// grid >= 0: only that grid's chunks (one grid's launch of the pass)
-cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void** d_gmf, void** d_phis,
-                     cudaStream_t s, int comp = 0, int grid = -1) {
+cudaError_t run_seg(apm_ctx* c, const Level& L, int q, const PassPlan& P, const PassSeg& sg, int first, int count,
+                    void** d_gmf, void** d_phis, cudaStream_t s, int comp) {
     const bool f64 = c->cfg.precision == APM_FP64;
     FftArgs a;
     a.g = L.d_grids;
@@ -349,14 +447,23 @@ cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void*
     a.wsA = c->wsA;
     a.wsB = c->wsB;
     a.F = c->cfg.mass_frac_bits;
-    a.chunks = grid < 0 ? P.d : P.d + P.first[grid];
-    a.n_chunks = grid < 0 ? P.n : P.first[grid + 1] - P.first[grid];
-    a.smem = P.smem;
+    a.chunks = P.d + first;
+    a.n_chunks = count;
+    a.smem = sg.smem;
     a.threads = P.threads;
     a.status = c->d_status;
     a.inject_wait = fault_wait() ? 1 : 0;
     a.comp = comp;
     if (c->cfg.gradient == APM_GRAD_SPECTRAL && (q == kPassYi || q == kPassXi)) a.wsB = c->wsC;
+    if (sg.fast_L) {
+        switch (q) {
+            case kPassYf: return launch_fft_yf_fast(sg.fast_L, a, s);
+            case kPassZ: return launch_fft_z_fast(sg.fast_L, a, s);
+            case kPassYi: return launch_fft_yi_fast(sg.fast_L, a, s);
+            case kPassXf: return launch_fft_xf_fast(sg.fast_L, a, (const int64_t* const*)d_gmf, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (q) {
         case kPassXf:
             return f64 ? launch_fft_xf<double>(a, (const int64_t* const*)d_gmf, s)
@@ -368,6 +475,21 @@ cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void*
         case kPassYi: return f64 ? launch_fft_yi<double>(a, s) : launch_fft_yi<float>(a, s);
         default: return f64 ? launch_fft_xi<double>(a, d_phis, s) : launch_fft_xi<float>(a, d_phis, s);
     }
+}
+
+// launches FFT pass q of a level with plan P: every segment, or with grid >= 0
+// only that grid's chunks (one grid's launch of the pass)
+cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void** d_gmf, void** d_phis,
+                     cudaStream_t s, int comp = 0, int grid = -1) {
+    if (grid >= 0) {
+        const PassSeg& sg = P.seg[P.seg_of[grid]];
+        return run_seg(c, L, q, P, sg, P.first[grid], P.count[grid], d_gmf, d_phis, s, comp);
+    }
+    for (const PassSeg& sg : P.seg) {
+        cudaError_t e = run_seg(c, L, q, P, sg, sg.first, sg.count, d_gmf, d_phis, s, comp);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Uploads the device pointers of one role if they changed since the last call.
@@ -431,6 +553,15 @@ Particles to_dev(const apm_particles* p) {
     q.vx = p->vx; q.vy = p->vy; q.vz = p->vz;
     q.m = p->m;
     return q;
+}
+
+// the interpolation calls visit the particles in the current order when it
+// was computed for this many particles (any order gives the same results).
+// The deposits keep the caller's order: in bin order, neighbouring threads
+// add into the same cells and their L2 reductions serialise (measured slower
+// on the batched level), while the interpolation's gathers gain from it.
+void use_order(const apm_ctx* c, Particles& P) {
+    if (c->order.perm && c->order.n == P.n) P.perm = c->order.perm;
 }
 
 bool particles_ok(const apm_particles* p) {
@@ -598,6 +729,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
     };
     size_t wsA_max = 0, wsB_max = 0;
     for (Level& L : c->levels) {
+        L.max_radix = f64 ? 8 : fft_max_radix();
         long long offA = 0, offB = 0;
         for (int gi : L.grids) {
             const apm_grid& a = grids[gi];
@@ -652,7 +784,7 @@ apm_status apm_set_hierarchy(apm_ctx* c, const apm_grid* grids, int32_t n) {
                 return APM_E_UNSUPPORTED;
             FftPlan1D* pls[3] = {&g.fx, &g.fy, &g.fz};
             for (int j = 0; j < 3; ++j) {
-                if (!fft_plan(g.M[j], f64 ? 8 : fft_max_radix(), pls[j])) return APM_E_UNSUPPORTED;
+                if (!fft_plan(g.M[j], f64 ? 8 : L.max_radix, pls[j])) return APM_E_UNSUPPORTED;
                 pls[j]->tw_off = twiddle(g.M[j]);
             }
             fft_plan_reversed(g.fy, &g.iy);
@@ -985,6 +1117,96 @@ apm_status apm_set_grid_batching(apm_ctx* c, int32_t batched) {
     return APM_OK;
 }
 
+apm_status apm_graph_begin(apm_ctx* c, void* stream) {
+    if (!c || !stream) return APM_E_INVALID;   // the legacy default stream cannot be captured
+    if (!c->has_hier) return APM_E_STATE;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) return APM_E_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return APM_E_STATE;
+    return cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess
+               ? APM_OK : APM_E_CUDA;
+}
+
+apm_status apm_graph_end(apm_ctx* c, void* stream, int32_t* graph_id) {
+    if (!c || !stream || !graph_id) return APM_E_INVALID;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture((cudaStream_t)stream, &g) != cudaSuccess || !g) {
+        cudaGetLastError();
+        return APM_E_STATE;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return APM_E_CUDA;
+    }
+    c->graphs.push_back(exec);
+    *graph_id = (int32_t)c->graphs.size() - 1;
+    return APM_OK;
+}
+
+apm_status apm_graph_launch(apm_ctx* c, int32_t graph_id, void* stream) {
+    if (!c || graph_id < 0 || graph_id >= (int32_t)c->graphs.size() || !c->graphs[graph_id]) return APM_E_INVALID;
+    return cudaGraphLaunch(c->graphs[graph_id], (cudaStream_t)stream) == cudaSuccess ? APM_OK : APM_E_CUDA;
+}
+
+apm_status apm_graph_destroy(apm_ctx* c, int32_t graph_id) {
+    if (!c || graph_id < 0 || graph_id >= (int32_t)c->graphs.size() || !c->graphs[graph_id]) return APM_E_INVALID;
+    cudaGraphExecDestroy(c->graphs[graph_id]);
+    c->graphs[graph_id] = nullptr;
+    return APM_OK;
+}
+
+apm_status apm_reserve_order(apm_ctx* c, int64_t n_max) {
+    Range nvtx_range("apm_reserve_order");
+    if (!c || n_max < 0 || n_max > (int64_t)INT32_MAX) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    apm_ctx::Order& o = c->order;
+    if (cudaDeviceSynchronize() != cudaSuccess) return APM_E_CUDA;
+    for (void* p : {(void*)o.count, (void*)o.sums, (void*)o.key, (void*)o.rank, (void*)o.perm})
+        if (p) dfree(c, p);
+    o = apm_ctx::Order();
+    if (n_max == 0) return APM_OK;
+    // bins of 2^shift root cells, at least 4 per side, at most 128^3 bins (so
+    // the scan's chunk totals fit one CTA)
+    const int N0 = c->grids[0].dims[0];
+    int shift = 2;
+    while (((N0 + (1 << shift) - 1) >> shift) > 128) ++shift;
+    const int nb = (N0 + (1 << shift) - 1) >> shift;
+    const size_t nbins = (size_t)nb * nb * nb;
+    apm_status st;
+    if ((st = dmalloc(c, (void**)&o.count, nbins * sizeof(unsigned))) != APM_OK ||
+        (st = dmalloc(c, (void**)&o.sums, 1024 * sizeof(unsigned))) != APM_OK ||
+        (st = dmalloc(c, (void**)&o.key, (size_t)n_max * sizeof(unsigned))) != APM_OK ||
+        (st = dmalloc(c, (void**)&o.rank, (size_t)n_max * sizeof(unsigned))) != APM_OK ||
+        (st = dmalloc(c, (void**)&o.perm, (size_t)n_max * sizeof(int))) != APM_OK) {
+        for (void* p : {(void*)o.count, (void*)o.sums, (void*)o.key, (void*)o.rank, (void*)o.perm})
+            if (p) dfree(c, p);
+        o = apm_ctx::Order();
+        return st;
+    }
+    o.cap = n_max;
+    o.shift = shift;
+    o.nb = nb;
+    return APM_OK;
+}
+
+apm_status apm_order_particles(apm_ctx* c, const apm_particles* particles, double half_dt, void* stream) {
+    Range nvtx_range("apm_order_particles");
+    if (!c || !particles_ok(particles)) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    apm_ctx::Order& o = c->order;
+    if (!o.perm || particles->n > o.cap) return APM_E_INVALID;
+    Particles P = to_dev(particles);
+    Trace t(c, K_ORDER, (cudaStream_t)stream);
+    if (launch_order(c->levels[0].dev, P, half_dt, o.shift, o.nb, o.count, o.sums, o.key, o.rank, o.perm,
+                     (cudaStream_t)stream) != cudaSuccess)
+        return APM_E_CUDA;
+    o.n = P.n;
+    return APM_OK;
+}
+
 apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
                               void* const* phi_short, void* stream) {
     Range nvtx_range("apm_autotune_level");
@@ -1040,6 +1262,20 @@ apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* g
         *ms = best;
         return APM_OK;
     };
+    // the launch shapes are those of the runtime-planned kernels: tune them with
+    // every pass on that kernel, then choose each pass's plan below
+    const int plan0[kFftPasses] = {L.plan[0], L.plan[1], L.plan[2], L.plan[3], L.plan[4]};
+    if (!f64) {
+        for (int q = 0; q < kFftPasses; ++q) L.plan[q] = 1;
+        for (int q = 0; q < kFftPasses && st == APM_OK; ++q) {
+            PassPlan P;
+            if ((st = build_pass(c, L, q, L.pass[q].budget, L.pass[q].threads, f64, P)) != APM_OK) break;
+            dfree(c, L.pass[q].d);
+            L.pass[q] = P;
+            apply_pass(L, q);
+        }
+        if (st == APM_OK) st = upload_grids();
+    }
     for (int q = 0; q < kFftPasses && st == APM_OK; ++q) {
         float best_ms = 0;
         st = time_pass(q, L.pass[q], &best_ms);
@@ -1064,6 +1300,81 @@ apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* g
         // the chosen shape leaves this pass's output in place for the next pass
         if (st == APM_OK && run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) st = APM_E_CUDA;
     }
+    // whole-level choices, each timed over the five passes (the fastest of
+    // kTuneLaunches level solves after a warm one): the kernel of each pass
+    // (compile-time plan or runtime plan, FP32), the grid packing, and the
+    // runtime plans' largest radix (FP32).  A different plan or radix rounds
+    // differently (both within the FP32 tolerances, tested); the packing only
+    // reorders work.
+    const int ncomp_t = c->cfg.gradient == APM_GRAD_SPECTRAL ? 4 : 1;
+    auto rebuild = [&]() -> apm_status {
+        for (int q = 0; q < kFftPasses; ++q) {
+            PassPlan P;
+            apm_status r = build_pass(c, L, q, L.pass[q].budget, L.pass[q].threads, f64, P);
+            if (r != APM_OK) return r;
+            dfree(c, L.pass[q].d);
+            L.pass[q] = P;
+            apply_pass(L, q);
+        }
+        return upload_grids();
+    };
+    auto time_level = [&](float* ms) -> apm_status {
+        float best = 0;
+        for (int k = 0; k <= kTuneLaunches; ++k) {
+            float t = 0;
+            if (cudaEventRecord(e0, s) != cudaSuccess) return APM_E_CUDA;
+            for (int q = 0; q < kFftPasses; ++q)
+                if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) return APM_E_CUDA;
+            for (int comp = 1; comp < ncomp_t; ++comp)
+                for (int q = kPassZ; q < kFftPasses; ++q)
+                    if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, comp) != cudaSuccess) return APM_E_CUDA;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                return APM_E_CUDA;
+            if (k == 1 || (k > 1 && t < best)) best = t;   // launch 0 warms
+        }
+        *ms = best;
+        return APM_OK;
+    };
+    // one knob at a time: keep the candidate when it is faster, else restore
+    auto try_knob = [&](auto set, auto restore) -> apm_status {
+        float base = 0, cand = 0;
+        apm_status r = time_level(&base);
+        if (r != APM_OK) return r;
+        set();
+        if ((r = rebuild()) != APM_OK || (r = time_level(&cand)) != APM_OK) return r;
+        if (cand < base) return APM_OK;
+        restore();
+        return rebuild();
+    };
+    if (st == APM_OK && !f64) {
+        // each pass: the compile-time plan (where its lengths have one) against
+        // the tuned runtime-planned kernel
+        for (int q = 0; q < kFftPasses && st == APM_OK; ++q) {
+            bool any_fast = false;
+            for (int k = 0; k < (int)L.hg.size(); ++k) {
+                const GridDev& g = L.hg[k];
+                const int len = (q == kPassXf || q == kPassXi) ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
+                any_fast = any_fast || fast_length(len);
+            }
+            if (any_fast && q != kPassXi && fft_fast_enabled())
+                st = try_knob([&] { L.plan[q] = 0; }, [&] { L.plan[q] = 1; });
+            else
+                L.plan[q] = plan0[q];
+        }
+        if (st == APM_OK) st = rebuild();
+    }
+    if (st == APM_OK && L.hg.size() > 1) {
+        const int old = L.packing;
+        st = try_knob([&] { L.packing = 1 - old; }, [&] { L.packing = old; });
+    }
+    if (st == APM_OK && !f64) {
+        const int old = L.max_radix, alt = old == 16 ? 8 : 16;
+        st = try_knob([&] { replan_level(L, alt); }, [&] { replan_level(L, old); });
+    }
+    // the chosen shapes leave the level's potential in phi_short
+    for (int q = 0; q < kFftPasses && st == APM_OK; ++q)
+        if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s) != cudaSuccess) st = APM_E_CUDA;
     // the spectral gradient's other components with the chosen shapes
     const int ncomp = c->cfg.gradient == APM_GRAD_SPECTRAL ? 4 : 1;
     for (int comp = 1; comp < ncomp && st == APM_OK; ++comp)
@@ -1083,10 +1394,14 @@ apm_status apm_get_fft_shapes(const apm_ctx* c, int32_t level, apm_fft_shapes* o
     if (!c || !out) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (level < 0 || level >= (int)c->levels.size()) return APM_E_INVALID;
+    const Level& L = c->levels[level];
     for (int q = 0; q < kFftPasses; ++q) {
-        out->budget[q] = c->levels[level].pass[q].budget;
-        out->threads[q] = c->levels[level].pass[q].threads;
+        out->budget[q] = L.pass[q].budget;
+        out->threads[q] = L.pass[q].threads;
+        out->plan[q] = L.plan[q];
     }
+    out->max_radix = L.max_radix;
+    out->packing = L.packing;
     return APM_OK;
 }
 
@@ -1094,13 +1409,20 @@ apm_status apm_set_fft_shapes(apm_ctx* c, int32_t level, const apm_fft_shapes* s
     if (!c || !shapes) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
     if (level < 0 || level >= (int)c->levels.size()) return APM_E_INVALID;
+    const bool f64 = c->cfg.precision == APM_FP64;
     for (int q = 0; q < kFftPasses; ++q) {
         const int t = shapes->threads[q];
         if (shapes->budget[q] < 1 || (t != 128 && t != 256)) return APM_E_INVALID;
+        if (shapes->plan[q] != 0 && shapes->plan[q] != 1) return APM_E_INVALID;
     }
+    if ((shapes->packing != 0 && shapes->packing != 1) ||
+        (shapes->max_radix != 8 && shapes->max_radix != 16) || (f64 && shapes->max_radix != 8))
+        return APM_E_INVALID;
     Level& L = c->levels[level];
-    const bool f64 = c->cfg.precision == APM_FP64;
     if (cudaDeviceSynchronize() != cudaSuccess) return APM_E_CUDA;
+    for (int q = 0; q < kFftPasses; ++q) L.plan[q] = shapes->plan[q];
+    L.packing = shapes->packing;
+    if (shapes->max_radix != L.max_radix && !replan_level(L, shapes->max_radix)) return APM_E_UNSUPPORTED;
     for (int q = 0; q < kFftPasses; ++q) {
         PassPlan P;
         apm_status st = build_pass(c, L, q, shapes->budget[q], shapes->threads[q], f64, P);
@@ -1177,6 +1499,7 @@ apm_status apm_interp(apm_ctx* c, int32_t level, const void* const* acc,
     if ((st = set_ptrs(c, L, R_ACC_IN, acc, (int)L.grids.size(), &d_acc, s)) != APM_OK) return st;
     const LevelDev* finer = level + 1 < (int)c->levels.size() ? &c->levels[level + 1].dev : nullptr;
     Particles P = to_dev(particles);
+    use_order(c, P);
     Trace t(c, K_INTERP, s);
     cudaError_t e = c->cfg.precision == APM_FP64
         ? launch_interp<double>(L.dev, finer, P, half_dt, (const void* const*)d_acc, acc_out, s)
@@ -1205,6 +1528,7 @@ apm_status apm_interp_all(apm_ctx* c, const void* const* acc, const apm_particle
         if (st != APM_OK) return st;
     }
     Particles P = to_dev(particles);
+    use_order(c, P);
     const void* const* const* tabs = (const void* const* const*)(c->d_tabs + (size_t)R_ACC_IN * nl);
     Trace t(c, K_INTERP, s);
     cudaError_t e = c->cfg.precision == APM_FP64

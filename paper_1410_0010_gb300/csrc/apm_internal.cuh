@@ -140,6 +140,42 @@ inline void fft_plan_reversed(const FftPlan1D& f, FftPlan1D* r) {
     }
 }
 
+// ---- FP32 transforms with compile-time plans (fft_fast.cuh) ------------------
+// Lengths with a compile-time radix plan: X(L, R1, R2, R3); R3 = 1 for two
+// stages.  Every radix is one the FP32 butterflies compute in registers.
+#define APM_FAST_LENGTHS(X) \
+    X(36, 6, 6, 1) X(40, 8, 5, 1) X(42, 7, 6, 1) X(45, 9, 5, 1) X(48, 8, 6, 1) X(49, 7, 7, 1) \
+    X(50, 10, 5, 1) X(54, 9, 6, 1) X(56, 8, 7, 1) X(60, 10, 6, 1) X(63, 9, 7, 1) X(64, 8, 8, 1) \
+    X(70, 10, 7, 1) X(72, 9, 8, 1) X(75, 15, 5, 1) X(80, 10, 8, 1) X(81, 9, 9, 1) X(84, 12, 7, 1) \
+    X(128, 16, 8, 1) X(150, 15, 10, 1) X(256, 16, 16, 1) X(512, 8, 8, 8)
+constexpr int kFastTx = 16;   // kx columns per CTA of a fast column pass
+constexpr int kFastNp = 16;   // complex lines (row pairs) per CTA of the fast x-forward pass
+
+constexpr int fast_gcd(int a, int b) { return b == 0 ? a : fast_gcd(b, a % b); }
+// threads of a fast pass CTA for `lines` lines: lines x the gcd of the stages'
+// butterfly counts (so the trips divide evenly), brought into [64, 256] by
+// powers of two
+constexpr int fast_threads(int r1, int r2, int r3, int lines) {
+    const int L = r1 * r2 * r3;
+    int g = fast_gcd(L / r1, L / r2);
+    if (r3 > 1) g = fast_gcd(g, L / r3);
+    int nt = lines * g;
+    while (nt < 64) nt *= 2;
+    while (nt > 256 && nt % 2 == 0) nt /= 2;
+    return nt;
+}
+// 1 when length L has a compile-time plan
+inline bool fast_length(int L) {
+#define APM_FAST_CASE(LL, A, B, C) if (L == LL) return true;
+    APM_FAST_LENGTHS(APM_FAST_CASE)
+#undef APM_FAST_CASE
+    return false;
+}
+// dynamic shared memory of a fast column-pass CTA: the buffer and the twiddles
+inline size_t fast_col_smem(int L) { return (size_t)(L * kFastTx + L) * sizeof(float2); }
+// ... and of a fast x-forward CTA (rows padded to kFastNp + 1 lines)
+inline size_t fast_row_smem(int L) { return (size_t)(L * (kFastNp + 1) + L) * sizeof(float2); }
+
 // Column-pass chunks carry (kx tile, line index of the other axis) as
 // (kt << 20) | other: other < 2^20, kt < 2^11.
 constexpr int kColOtherBits = 20;
@@ -415,6 +451,8 @@ __device__ __forceinline__ unsigned long long wmul63_small(unsigned long long a,
 struct Particles {
     long long n;
     const double *x, *y, *z, *vx, *vy, *vz, *m;
+    const int* perm = nullptr;   // processing order (launch_order): slot i visits particle perm[i]
+    __device__ __forceinline__ long long at(long long i) const { return perm ? (long long)perm[i] : i; }
 };
 
 // ---------------------------------------------------------------------------
@@ -458,6 +496,14 @@ struct FftArgs {
     int comp = 0;          // spectral gradient: component of the z / xi passes (0 phi, 1-3 A_x..A_z)
 };
 cudaError_t fft_configure();
+
+// Particle processing order (k_order.cu): a counting sort of the particle
+// indices by root-level bin (cubes of 2^shift root cells, nb bins per axis) of
+// their drifted positions into perm; count holds nb^3 bins, sums
+// order_scan_chunks(nb^3) <= 1024 entries, key and rank n entries each.
+int order_scan_chunks(int nbins);
+cudaError_t launch_order(const LevelDev& root, const Particles& P, double half_dt, int shift, int nb,
+                         unsigned* count, unsigned* sums, unsigned* key, unsigned* rank, int* perm, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_xf(const FftArgs& a, const int64_t* const* gmf, cudaStream_t s);
 template <typename T>
@@ -472,6 +518,16 @@ template <typename T>
 cudaError_t launch_fft_zgrad(const FftArgs& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
+// FP32 column passes of length L with a compile-time plan (fast_length(L)):
+// yf, z (with the table) and yi; a.chunks hold kFastTx columns per CTA
+cudaError_t launch_fft_yf_fast(int L, const FftArgs& a, cudaStream_t s);
+cudaError_t launch_fft_z_fast(int L, const FftArgs& a, cudaStream_t s);
+cudaError_t launch_fft_yi_fast(int L, const FftArgs& a, cudaStream_t s);
+// FP32 x-forward pass of length M0 = L with a compile-time plan: kFastNp row
+// pairs per CTA (the x inverse keeps fft_core.cuh's Stockham kernel, whose
+// first stage reads each row's half spectrum in order and whose last stage
+// writes each row in order: measured faster than in-place alternatives)
+cudaError_t launch_fft_xf_fast(int L, const FftArgs& a, const int64_t* const* gmf, cudaStream_t s);
 
 // accelerations + parent carry for the four-point and spectral gradients (the
 // two-point one runs launch_accel), on launch_accel's block work list

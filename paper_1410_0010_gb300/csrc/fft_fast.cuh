@@ -1,0 +1,371 @@
+// fft_fast.cuh -- FP32 FFT passes with the transform length and its radices
+// fixed at compile time (the lengths of fast_radices()), for the same five
+// passes, work lists and data layout as fft_core.cuh's runtime-planned
+// kernels, which remain the path for every other length and for FP64.
+//
+// A length L = R1 R2 (R3) is transformed in place in ONE shared-memory
+// buffer, element-major (line fastest):
+//   forward: decimation in frequency.  Element n = n1 R2 R3 + n2 R3 + n3 sits
+//     at position n.  Stage s takes a DFT of radix R_s over digit s of the
+//     position and multiplies its output k by exp(-2 pi i lo k / (R_s S_s))
+//     (S_s = product of the radices after s, lo = the digits after s), in
+//     place; after the last stage the spectrum X[k1 + R1 k2 + R1 R2 k3]
+//     sits at position (k1, k2, k3) (digit-reversed order).
+//   inverse: decimation in time, the forward's exact reverse: stages from the
+//     last digit to the first, each multiplying by the conjugate twiddles
+//     before its inverse DFT; it takes the digit-reversed spectrum and leaves
+//     the signal in natural order.
+// A butterfly reads and writes the same R positions, so no second buffer is
+// needed; the first stage reads its inputs straight from HBM and the last
+// stage writes straight to HBM, with the natural element index computed from
+// the digits.  Every index, trip count and twiddle stride is a compile-time
+// constant except the butterfly number of the thread.
+#pragma once
+#include "fft_core.cuh"
+
+namespace apm {
+namespace {
+
+// DFT of radix R in registers: the building blocks of fft_core.cuh (direct
+// radices 2, 3, 4, 5, 7, 8 and composites R1 x R2)
+template <int DIR, int R> struct FastDft;
+#define APM_FAST_DFT_DIRECT(R) \
+    template <int DIR> struct FastDft<DIR, R> { \
+        __device__ __forceinline__ static void run(float2* v) { Dft<float, DIR, R>::run(v); } \
+    };
+#define APM_FAST_DFT_COMPOSITE(R, A, B) \
+    template <int DIR> struct FastDft<DIR, R> { \
+        __device__ __forceinline__ static void run(float2* v) { DftC<float, DIR, A, B>::run(v); } \
+    };
+APM_FAST_DFT_DIRECT(2)
+APM_FAST_DFT_DIRECT(3)
+APM_FAST_DFT_DIRECT(4)
+APM_FAST_DFT_DIRECT(5)
+APM_FAST_DFT_DIRECT(7)
+APM_FAST_DFT_DIRECT(8)
+APM_FAST_DFT_COMPOSITE(6, 3, 2)
+APM_FAST_DFT_COMPOSITE(9, 3, 3)
+APM_FAST_DFT_COMPOSITE(10, 5, 2)
+APM_FAST_DFT_COMPOSITE(12, 3, 4)
+APM_FAST_DFT_COMPOSITE(14, 7, 2)
+APM_FAST_DFT_COMPOSITE(15, 5, 3)
+APM_FAST_DFT_COMPOSITE(16, 4, 4)
+#undef APM_FAST_DFT_DIRECT
+#undef APM_FAST_DFT_COMPOSITE
+
+// The compile-time plan: radices R1, R2, R3 (R3 = 1 for two stages).
+template <int A, int B, int Cc> struct FastPlan {
+    static constexpr int R1 = A, R2 = B, R3 = Cc;
+    static constexpr int L = A * B * Cc;
+    static constexpr int NST = Cc == 1 ? 2 : 3;
+    // radix and inner stride of stage s (0-based)
+    static constexpr int radix(int s) { return s == 0 ? A : (s == 1 ? B : Cc); }
+    static constexpr int inner(int s) { return s == 0 ? B * Cc : (s == 1 ? Cc : 1); }
+    // natural (frequency) index of the digit-reversed position with digits
+    // (d1, d2, d3): d1 + R1 d2 + R1 R2 d3
+    __device__ __forceinline__ static int natural(int pos) {
+        const int d1 = pos / (B * Cc), rest = pos - d1 * (B * Cc);
+        const int d2 = rest / Cc, d3 = rest - d2 * Cc;
+        return d1 + A * d2 + A * B * d3;
+    }
+    // the position of natural index k (the inverse of natural())
+    __device__ __forceinline__ static int position(int k) {
+        const int d1 = k % A, q = k / A;
+        const int d2 = q % B, d3 = q / B;
+        return d1 * (B * Cc) + d2 * Cc + d3;
+    }
+};
+
+// One DIF stage s over TX lines with NT threads (line l of position p at
+// buf[p PITCH + l]): butterfly b = (hi, lo) of the
+// stage's L / R butterflies per line reads positions hi R S + k S + lo, takes
+// the DFT (DIR -1 forward; +1 the unnormalised inverse, with conjugate
+// twiddles) and multiplies output k by tw[lo k L / (R S)] (or its conjugate).
+//  IN_G: the inputs come from global memory (natural index = position)
+//  OUT_G: the outputs go to global memory (natural index from the digits;
+//         only for the last stage, whose digits are complete)
+template <class P, int S_, int TX, int NT, bool IN_G, bool OUT_G, class GIN, class GOUT, int PITCH = TX,
+          int DIR = -1>
+__device__ __forceinline__ void fast_dif_stage(float2* buf, const float2* __restrict__ tw, const GIN& gin,
+                                               const GOUT& gout) {
+    constexpr int R = P::radix(S_), S = P::inner(S_), L = P::L;
+    constexpr int NB = L / R, ITEMS = NB * TX, TRIPS = (ITEMS + NT - 1) / NT;
+    constexpr int TWS = L / (R * S);
+#pragma unroll
+    for (int it = 0; it < TRIPS; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (ITEMS % NT != 0 && i >= ITEMS) break;
+        const int line = i % TX, b = i / TX;
+        const int hi = b / S, lo = b - hi * S;
+        const int base = hi * R * S + lo;
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (IN_G) v[k] = gin.ld(base + k * S);
+            else v[k] = buf[(base + k * S) * PITCH + line];
+        }
+        FastDft<DIR, R>::run(v);
+        if constexpr (S > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, DIR>(tw, lo * k * TWS));
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (OUT_G) gout.st(P::natural(base + k * S), v[k]);
+            else buf[(base + k * S) * PITCH + line] = v[k];
+        }
+    }
+}
+
+// One DIT (inverse) stage s: butterfly (hi, lo) multiplies input k by
+// conj(tw[lo k L / (R S)]), takes the inverse DFT and writes output r to
+// position hi R S + r S + lo.
+//  IN_G: the inputs come from global memory (natural index from the digits;
+//        only for the first inverse stage, the last digit)
+//  OUT_G: the outputs go to global memory (the first digit's stage: the
+//         positions are then natural indices)
+template <class P, int S_, int TX, int NT, bool IN_G, bool OUT_G, class GIN, class GOUT, int PITCH = TX>
+__device__ __forceinline__ void fast_dit_stage(float2* buf, const float2* __restrict__ tw, const GIN& gin,
+                                               const GOUT& gout) {
+    constexpr int R = P::radix(S_), S = P::inner(S_), L = P::L;
+    constexpr int NB = L / R, ITEMS = NB * TX, TRIPS = (ITEMS + NT - 1) / NT;
+    constexpr int TWS = L / (R * S);
+#pragma unroll
+    for (int it = 0; it < TRIPS; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (ITEMS % NT != 0 && i >= ITEMS) break;
+        const int line = i % TX, b = i / TX;
+        const int hi = b / S, lo = b - hi * S;
+        const int base = hi * R * S + lo;
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (IN_G) v[k] = gin.ld(P::natural(base + k * S));
+            else v[k] = buf[(base + k * S) * PITCH + line];
+        }
+        if constexpr (S > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, 1>(tw, lo * k * TWS));
+        }
+        FastDft<1, R>::run(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (OUT_G) gout.st(base + k * S, v[k]);
+            else buf[(base + k * S) * PITCH + line] = v[k];
+        }
+    }
+}
+
+// The z pass's middle: the forward's last stage (S = 1), the table multiply at
+// the natural index, and the inverse's first stage on the same registers.
+template <class P, int TX, int NT, class TAB>
+__device__ __forceinline__ void fast_mid_stage(float2* buf, const TAB& tabf) {
+    constexpr int SL = P::NST - 1;
+    constexpr int R = P::radix(SL), L = P::L;
+    constexpr int NB = L / R, ITEMS = NB * TX, TRIPS = (ITEMS + NT - 1) / NT;
+#pragma unroll
+    for (int it = 0; it < TRIPS; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (ITEMS % NT != 0 && i >= ITEMS) break;
+        const int line = i % TX, hi = i / TX;
+        const int base = hi * R;
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = buf[(base + k) * TX + line];
+        FastDft<-1, R>::run(v);
+        // natural index of output k: the digits of hi, then k as the last digit
+        const int k0 = P::natural(base);
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = tabf.apply(k0 + k * (L / R), v[k]);
+        FastDft<1, R>::run(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) buf[(base + k) * TX + line] = v[k];
+    }
+}
+
+// Global element n of this thread's line: p[n stride] for n < n_in (zero
+// beyond: the padding); nothing for a dead line (kx >= Hx).  Offsets stay
+// 32-bit (lines of at most 1024 elements, strides below 1024 x 513).
+struct FastIn {
+    const float2* __restrict__ p;
+    int stride, n;
+    bool live;
+    __device__ __forceinline__ float2 ld(int i) const {
+        return (live && i < n) ? p[i * stride] : make_float2(0.f, 0.f);
+    }
+};
+// Output element i at window index w = (i - s0) mod L, written when w < n, and
+// again at w + L when that is inside the window too (a periodic root's window
+// N + 4 exceeds M = N).
+template <int L> struct FastOut {
+    float2* __restrict__ p;
+    int stride, n, s0;
+    bool live;
+    __device__ __forceinline__ void st(int i, float2 v) const {
+        if (!live) return;
+        int w = i - s0;
+        if (w < 0) w += L;
+        if (w < n) p[w * stride] = v;
+        if (w + L < n) p[(w + L) * stride] = v;
+    }
+};
+
+// Column pass (AX 1: y, 2: z) with compile-time plan P, TX kx columns per CTA
+// (the level's lines for this pass) and NT threads; the same work list and
+// layout as k_col (MODE 0 yf, 1 z with the table, 2 yi).
+template <class P, int AX, int MODE, int TX, int NT>
+__global__ void __launch_bounds__(NT) k_col_fast(const GridDev* __restrict__ grids, const Chunk* __restrict__ chunks,
+                                                 const float2* __restrict__ tw_arena, const float* __restrict__ tab,
+                                                 float2* __restrict__ wsA, float2* __restrict__ wsB) {
+    constexpr int L = P::L;
+    extern __shared__ __align__(16) unsigned char smem_fast[];
+    float2* buf = reinterpret_cast<float2*>(smem_fast);
+    float2* tw = buf + L * TX;
+    const Chunk ch = chunks[blockIdx.x];
+    const GridDev& g = grids[ch.grid];
+    const int Hx = g.Hx;
+    const int other = ch.tile & ((1 << kColOtherBits) - 1);
+    const int kx0 = (ch.tile >> kColOtherBits) * TX;
+    const FftPlan1D& pl = AX == 1 ? g.fy : g.fz;
+    for (int t = threadIdx.x; t < L; t += NT) tw[t] = tw_arena[pl.tw_off + t];
+    const int M1 = g.M[1];
+
+    // global accessors of this thread's line: with NT a multiple of TX the line
+    // (threadIdx.x % TX) is the same in every trip of every stage
+    static_assert(NT % TX == 0, "NT must be a multiple of TX");
+    const int line = threadIdx.x % TX;
+    const bool live = kx0 + line < Hx;
+    FastIn gin;
+    FastOut<L> gout;
+    gin.live = gout.live = live;
+    if (AX == 1 && MODE == 0) {
+        gin.p = wsA + (g.wsA + (long long)other * g.G[1] * Hx + kx0 + line);
+        gin.stride = Hx; gin.n = g.G[1];
+        gout.p = wsB + (g.wsB + (long long)other * M1 * Hx + kx0 + line);
+        gout.stride = Hx; gout.n = M1; gout.s0 = 0;
+    } else if (AX == 2) {
+        gin.p = wsB + (g.wsB + (long long)other * Hx + kx0 + line);
+        gin.stride = M1 * Hx; gin.n = g.G[2];
+        gout.p = wsA + (g.wsA + (long long)other * Hx + kx0 + line);
+        gout.stride = M1 * Hx; gout.n = g.W[2]; gout.s0 = g.s0[2];
+    } else {
+        gin.p = wsA + (g.wsA + (long long)other * M1 * Hx + kx0 + line);
+        gin.stride = Hx; gin.n = M1;
+        gout.p = wsB + (g.wsB + (long long)other * g.W[1] * Hx + kx0 + line);
+        gout.stride = Hx; gout.n = g.W[1]; gout.s0 = g.s0[1];
+    }
+    __syncthreads();   // twiddles
+
+    if constexpr (MODE == 0) {
+        if constexpr (P::NST == 2) {
+            fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gout);
+            __syncthreads();
+            fast_dif_stage<P, 1, TX, NT, false, true>(buf, tw, gin, gout);
+        } else {
+            fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gout);
+            __syncthreads();
+            fast_dif_stage<P, 1, TX, NT, false, false>(buf, tw, gin, gout);
+            __syncthreads();
+            fast_dif_stage<P, 2, TX, NT, false, true>(buf, tw, gin, gout);
+        }
+    } else if constexpr (MODE == 2) {
+        if constexpr (P::NST == 2) {
+            fast_dit_stage<P, 1, TX, NT, true, false>(buf, tw, gin, gout);
+            __syncthreads();
+            fast_dit_stage<P, 0, TX, NT, false, true>(buf, tw, gin, gout);
+        } else {
+            fast_dit_stage<P, 2, TX, NT, true, false>(buf, tw, gin, gout);
+            __syncthreads();
+            fast_dit_stage<P, 1, TX, NT, false, false>(buf, tw, gin, gout);
+            __syncthreads();
+            fast_dit_stage<P, 0, TX, NT, false, true>(buf, tw, gin, gout);
+        }
+    } else {
+        // phi-hat = T(kappa) rho-hat between the forward and the inverse
+        const int ky = other;
+        const int fy = ky <= M1 / 2 ? ky : M1 - ky;
+        TabCol<float> tabf;   // a dead line reads column 0 (its results are never stored)
+        tabf.p = tab + (g.tab_off + (long long)fy * Hx + (live ? kx0 + line : 0));
+        tabf.zst = g.Hy2 * Hx;
+        tabf.L = L;
+        fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gout);
+        __syncthreads();
+        if constexpr (P::NST == 3) {
+            fast_dif_stage<P, 1, TX, NT, false, false>(buf, tw, gin, gout);
+            __syncthreads();
+        }
+        fast_mid_stage<P, TX, NT>(buf, tabf);
+        __syncthreads();
+        if constexpr (P::NST == 3) {
+            fast_dit_stage<P, 1, TX, NT, false, false>(buf, tw, gin, gout);
+            __syncthreads();
+        }
+        fast_dit_stage<P, 0, TX, NT, false, true>(buf, tw, gin, gout);
+    }
+}
+
+// ---- x-forward pass -------------------------------------------------------------
+// A CTA holds NP complex lines, each packing two real rows (2p, 2p+1) of the
+// grid (two-for-one real transforms); buffer element (position, line) at
+// pos (NP + 1) + line (the padding keeps the row-wise passes conflict-free).
+struct NoIO {
+    __device__ float2 ld(int) const { return make_float2(0.f, 0.f); }
+    __device__ void st(int, float2) const {}
+};
+
+// xf: GMF rows -> half spectra along x, A[z][y][kx] (the layout of k_xf).
+// Load pass: the CTA's rows are one contiguous int64 range, read with
+// consecutive threads on consecutive cells and converted (hardware int64 ->
+// float rounding, exact power-of-two scale); positions past G0 and missing
+// rows are zero.  Then the forward stages in place, and the separation of the
+// two real rows, A_k = (Z_k + conj Z_{L-k}) / 2, B_k = (Z_k - conj Z_{L-k}) / 2i,
+// written with consecutive threads on consecutive kx.
+template <class P, int NP, int NT>
+__global__ void __launch_bounds__(NT) k_xf_fast(const GridDev* __restrict__ grids, const Chunk* __restrict__ chunks,
+                                                const int64_t* const* __restrict__ gmf,
+                                                const float2* __restrict__ tw_arena, float2* __restrict__ wsA,
+                                                int F) {
+    constexpr int L = P::L, PITCH = NP + 1, H = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_fast[];
+    float2* buf = reinterpret_cast<float2*>(smem_fast);
+    float2* tw = buf + L * PITCH;
+    const Chunk ch = chunks[blockIdx.x];
+    const GridDev& g = grids[ch.grid];
+    const int G0 = g.G[0];
+    const long long r_first = 2LL * ch.tile * NP;
+    const int nr = (int)min(2LL * NP, (long long)g.G[1] * g.G[2] - r_first);
+    const int64_t* __restrict__ in = gmf[ch.grid] + r_first * G0;
+    for (int t = threadIdx.x; t < L; t += NT) tw[t] = tw_arena[g.fx.tw_off + t];
+    const float scale = pow2_neg<float>(F);
+    float* fb = reinterpret_cast<float*>(buf);
+    // element (x, row q): buffer float (x PITCH + q / 2) * 2 + (q & 1)
+    for (int f = threadIdx.x; f < 2 * NP * L; f += NT) {
+        const int q = f / L, x = f - q * L;
+        float v = 0.f;
+        if (q < nr && x < G0) v = fixed_to_real<float>(in[q * G0 + x], scale);
+        fb[(x * PITCH + (q >> 1)) * 2 + (q & 1)] = v;
+    }
+    __syncthreads();
+    const NoIO none;
+    fast_dif_stage<P, 0, NP, NT, false, false, NoIO, NoIO, PITCH>(buf, tw, none, none);
+    __syncthreads();
+    fast_dif_stage<P, 1, NP, NT, false, false, NoIO, NoIO, PITCH>(buf, tw, none, none);
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        fast_dif_stage<P, 2, NP, NT, false, false, NoIO, NoIO, PITCH>(buf, tw, none, none);
+        __syncthreads();
+    }
+    float2* __restrict__ out = wsA + (g.wsA + r_first * H);
+    for (int f = threadIdx.x; f < NP * H; f += NT) {
+        const int p = f / H, k = f - p * H;
+        const int q0 = 2 * p;
+        if (q0 >= nr) continue;
+        const float2 z = buf[P::position(k) * PITCH + p];
+        const float2 zm = buf[P::position(k == 0 ? 0 : L - k) * PITCH + p];
+        out[q0 * H + k] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+        if (q0 + 1 < nr) out[(q0 + 1) * H + k] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+}
+
+}  // namespace
+}  // namespace apm

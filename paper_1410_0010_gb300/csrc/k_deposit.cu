@@ -22,6 +22,14 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
     const int nrows = G1 * g.G[2];
     const double scale = ldexp(1.0, F);
     const double vol = __dmul_rn(__dmul_rn(g.delta, g.delta), g.delta);
+    // when delta is a power of two, 2^e, the two products are exact exponent
+    // shifts and rint((rho delta^3) 2^F) = rint(rho 2^(F + 3e)), which
+    // scaled_rint computes with integer operations (the FP64 products remain
+    // for other cell sizes and for values scaled_rint cannot hold)
+    const unsigned long long db = (unsigned long long)__double_as_longlong(g.delta);
+    const int de = (int)((db >> 52) & 0x7FF);
+    const bool pow2 = (db & 0xFFFFFFFFFFFFFULL) == 0 && de > 0 && de < 0x7FF;
+    const int K = F + 3 * (de - 1023);
     const double* own = gas ? gas[c.grid] : nullptr;
     const double* par = (pgas && g.parent >= 0) ? pgas[g.parent] : nullptr;
     int64_t* __restrict__ out = gmf[c.grid];
@@ -58,8 +66,12 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
             if (px >= 0 && px < p->N[0] && py >= 0 && py < p->N[1] && pz >= 0 && pz < p->N[2])
                 rho = par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
         }
-        if (APM_IN_BOUNDS((long long)r * G0 + x, g.cells_gmf, L.status))
-            row[x] = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
+        if (APM_IN_BOUNDS((long long)r * G0 + x, g.cells_gmf, L.status)) {
+            bool ok = false;
+            long long v = pow2 ? scaled_rint(rho, K, ok) : 0;
+            if (!ok) v = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
+            row[x] = v;
+        }
     }
 }
 
@@ -211,8 +223,9 @@ __global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(Level
                                                  double box, int F,
                                                  int64_t* const* __restrict__ gmf,
                                                  unsigned* __restrict__ status) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= P.n) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const long long p = P.at(i);
     long long X[3], M;
     bool outside;
     // the candidate test comes first on refined levels (most particles leave there)
@@ -251,8 +264,9 @@ __global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(Level
 __global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit_levels(
     const LevelDev* __restrict__ levels, int nl, Particles P, double half_dt, double box, int F,
     int64_t* const* const* __restrict__ gmfs, unsigned* __restrict__ status) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= P.n) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const long long p = P.at(i);
     long long X[3], M;
     bool outside;
     if (!particle_fixed(levels[0], P, p, half_dt, box, F, X, &M, &outside, status)) return;

@@ -410,8 +410,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_interp(LevelDev L, LevelDev F, int has_finer, Particles P,
                                                 double half_dt, const void* const* __restrict__ acc_p,
                                                 T* __restrict__ out) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= P.n) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const long long p = P.at(i);
     long long X[3];
     particle_position(L, P, p, half_dt, X);
     long long ic[3];
@@ -443,8 +444,9 @@ template <typename T>
 __global__ void __launch_bounds__(kIntThreads, APM_INT_MIN_CTAS) k_interp_levels(const LevelDev* __restrict__ levels, int nl, Particles P,
                                                        double half_dt, const void* const* const* __restrict__ accs,
                                                        T* __restrict__ out) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= P.n) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const long long p = P.at(i);
     long long X[3];
     particle_position(levels[0], P, p, half_dt, X);
     int own_l = -1, own_g = -1;

@@ -186,6 +186,40 @@ class Solver:
                                        ptr_array([_ptr(t) for t in phis]), _stream_handle(stream)),
               "apm_autotune_level")
 
+    def reserve_order(self, n_max):
+        """Workspace for the particle processing order of up to n_max
+        particles (0 frees it); while reserved, step() orders the particles
+        (apm_order_particles) and the interpolation visits them in that
+        order; results are bit-identical either way."""
+        check(lib().apm_reserve_order(self._ctx, int(n_max)), "apm_reserve_order")
+        self.order_capacity = int(n_max)
+
+    def order_particles(self, particles, half_dt, stream=None):
+        P = particles if isinstance(particles, Particles) else Particles(particles)
+        check(lib().apm_order_particles(self._ctx, ctypes.byref(P.c), float(half_dt), _stream_handle(stream)),
+              "apm_order_particles")
+
+    def capture(self, fn):
+        """Records the work fn() issues (typically step() and kick_drift()) as a
+        CUDA graph owned by the library (apm_graph_begin / apm_graph_end), on a
+        side stream ordered after the current one, and returns a Graph whose
+        replay() launches it on the current stream.  Run fn() once before
+        capturing it."""
+        side = torch.cuda.Stream(device=self.device)
+        cur = torch.cuda.current_stream(self.device)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            h = _stream_handle(side)
+            check(lib().apm_graph_begin(self._ctx, h), "apm_graph_begin")
+            try:
+                fn()
+            finally:
+                gid = ctypes.c_int32(-1)
+                rc = lib().apm_graph_end(self._ctx, h, ctypes.byref(gid))
+            check(rc, "apm_graph_end")
+        cur.wait_stream(side)
+        return Graph(self, int(gid.value))
+
     def set_grid_batching(self, batched):
         """True (default): one launch per FFT pass (and for the accelerations)
         over all grids of a level; False: one launch sequence per grid, the
@@ -195,13 +229,20 @@ class Solver:
     def fft_shapes(self, level):
         sh = ApmFftShapes()
         check(lib().apm_get_fft_shapes(self._ctx, level, ctypes.byref(sh)), "apm_get_fft_shapes")
-        return {"budget": list(sh.budget), "threads": list(sh.threads)}
+        return {"budget": list(sh.budget), "threads": list(sh.threads), "plan": list(sh.plan),
+                "max_radix": int(sh.max_radix), "packing": int(sh.packing)}
 
     def set_fft_shapes(self, level, shapes):
+        """Sets a level's shapes; keys missing from `shapes` keep their current
+        values (plan, max_radix and packing may be left out)."""
+        cur = self.fft_shapes(level)
         sh = ApmFftShapes()
         for i in range(5):
             sh.budget[i] = int(shapes["budget"][i])
             sh.threads[i] = int(shapes["threads"][i])
+            sh.plan[i] = int(shapes.get("plan", cur["plan"])[i])
+        sh.max_radix = int(shapes.get("max_radix", cur["max_radix"]))
+        sh.packing = int(shapes.get("packing", cur["packing"]))
         check(lib().apm_set_fft_shapes(self._ctx, level, ctypes.byref(sh)), "apm_set_fft_shapes")
 
     def shape_key(self, level):
@@ -282,10 +323,10 @@ class Solver:
                 self.step(P, 0.5 * dt, bufs, pacc, gas=gas, stream=stream)
                 self.kick_drift(P, pacc, dt, stream)
                 if graph and k < steps:
-                    g = torch.cuda.CUDAGraph()
-                    with torch.cuda.graph(g):
+                    def one():
                         self.step(P, 0.5 * dt, bufs, pacc, gas=gas)
                         self.kick_drift(P, pacc, dt)
+                    g = self.capture(one)
             if callback is not None:
                 callback(k, P, pacc)
 
@@ -329,6 +370,8 @@ class Solver:
                     check_field(g, tuple(self.grids[gi][3])[::-1], torch.float64, self.device, f"gas of grid {gi}")
         levs = range(self.n_levels) if levels is None else levels
         whole = batched and (levels is None or list(levels) == list(range(self.n_levels)))
+        if 0 < P.n <= getattr(self, "order_capacity", 0):
+            self.order_particles(P, half_dt, stream)
         if whole:   # every level: one pass over the particles (apm_deposit_all)
             self.deposit_all(P, half_dt, self._per_grid(bufs, "gmf"), gas, stream)
         for lev in levs:
@@ -362,10 +405,26 @@ class Solver:
             self.interp(lev, bufs[lev]["acc"], P, half_dt, pacc, stream)
 
 
+class Graph:
+    """A library-owned CUDA graph of a Solver (Solver.capture)."""
+
+    def __init__(self, solver, gid):
+        self.s = solver
+        self.gid = gid
+
+    def replay(self, stream=None):
+        check(lib().apm_graph_launch(self.s._ctx, self.gid, _stream_handle(stream)), "apm_graph_launch")
+
+    def destroy(self):
+        if self.gid >= 0 and getattr(self.s, "_ctx", None):
+            check(lib().apm_graph_destroy(self.s._ctx, self.gid), "apm_graph_destroy")
+        self.gid = -1
+
+
 class StepPipeline:
     """End-to-end solves from pinned host particles to host accelerations, with
     the copies overlapped: two device particle/acceleration buffer sets, each
-    with its own captured solve (CUDA graph), and a copy stream that uploads
+    with its own captured solve (a library-owned CUDA graph), and a copy stream that uploads
     step k+1's particles and downloads step k-1's accelerations while step k
     solves.  Every step still copies all of its inputs in and its result out.
 
@@ -393,10 +452,8 @@ class StepPipeline:
             for k in PARTICLE_KEYS:
                 P.t[k].copy_(host[k])
             solver.step(P, half_dt, bufs, pacc, gas=gas, levels=levels)     # warm, outside capture
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                solver.step(P, half_dt, bufs, pacc, gas=gas, levels=levels)
-            self.graphs.append(g)
+            self.graphs.append(solver.capture(
+                lambda P=P, pacc=pacc: solver.step(P, half_dt, bufs, pacc, gas=gas, levels=levels)))
         torch.cuda.synchronize(dev)
         solver.sync_status()
 

@@ -78,7 +78,7 @@ def test_odd_starts_odd_lengths_and_faces(gradient, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_spectral_autotuned_solve_is_bit_identical(precision):
+def test_spectral_autotuned_solve_matches_the_plain_one(precision):
     import torch
 
     from paper_1410_0010_gb300.solver import Particles, Solver
@@ -99,8 +99,23 @@ def test_spectral_autotuned_solve_is_bit_identical(precision):
     s.step(P, 1e-3, bufs, pacc, tune=True)
     s.sync_status()
     tuned = [[t.clone() for t in b["phis"]] + [t.clone() for t in b["acc"]] for b in bufs]
-    for a, b in zip(plain, tuned):
-        for x, y in zip(a, b):
-            assert torch.equal(x, y)
-    assert torch.equal(pa, pacc)
+    if precision == "fp64":
+        # FP64 has one plan per length: launch shapes and packing only regroup work
+        for a, b in zip(plain, tuned):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+        assert torch.equal(pa, pacc)
+    else:
+        # the FP32 tuner may also pick another plan, which rounds differently
+        num = sum(float(((x.double() - y.double()) ** 2).sum()) for a, b in zip(plain, tuned) for x, y in zip(a, b))
+        den = sum(float((x.double() ** 2).sum()) for a in plain for x in a)
+        assert (num / den) ** 0.5 <= 2e-5
+        # and the tuned shapes reproduce the tuned solve bit for bit
+        tuned_pacc = pacc.clone()
+        s.step(P, 1e-3, bufs, pacc)
+        again = [[t.clone() for t in b["phis"]] + [t.clone() for t in b["acc"]] for b in bufs]
+        for a, b in zip(again, tuned):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+        assert torch.equal(pacc, tuned_pacc)
     s.close()
