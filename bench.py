@@ -117,8 +117,11 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
     acceleration kernel reads phi and the three components on the output
     cells instead of differencing."""
     out = {k: 0 for k in ("gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green",
-                          "fft_y_inv", "fft_x_inv", "accel_carry", "tsc_interp")}
+                          "fft_y_inv", "fft_x_inv", "accel_carry", "tsc_interp", "particle_order")}
     n = w.n_particles
+    # the particle order: positions and velocities read (48 B), bin and rank
+    # written and read back (16 B), the permutation written (4 B)
+    out["particle_order"] = 68 * n if getattr(solver, "order_capacity", 0) else 0
     for lev in levels:
         for gi in solver.level_grids[lev]:
             inf = solver.info[gi]
@@ -415,9 +418,13 @@ def run_apm(args):
     w = workload(args.workload)
     levels = list(range(1 + max(g.level for g in w.grids))) if w.solve_levels is None else w.solve_levels
 
-    def make(precision, gradient=args.gradient):
+    use_order = args.order == "on" or (args.order == "auto" and not w.spatial_order)
+
+    def make(precision, gradient=args.gradient, order=use_order):
         s = Solver(w.grids, periodic=w.periodic, precision=precision,
                    mass_frac_bits=w.mass_frac_bits, device=local, gradient=gradient)
+        if order:    # the particle processing order, recomputed every step (apm_order_particles)
+            s.reserve_order(w.n_particles)
         return s, s.alloc_all()
 
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in w.particles.items()}
@@ -457,10 +464,8 @@ def run_apm(args):
         step32()
     s32.sync_status()
     graph = None
-    try:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step32()
+    try:   # the step as a library-owned CUDA graph (apm_graph_begin / apm_graph_end)
+        graph = s32.capture(step32)
         graph.replay()
         torch.cuda.synchronize()
         s32.sync_status()
@@ -544,22 +549,26 @@ def run_apm(args):
     per_grid = None
     if not args.no_per_grid:
         per_grid = {"launch": "one launch sequence per grid for apm_solve_level and apm_accel; "
-                              "deposit and interpolation one pass over the particles for all levels"}
+                              "deposit and interpolation one pass over the particles for all levels, "
+                              "in the particles' own order"}
         for prec in ("fp64", "fp32"):
-            sp, bp = make(prec)
+            sp, bp = make(prec, order=False)
             sp.set_grid_batching(False)
             pp = torch.zeros((3, n), dtype=sp.dtype, device=dev)
 
             def stepp():
                 sp.step(P, w.half_dt, bp, pp, gas=gas, levels=levels)
 
-            if not args.no_tune:
+            # the main solver's shapes and plans (its own tuning for FP64), so the
+            # FP32 per-grid step runs the same kernels grid by grid
+            if prec == "fp32" and shapes32:
+                for lev, sh in shapes32.items():
+                    sp.set_fft_shapes(lev, sh)
+            elif not args.no_tune:
                 sp.autotune(P, w.half_dt, bp, gas=gas, levels=levels)
             stepp()
             sp.sync_status()
-            gp = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(gp):
-                stepp()
+            gp = sp.capture(stepp)
             gp.replay()
             torch.cuda.synchronize()
             sp.sync_status()
@@ -592,10 +601,11 @@ def run_apm(args):
         pe = torch.zeros((3, n), dtype=torch.float32, device=dev)
         s32.step(Pe, w.half_dt, b32, pe, gas=gas, levels=levels)
         s32.kick_drift(Pe, pe, dt)
-        ge = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(ge):
+        def evo():
             s32.step(Pe, w.half_dt, b32, pe, gas=gas, levels=levels)
             s32.kick_drift(Pe, pe, dt)
+
+        ge = s32.capture(evo)
         ge.replay()
         torch.cuda.synchronize()
         s32.sync_status()
@@ -630,9 +640,7 @@ def run_apm(args):
             for _ in range(args.warmup):
                 stepv()
             sv.sync_status()
-            gv = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(gv):
-                stepv()
+            gv = sv.capture(stepv)
             gv.replay()
             torch.cuda.synchronize()
             sv.sync_status()
@@ -713,6 +721,7 @@ def run_apm(args):
                    "interior_cells": cells, "particles": n, "periodic": w.periodic,
                    "l2": "inputs larger than L2 (no flush)", "cuda_graph": used_graph,
                    "parallelism": f"replicas x{world}", "gradient": args.gradient,
+                   "particle_order": "on" if use_order else "off",
                    "fft_shapes": shapes32},
         "particles_per_s": job_rate(ranks, n, ms) * 1e6,
         "roofline": roofline,
@@ -739,6 +748,23 @@ def run_apm(args):
     return 0
 
 
+def probe_peaks():
+    """Builds and runs the compute-peak probe (csrc/peak_probe.cu) and writes
+    profiles/compute_peaks.json: measured FP32/FP64 FMA, INT32 multiply-add,
+    warp-issue and 64-bit reduction rates of this GPU, the denominators of the
+    kernels that are bound by instruction issue rather than HBM."""
+    from paper_1410_0010_gb300 import buildlib
+    exe = buildlib.build_probe()
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    doc = json.loads(out.strip().splitlines()[-1])
+    doc["command"] = "python bench.py --probe-peaks"
+    doc["when"] = time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
+    path = os.path.join(ROOT, "profiles", "compute_peaks.json")
+    with open(path, "w") as f:
+        json.dump(doc, f, indent=1)
+    return path
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -748,6 +774,10 @@ def main():
     ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "c5s"], default="c5")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--order", choices=["auto", "on", "off"], default="auto",
+                    help="sort the particles by root-level bin every step before the particle kernels "
+                         "(apm_order_particles; results are bit-identical either way); auto: unless the "
+                         "workload stores its particles in spatial order (the Zel'dovich lattice)")
     ap.add_argument("--no-per-grid", action="store_true",
                     help="skip timing the plain per-grid launch path (FP64 and FP32)")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")
@@ -759,7 +789,13 @@ def main():
                     help="the gradient operator of the measured solve (default: the two-point difference)")
     ap.add_argument("--no-gradients", action="store_true",
                     help="skip timing the other gradient operators")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="measure this GPU's FP32/FP64/INT32, issue and reduction rates into "
+                         "profiles/compute_peaks.json, then exit")
     args = ap.parse_args()
+    if args.probe_peaks:
+        print(probe_peaks())
+        return 0
     if args.write_traffic:
         print(write_traffic(args.write_traffic))
         return 0
