@@ -345,8 +345,7 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
     P.seg_of.assign(ng, 0);
     P.seg.clear();
     // the kernel of each grid: a compile-time plan for the FP32 passes of its
-    // length, if there is one (not for the x-inverse pass, whose Stockham
-    // kernel measured faster; not for the spectral gradient's z pass, whose
+    // length, if there is one (not for the spectral gradient's z pass, whose
     // components share this work list with the runtime-planned kernel, nor for
     // the x-forward pass while its bulk-copy wait is made to run out)
     std::vector<int> fast(ng, 0), lens(ng, 0);
@@ -354,7 +353,7 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
     for (int k = 0; k < ng; ++k) {
         const GridDev& g = L.hg[k];
         lens[k] = row ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
-        if (!f64 && q != kPassXi && L.plan[q] == 0 && fft_fast_enabled() && fast_length(lens[k]) &&
+        if (!f64 && L.plan[q] == 0 && fft_fast_enabled() && fast_length(lens[k]) &&
             !(q == kPassZ && c->cfg.gradient == APM_GRAD_SPECTRAL) && !(q == kPassXf && fault_wait()))
             fast[k] = lens[k];
     }
@@ -461,7 +460,7 @@ cudaError_t run_seg(apm_ctx* c, const Level& L, int q, const PassPlan& P, const 
             case kPassZ: return launch_fft_z_fast(sg.fast_L, a, s);
             case kPassYi: return launch_fft_yi_fast(sg.fast_L, a, s);
             case kPassXf: return launch_fft_xf_fast(sg.fast_L, a, (const int64_t* const*)d_gmf, s);
-            default: return cudaErrorInvalidValue;
+            default: return launch_fft_xi_fast(sg.fast_L, a, d_phis, s);
         }
     }
     switch (q) {
@@ -1357,7 +1356,7 @@ apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* g
                 const int len = (q == kPassXf || q == kPassXi) ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
                 any_fast = any_fast || fast_length(len);
             }
-            if (any_fast && q != kPassXi && fft_fast_enabled())
+            if (any_fast && fft_fast_enabled())
                 st = try_knob([&] { L.plan[q] = 0; }, [&] { L.plan[q] = 1; });
             else
                 L.plan[q] = plan0[q];

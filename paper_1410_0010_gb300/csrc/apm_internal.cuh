@@ -149,7 +149,7 @@ inline void fft_plan_reversed(const FftPlan1D& f, FftPlan1D* r) {
     X(70, 10, 7, 1) X(72, 9, 8, 1) X(75, 15, 5, 1) X(80, 10, 8, 1) X(81, 9, 9, 1) X(84, 12, 7, 1) \
     X(128, 16, 8, 1) X(150, 15, 10, 1) X(256, 16, 16, 1) X(512, 8, 8, 8)
 constexpr int kFastTx = 16;   // kx columns per CTA of a fast column pass
-constexpr int kFastNp = 16;   // complex lines (row pairs) per CTA of the fast x-forward pass
+constexpr int kFastNp = 16;   // complex lines (row pairs) per CTA of a fast x pass
 
 constexpr int fast_gcd(int a, int b) { return b == 0 ? a : fast_gcd(b, a % b); }
 // threads of a fast pass CTA for `lines` lines: lines x the gcd of the stages'
@@ -173,7 +173,7 @@ inline bool fast_length(int L) {
 }
 // dynamic shared memory of a fast column-pass CTA: the buffer and the twiddles
 inline size_t fast_col_smem(int L) { return (size_t)(L * kFastTx + L) * sizeof(float2); }
-// ... and of a fast x-forward CTA (rows padded to kFastNp + 1 lines)
+// ... and of a fast x-pass CTA (rows padded to kFastNp + 1 lines)
 inline size_t fast_row_smem(int L) { return (size_t)(L * (kFastNp + 1) + L) * sizeof(float2); }
 
 // Column-pass chunks carry (kx tile, line index of the other axis) as
@@ -523,11 +523,10 @@ cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
 cudaError_t launch_fft_yf_fast(int L, const FftArgs& a, cudaStream_t s);
 cudaError_t launch_fft_z_fast(int L, const FftArgs& a, cudaStream_t s);
 cudaError_t launch_fft_yi_fast(int L, const FftArgs& a, cudaStream_t s);
-// FP32 x-forward pass of length M0 = L with a compile-time plan: kFastNp row
-// pairs per CTA (the x inverse keeps fft_core.cuh's Stockham kernel, whose
-// first stage reads each row's half spectrum in order and whose last stage
-// writes each row in order: measured faster than in-place alternatives)
+// FP32 x passes of length M0 = L with a compile-time plan: kFastNp row pairs
+// per CTA (both use fast_row_smem)
 cudaError_t launch_fft_xf_fast(int L, const FftArgs& a, const int64_t* const* gmf, cudaStream_t s);
+cudaError_t launch_fft_xi_fast(int L, const FftArgs& a, void* const* phis, cudaStream_t s);
 
 // accelerations + parent carry for the four-point and spectral gradients (the
 // two-point one runs launch_accel), on launch_accel's block work list

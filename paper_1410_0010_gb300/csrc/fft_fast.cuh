@@ -367,5 +367,121 @@ __global__ void __launch_bounds__(NT) k_xf_fast(const GridDev* __restrict__ grid
     }
 }
 
+// ---- x-inverse pass ---------------------------------------------------------------
+// One DIF stage s with the butterflies of a line on consecutive threads (item
+// i: butterfly i % NB, line i / NB), so the HBM accesses of the first and last
+// stages run along rows; buffer element (position, line) at pos PITCH + line.
+// The global accessors take the line: gin.ld(line, n), gout.st(line, n, v).
+template <class P, int S_, int NL, int NT, bool IN_G, bool OUT_G, int DIR, int PITCH, class GIN, class GOUT>
+__device__ __forceinline__ void fast_dif_stage_rows(float2* buf, const float2* __restrict__ tw, const GIN& gin,
+                                                    const GOUT& gout) {
+    constexpr int R = P::radix(S_), S = P::inner(S_), L = P::L;
+    constexpr int NB = L / R, ITEMS = NB * NL, TRIPS = (ITEMS + NT - 1) / NT;
+    constexpr int TWS = L / (R * S);
+#pragma unroll 1
+    for (int it = 0; it < TRIPS; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (ITEMS % NT != 0 && i >= ITEMS) break;
+        const int line = i / NB, b = i - line * NB;
+        const int hi = b / S, lo = b - hi * S;
+        const int base = hi * R * S + lo;
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (IN_G) v[k] = gin.ld(line, base + k * S);
+            else v[k] = buf[(base + k * S) * PITCH + line];
+        }
+        FastDft<DIR, R>::run(v);
+        if constexpr (S > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, DIR>(tw, lo * k * TWS));
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (OUT_G) gout.st(line, P::natural(base + k * S), v[k]);
+            else buf[(base + k * S) * PITCH + line] = v[k];
+        }
+    }
+}
+
+// xi: half spectra -> real rows of the window, C2R two rows per complex line,
+// as an in-place decimation-in-frequency inverse (DIR +1).  The first stage
+// reads line p's inputs in natural order straight from HBM: Z_k = A_k + i B_k
+// (A, B the half spectra of rows 2p, 2p+1), extended by Hermitian symmetry
+// (A_{L-k} = conj A_k) past H.  The last stage writes straight to the window:
+// real part to row 2p, imaginary part to row 2p+1, at window cell
+// w = (x - s0) mod L (and w + L when inside the window), times 1/(M0 M1 M2);
+// with a two-stage plan its neighbouring butterflies write neighbouring x.
+template <int L> struct XiRowsIn {
+    const float2* __restrict__ p;    // row 0 of this CTA
+    int nr;                          // rows of this CTA
+    __device__ __forceinline__ float2 ld(int line, int k) const {
+        constexpr int H = L / 2 + 1;
+        const int kk = k < H ? k : L - k;
+        const float2* row = p + (2 * line) * H;
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+        if (2 * line < nr) a = row[kk];
+        if (2 * line + 1 < nr) b = row[H + kk];
+        if (k >= H) {
+            a.y = -a.y;
+            b.y = -b.y;
+        }
+        return make_float2(a.x - b.y, a.y + b.x);
+    }
+};
+template <int L> struct XiRowsOut {
+    float* __restrict__ p;           // row 0 of this CTA in the window
+    int W0, s0, nr;
+    float norm;
+    __device__ __forceinline__ void st(int line, int x, float2 v) const {
+        float* row = p + (2 * line) * W0;
+        int w = x - s0;
+        if (w < 0) w += L;
+        for (; w < W0; w += L) {
+            if (2 * line < nr) row[w] = v.x * norm;
+            if (2 * line + 1 < nr) row[W0 + w] = v.y * norm;
+        }
+    }
+};
+
+template <class P, int NP, int NT>
+__global__ void __launch_bounds__(NT) k_xi_fast(const GridDev* __restrict__ grids, const Chunk* __restrict__ chunks,
+                                                const float2* __restrict__ tw_arena,
+                                                const float2* __restrict__ wsB, void* const* __restrict__ phis,
+                                                int comp) {
+    constexpr int L = P::L, H = L / 2 + 1, PITCH = NP + 1;
+    extern __shared__ __align__(16) unsigned char smem_fast[];
+    float2* buf = reinterpret_cast<float2*>(smem_fast);
+    float2* tw = buf + L * PITCH;
+    const Chunk ch = chunks[blockIdx.x];
+    const GridDev& g = grids[ch.grid];
+    const int W0 = g.W[0];
+    const long long r_first = 2LL * ch.tile * NP;
+    const int nr = (int)min(2LL * NP, (long long)g.W[1] * g.W[2] - r_first);
+    for (int t = threadIdx.x; t < L; t += NT) tw[t] = tw_arena[g.fx.tw_off + t];
+    XiRowsIn<L> gin;
+    gin.p = wsB + (g.wsB + r_first * H);
+    gin.nr = nr;
+    XiRowsOut<L> gout;
+    // component comp of a spectral-gradient solve: the comp-th window of W cells
+    gout.p = reinterpret_cast<float*>(phis[ch.grid]) + (long long)comp * g.W[0] * g.W[1] * g.W[2] + r_first * W0;
+    gout.W0 = W0;
+    gout.s0 = g.s0[0];
+    gout.nr = nr;
+    gout.norm = (float)g.inv_m3;
+    __syncthreads();   // twiddles
+    using GI = XiRowsIn<L>;
+    using GO = XiRowsOut<L>;
+    fast_dif_stage_rows<P, 0, NP, NT, true, false, 1, PITCH, GI, GO>(buf, tw, gin, gout);
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        fast_dif_stage_rows<P, 1, NP, NT, false, false, 1, PITCH, GI, GO>(buf, tw, gin, gout);
+        __syncthreads();
+        fast_dif_stage_rows<P, 2, NP, NT, false, true, 1, PITCH, GI, GO>(buf, tw, gin, gout);
+    } else {
+        fast_dif_stage_rows<P, 1, NP, NT, false, true, 1, PITCH, GI, GO>(buf, tw, gin, gout);
+    }
+}
+
 }  // namespace
 }  // namespace apm
