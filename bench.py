@@ -123,7 +123,8 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
     # written and read back (16 B), the permutation written (4 B)
     out["particle_order"] = 68 * n if getattr(solver, "order_capacity", 0) else 0
     for lev in levels:
-        for gi in solver.level_grids[lev]:
+        kinds = solver.pass_kernels(lev)
+        for j, gi in enumerate(solver.level_grids[lev]):
             inf = solver.info[gi]
             G, M, Wd, F = inf["gmf"], inf["fft"], inf["phi_short"], inf["field"]
             Hx = M[0] // 2 + 1
@@ -131,13 +132,19 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
             gas_b = 8 * int(np.prod(w.grids[gi].dims)) if (w.gas is not None and w.gas[gi] is not None) else 0
             out["gas_init"] += 8 * cg + gas_b
             out["tsc_deposit"] += 8 * cg                      # the accumulated field
-            out["fft_x_fwd"] += 8 * cg + csz * G[1] * G[2] * Hx
-            out["fft_y_fwd"] += csz * G[1] * G[2] * Hx + csz * G[2] * M[1] * Hx
+            if kinds[0][j] == 2:                       # fused x + y forward: GMF in, y spectrum out
+                out["fft_x_fwd"] += 8 * cg + csz * G[2] * M[1] * Hx
+            else:
+                out["fft_x_fwd"] += 8 * cg + csz * G[1] * G[2] * Hx
+                out["fft_y_fwd"] += csz * G[1] * G[2] * Hx + csz * G[2] * M[1] * Hx
             comps = inf.get("comps", 1)
             out["fft_z_green"] += comps * (csz * G[2] * M[1] * Hx + csz * Wd[2] * M[1] * Hx
                                            + rsz * Hx * (M[1] // 2 + 1) * (M[2] // 2 + 1))
-            out["fft_y_inv"] += comps * (csz * Wd[2] * M[1] * Hx + csz * Wd[2] * Wd[1] * Hx)
-            out["fft_x_inv"] += comps * (csz * Wd[2] * Wd[1] * Hx + rsz * Wd[0] * Wd[1] * Wd[2])
+            if kinds[4][j] == 2:                       # fused y + x inverse: z output in, window out
+                out["fft_x_inv"] += comps * (csz * Wd[2] * M[1] * Hx + rsz * Wd[0] * Wd[1] * Wd[2])
+            else:
+                out["fft_y_inv"] += comps * (csz * Wd[2] * M[1] * Hx + csz * Wd[2] * Wd[1] * Hx)
+                out["fft_x_inv"] += comps * (csz * Wd[2] * Wd[1] * Hx + rsz * Wd[0] * Wd[1] * Wd[2])
             ec = F[0] * F[1] * F[2]
             if comps > 1:
                 out["accel_carry"] += 4 * rsz * ec + 4 * rsz * ec
@@ -269,8 +276,8 @@ def sample_grids(w, n_grids=2):
 def oracle_sample(w, n_grids=2, outputs=None):
     """The sampled grids of the workload (sample_grids) solved by the FP64 CPU
     oracle: TSC deposit of every particle touching each GMF (with the grid's
-    gas), naive-DFT convolution on its M grid, FD accelerations (the parent
-    carry is omitted: zero parent fields).  Returns (interior cells, seconds,
+    gas and, on its border, the parent's), naive-DFT convolution on its M
+    grid, FD accelerations (the parent carry is omitted: zero parent fields).  Returns (interior cells, seconds,
     description); with outputs={} it also fills outputs[gi] = (phi_short, acc)."""
     import oracle
     cfg = oracle.Config(periodic=w.periodic, mass_frac_bits=w.mass_frac_bits)
@@ -280,7 +287,9 @@ def oracle_sample(w, n_grids=2, outputs=None):
     t0 = time.perf_counter()
     for gi in ids:
         gas = None if w.gas is None else w.gas[gi]
-        gmf, _ = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt, gas=gas)
+        par = w.grids[gi].parent
+        pgas = None if (w.gas is None or par < 0) else w.gas[par]   # the border's baryons (Sec. 2)
+        gmf, _ = oracle.deposit(cfg, grids, gi, w.particles, w.half_dt, gas=gas, parent_gas=pgas)
         phis = oracle.solve(cfg, grids, gi, gmf)
         _, acc = oracle.accel(cfg, grids, gi, phis)
         if outputs is not None:

@@ -315,9 +315,13 @@ apm_status apm_order_particles(apm_ctx* ctx, const apm_particles* particles, dou
  *  threads[p] the runtime-planned pass's CTA size, 128 or 256;
  *  plan[p]    0: FP32 grids whose length has a compile-time plan (every
  *             {2,3,5,7}-smooth length from 36 to 84, and 128, 150, 256, 512)
- *             run the kernel specialised for it (16 lines per CTA; not the x
- *             inverse, nor the spectral gradient's z pass); 1: every grid runs
- *             the runtime-planned kernel;
+ *             run the kernel specialised for it (16 lines per CTA; not the
+ *             spectral gradient's z pass); 1: every grid runs the
+ *             runtime-planned kernel; 2 (x forward and x inverse only): as 0,
+ *             and grids with M0 = M1 whose M x (M/2 + 1) plane fits 200 KB run
+ *             the x and y transforms of a whole z plane in one kernel (the y
+ *             pass then has no work for them; the inverse needs the window no
+ *             taller than M1, which excludes a periodic root);
  *  max_radix  the largest stage radix of the runtime plans: 16 (FP32
  *             default; composite radices in registers) or 8 (FP64: always 8);
  *  packing    0: the grids of a level enter each work list in hierarchy order;
@@ -354,6 +358,18 @@ apm_status apm_autotune_level(apm_ctx* ctx, int32_t level, const int64_t* const*
  * outside the rules above (FP64: max_radix 8). */
 apm_status apm_get_fft_shapes(const apm_ctx* ctx, int32_t level, apm_fft_shapes* out);
 apm_status apm_set_fft_shapes(apm_ctx* ctx, int32_t level, const apm_fft_shapes* shapes);
+
+/* The kernel that FFT pass `pass` (0 x forward, 1 y forward, 2 z with the
+ * table, 3 y inverse, 4 x inverse) runs for each of the n grids of `level`
+ * under its current shapes, in the level's grid order (that of
+ * apm_solve_level's arrays): kinds[i] = 0 the runtime-planned kernel, 1 the
+ * kernel with the compile-time plan of the grid's length, 2 the fused plane
+ * kernel (this x pass and the y pass together), 3 nothing (the grid's y pass
+ * is done by the fused kernel).  An extension without a counterpart in the
+ * paper (its cost accounting names the passes, not their kernels).
+ * APM_E_STATE without a hierarchy; APM_E_INVALID for a bad level or pass, or
+ * n different from the level's grid count. */
+apm_status apm_get_pass_kernels(const apm_ctx* ctx, int32_t level, int32_t pass, int32_t* kinds, int32_t n);
 
 /* TSC interpolation of the cell accelerations to the particles (Sec. 2, the
  * same 27 weights as the deposit, at the same drifted position).  Only
@@ -398,7 +414,10 @@ apm_status apm_kick_drift(apm_ctx* ctx, int64_t n, double* x, double* y, double*
  * timed).  apm_profile_read synchronises the device, adds the elapsed times of
  * the recorded launches of kernel `kernel` (0 <= kernel < apm_kernel_count())
  * to its totals and returns the totals since the last enable:
- * launches and summed device milliseconds.  Disabling frees the pool. */
+ * launches and summed device milliseconds.  An FFT pass whose grids run
+ * different kernels (segments) is one bracket that counts each segment's
+ * launch; a y pass fused into its x pass launches and counts nothing.
+ * Disabling frees the pool. */
 apm_status apm_profile_enable(apm_ctx* ctx, int32_t on, int32_t capacity);
 apm_status apm_profile_read(apm_ctx* ctx, int32_t kernel, int64_t* launches, double* total_ms);
 int32_t apm_kernel_count(void);

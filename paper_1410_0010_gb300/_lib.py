@@ -77,6 +77,7 @@ SIGNATURES = {
     "apm_order_particles": (c_i32, [c_void_p, ctypes.POINTER(ApmParticles), c_dbl, c_void_p]),
     "apm_get_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
     "apm_set_fft_shapes": (c_i32, [c_void_p, c_i32, ctypes.POINTER(ApmFftShapes)]),
+    "apm_get_pass_kernels": (c_i32, [c_void_p, c_i32, c_i32, ctypes.POINTER(c_i32), c_i32]),
     "apm_kick_drift": (c_i32, [c_void_p, c_i64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_void_p, c_dbl, c_void_p]),
     "apm_sync_status": (c_i32, [c_void_p, c_void_p]),

@@ -1,6 +1,7 @@
 // apm_api.cu -- the C ABI of libapm (include/apm.h): context, hierarchy
 // planning and validation, device arenas, and the per-level launch sequences.
 #include <algorithm>
+#include <climits>
 #include <array>
 #include <cmath>
 #include <cstdlib>
@@ -42,6 +43,7 @@ struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> ev;          // 2 per pair
     std::vector<int> kind;                // per used pair
+    std::vector<int> n_launch;            // kernel launches inside each pair
     int used = 0;
     long long launches[K_COUNT] = {};
     double ms[K_COUNT] = {};
@@ -350,12 +352,31 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
     // the x-forward pass while its bulk-copy wait is made to run out)
     std::vector<int> fast(ng, 0), lens(ng, 0);
     const bool row = q == kPassXf || q == kPassXi;
+    // with plan 2 on the x-forward pass, a grid with M0 = M1 whose plane fits
+    // runs the fused x + y forward (k_xy_fast) as its x-forward segment (kind
+    // -L) and has no y-forward work (kind kSkip); other grids run plan 0
+    constexpr int kSkip = INT_MIN;
+    // (the kernel stores row pair p in plane rows 2p, 2p + 1: an odd G1 needs
+    // G1 < M1, so that the pairs fit the M1 rows of the plane)
+    auto fused_xy = [&](const GridDev& g) {
+        return !f64 && L.plan[kPassXf] == 2 && fft_fast_enabled() && !fault_wait() && g.M[0] == g.M[1] &&
+               fast_xy_length(g.M[0]) && 2 * ((g.G[1] + 1) / 2) <= g.M[1];
+    };
+    // ... and the fused y + x inverse (k_yx_fast) as its x-inverse segment when
+    // the window's row pairs are distinct rows of the transform (2 ceil(W1/2)
+    // <= M1: a periodic root, whose window is taller than M1, is excluded)
+    auto fused_yx = [&](const GridDev& g) {
+        return !f64 && L.plan[kPassXi] == 2 && fft_fast_enabled() && g.M[0] == g.M[1] && fast_xy_length(g.M[0]) &&
+               2 * ((g.W[1] + 1) / 2) <= g.M[1];
+    };
     for (int k = 0; k < ng; ++k) {
         const GridDev& g = L.hg[k];
         lens[k] = row ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
-        if (!f64 && L.plan[q] == 0 && fft_fast_enabled() && fast_length(lens[k]) &&
+        if (!f64 && L.plan[q] != 1 && fft_fast_enabled() && fast_length(lens[k]) &&
             !(q == kPassZ && c->cfg.gradient == APM_GRAD_SPECTRAL) && !(q == kPassXf && fault_wait()))
             fast[k] = lens[k];
+        if ((q == kPassXf || q == kPassYf) && fused_xy(g)) fast[k] = q == kPassXf ? -lens[k] : kSkip;
+        if ((q == kPassXi || q == kPassYi) && fused_yx(g)) fast[k] = q == kPassXi ? -lens[k] : kSkip;
     }
     std::vector<int> kinds(fast);
     std::sort(kinds.begin(), kinds.end());
@@ -368,6 +389,16 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
     }
     for (int kind : kinds) {
+        if (kind == kSkip) {            // fused into the x-forward segment: no chunks
+            for (int k = 0; k < ng; ++k)
+                if (fast[k] == kSkip) {
+                    P.lines[k] = kFastTx;
+                    P.first[k] = 0;
+                    P.count[k] = 0;
+                    P.seg_of[k] = 0;
+                }
+            continue;
+        }
         PassSeg sg;
         sg.first = (int)list.size();
         sg.fast_L = kind;
@@ -375,6 +406,16 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
             if (fast[k] != kind) continue;
             const GridDev& g = L.hg[k];
             const int len = lens[k];
+            if (kind < 0) {             // fused x + y passes: one chunk per z (window) plane
+                P.lines[k] = kFastNp;
+                P.first[k] = (int)list.size();
+                P.seg_of[k] = (int)P.seg.size();
+                sg.smem = fast_xy_smem(len);
+                const int planes = q == kPassXf ? g.G[2] : g.W[2];
+                for (int zp = 0; zp < planes; ++zp) list.push_back({k, zp});
+                P.count[k] = (int)list.size() - P.first[k];
+                continue;
+            }
             int lines;
             if (kind) {
                 lines = row ? kFastNp : kFastTx;
@@ -454,6 +495,9 @@ cudaError_t run_seg(apm_ctx* c, const Level& L, int q, const PassPlan& P, const 
     a.inject_wait = fault_wait() ? 1 : 0;
     a.comp = comp;
     if (c->cfg.gradient == APM_GRAD_SPECTRAL && (q == kPassYi || q == kPassXi)) a.wsB = c->wsC;
+    if (sg.fast_L < 0)
+        return q == kPassXf ? launch_fft_xy_fast(-sg.fast_L, a, (const int64_t* const*)d_gmf, s)
+                            : launch_fft_yx_fast(-sg.fast_L, a, d_phis, s);
     if (sg.fast_L) {
         switch (q) {
             case kPassYf: return launch_fft_yf_fast(sg.fast_L, a, s);
@@ -481,6 +525,7 @@ cudaError_t run_seg(apm_ctx* c, const Level& L, int q, const PassPlan& P, const 
 cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void** d_gmf, void** d_phis,
                      cudaStream_t s, int comp = 0, int grid = -1) {
     if (grid >= 0) {
+        if (P.count[grid] == 0) return cudaSuccess;   // fused into another pass
         const PassSeg& sg = P.seg[P.seg_of[grid]];
         return run_seg(c, L, q, P, sg, P.first[grid], P.count[grid], d_gmf, d_phis, s, comp);
     }
@@ -530,7 +575,12 @@ struct Trace {
         if (!P.on || P.used * 2 + 1 >= (int)P.ev.size()) return;
         pair = P.used++;
         P.kind[pair] = k;
+        P.n_launch[pair] = 1;
         cudaEventRecord(P.ev[2 * pair], s);
+    }
+    // the bracket holds n launches of the kernel (an FFT pass of several segments)
+    void launches(int n) {
+        if (pair >= 0) c->prof.n_launch[pair] = n;
     }
     ~Trace() {
         if (pair >= 0) cudaEventRecord(c->prof.ev[2 * pair + 1], s);
@@ -1096,14 +1146,20 @@ apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
     const int g_first = c->batched ? -1 : 0, g_last = c->batched ? -1 : ng - 1;
     for (int gk = g_first; gk <= g_last; ++gk) {
         for (int q = 0; q < kFftPasses; ++q) {
+            // a y pass fused into its x pass launches nothing (and is not traced)
+            const PassPlan& P = L.pass[q];
+            if (gk < 0 ? P.seg.empty() : P.count[gk] == 0) continue;
             Trace t(c, kind[q], s);
-            if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, 0, gk) != cudaSuccess) return APM_E_CUDA;
+            t.launches(gk < 0 ? (int)P.seg.size() : 1);
+            if (run_pass(c, L, q, P, d_gmf, d_phis, s, 0, gk) != cudaSuccess) return APM_E_CUDA;
         }
         // the spectral gradient's acceleration components: z (table times
         // -i D_comp), y inverse and x inverse again on the kept forward transform
         for (int comp = 1; comp < ncomp; ++comp)
             for (int q = kPassZ; q < kFftPasses; ++q) {
+                if (gk < 0 ? L.pass[q].seg.empty() : L.pass[q].count[gk] == 0) continue;
                 Trace t(c, kind[q], s);
+                t.launches(gk < 0 ? (int)L.pass[q].seg.size() : 1);
                 if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, comp, gk) != cudaSuccess) return APM_E_CUDA;
             }
     }
@@ -1362,6 +1418,17 @@ apm_status apm_autotune_level(apm_ctx* c, int32_t level, const int64_t* const* g
                 L.plan[q] = plan0[q];
         }
         if (st == APM_OK) st = rebuild();
+        // the fused plane kernels: x + y forward, y + x inverse (grids with
+        // M0 = M1 whose plane fits)
+        bool any_fuse = false;
+        for (const GridDev& g : L.hg) any_fuse = any_fuse || (g.M[0] == g.M[1] && fast_xy_length(g.M[0]));
+        if (any_fuse && fft_fast_enabled()) {
+            for (int q : {(int)kPassXf, (int)kPassXi}) {
+                if (st != APM_OK) break;
+                const int old = L.plan[q];
+                st = try_knob([&] { L.plan[q] = 2; }, [&] { L.plan[q] = old; });
+            }
+        }
     }
     if (st == APM_OK && L.hg.size() > 1) {
         const int old = L.packing;
@@ -1404,6 +1471,24 @@ apm_status apm_get_fft_shapes(const apm_ctx* c, int32_t level, apm_fft_shapes* o
     return APM_OK;
 }
 
+apm_status apm_get_pass_kernels(const apm_ctx* c, int32_t level, int32_t pass, int32_t* kinds, int32_t n) {
+    if (!c || !kinds) return APM_E_INVALID;
+    if (!c->has_hier) return APM_E_STATE;
+    if (level < 0 || level >= (int)c->levels.size() || pass < 0 || pass >= kFftPasses) return APM_E_INVALID;
+    const Level& L = c->levels[level];
+    const PassPlan& P = L.pass[pass];
+    if (n != (int)L.hg.size() || (int)P.count.size() != n) return APM_E_INVALID;
+    for (int k = 0; k < n; ++k) {
+        if (P.count[k] == 0) {
+            kinds[k] = 3;
+            continue;
+        }
+        const int f = P.seg[P.seg_of[k]].fast_L;
+        kinds[k] = f < 0 ? 2 : (f > 0 ? 1 : 0);
+    }
+    return APM_OK;
+}
+
 apm_status apm_set_fft_shapes(apm_ctx* c, int32_t level, const apm_fft_shapes* shapes) {
     if (!c || !shapes) return APM_E_INVALID;
     if (!c->has_hier) return APM_E_STATE;
@@ -1412,7 +1497,8 @@ apm_status apm_set_fft_shapes(apm_ctx* c, int32_t level, const apm_fft_shapes* s
     for (int q = 0; q < kFftPasses; ++q) {
         const int t = shapes->threads[q];
         if (shapes->budget[q] < 1 || (t != 128 && t != 256)) return APM_E_INVALID;
-        if (shapes->plan[q] != 0 && shapes->plan[q] != 1) return APM_E_INVALID;
+        const int pmax = (q == kPassXf || q == kPassXi) ? 2 : 1;   // 2: fused with the y pass
+        if (shapes->plan[q] < 0 || shapes->plan[q] > pmax) return APM_E_INVALID;
     }
     if ((shapes->packing != 0 && shapes->packing != 1) ||
         (shapes->max_radix != 8 && shapes->max_radix != 16) || (f64 && shapes->max_radix != 8))
@@ -1565,6 +1651,7 @@ apm_status apm_profile_enable(apm_ctx* c, int32_t on, int32_t capacity) {
     if (capacity < 1) return APM_E_INVALID;
     P.ev.resize(2 * (size_t)capacity);
     P.kind.assign(capacity, 0);
+    P.n_launch.assign(capacity, 1);
     for (cudaEvent_t& e : P.ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
@@ -1587,7 +1674,7 @@ apm_status apm_profile_read(apm_ctx* c, int32_t kernel, int64_t* launches, doubl
                 cudaGetLastError();
                 continue;
             }
-            P.launches[P.kind[i]] += 1;
+            P.launches[P.kind[i]] += P.n_launch[i];
             P.ms[P.kind[i]] += ms;
         }
         P.used = 0;

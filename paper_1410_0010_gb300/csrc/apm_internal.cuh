@@ -523,6 +523,16 @@ cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
 cudaError_t launch_fft_yf_fast(int L, const FftArgs& a, cudaStream_t s);
 cudaError_t launch_fft_z_fast(int L, const FftArgs& a, cudaStream_t s);
 cudaError_t launch_fft_yi_fast(int L, const FftArgs& a, cudaStream_t s);
+// the fused x + y forward over one z plane (k_xy_fast) of a grid with
+// M0 = M1 = L: the plane (L rows x L/2 + 1 columns) and the twiddles
+constexpr int kFastXyThreads = 384;
+inline size_t fast_xy_smem(int L) { return (size_t)(L * (L / 2 + 1) + L) * sizeof(float2); }
+inline bool fast_xy_length(int L) { return fast_length(L) && fast_xy_smem(L) <= (size_t)kFftSmemLimit; }
+cudaError_t launch_fft_xy_fast(int L, const FftArgs& a, const int64_t* const* gmf, cudaStream_t s);
+// ... and its inverse, the fused y + x inverse over one window plane
+// (k_yx_fast), for grids whose window fits the transform (W1 <= M1)
+cudaError_t launch_fft_yx_fast(int L, const FftArgs& a, void* const* phis, cudaStream_t s);
+
 // FP32 x passes of length M0 = L with a compile-time plan: kFastNp row pairs
 // per CTA (both use fast_row_smem)
 cudaError_t launch_fft_xf_fast(int L, const FftArgs& a, const int64_t* const* gmf, cudaStream_t s);

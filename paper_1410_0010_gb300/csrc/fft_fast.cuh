@@ -483,5 +483,360 @@ __global__ void __launch_bounds__(NT) k_xi_fast(const GridDev* __restrict__ grid
     }
 }
 
+// ---- fused x + y forward over one z plane --------------------------------------
+// For a grid whose x and y lengths are both L (a compile-time plan), one CTA
+// transforms a whole z plane: the x transforms of its GMF row pairs and the y
+// transforms of the resulting half spectra, in one shared-memory plane of
+// L rows x H = L/2 + 1 columns, writing only the y spectrum B[z][ky][kx] (the
+// layout of the y-forward pass) to HBM.  The x spectrum never leaves the SM.
+//  - x lines: line p (rows 2p, 2p+1) lives line-major in plane rows 2p and
+//    2p + 1 (2H = L + 2 >= L positions); DIF stages with consecutive threads on
+//    consecutive butterflies of a line; the first reads the int64 rows from HBM;
+//  - separation of the two real rows, one warp per line: it reads the line's
+//    digit-reversed Z_k and Z_{L-k} into registers, then writes A_k to row 2p
+//    and B_k to row 2p + 1 (column k);
+//  - y: DIF stages over the H columns (element-major, consecutive threads on
+//    consecutive columns), the last writing natural ky to HBM.
+template <int L> struct XyIn {
+    const int64_t* __restrict__ p;   // row 0 of the z plane
+    int G0, G1;
+    float scale;
+    __device__ __forceinline__ float2 ld(int line, int x) const {
+        float a = 0.f, b = 0.f;
+        if (x < G0) {
+            const int64_t* row = p + (long long)(2 * line) * G0;
+            if (2 * line < G1) a = fixed_to_real<float>(row[x], scale);
+            if (2 * line + 1 < G1) b = fixed_to_real<float>(row[G0 + x], scale);
+        }
+        return make_float2(a, b);
+    }
+};
+template <int L> struct XyOut {
+    float2* __restrict__ p;          // B row ky = 0 of this plane, column 0
+    int Hx;
+    __device__ __forceinline__ void st(int col, int ky, float2 v) const { p[ky * Hx + col] = v; }
+};
+
+// one DIF stage of the x lines (line-major, line storage LS complex apart,
+// butterflies on consecutive threads); nl lines (runtime)
+template <class P, int S_, int NT, bool IN_G, int LS, class GIN>
+__device__ __forceinline__ void xy_x_stage(float2* buf, const float2* __restrict__ tw, const GIN& gin, int nl) {
+    constexpr int R = P::radix(S_), S = P::inner(S_), L = P::L;
+    constexpr int NB = L / R;
+    constexpr int TWS = L / (R * S);
+    const int items = NB * nl;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < items; i += NT) {
+        const int line = i / NB, b = i - line * NB;
+        const int hi = b / S, lo = b - hi * S;
+        const int base = hi * R * S + lo;
+        float2* lb = buf + line * LS;
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (IN_G) v[k] = gin.ld(line, base + k * S);
+            else v[k] = lb[base + k * S];
+        }
+        FastDft<-1, R>::run(v);
+        if constexpr (S > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], tw[lo * k * TWS]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) lb[base + k * S] = v[k];
+    }
+}
+
+// one DIF stage of the y columns (element-major, H columns, columns on
+// consecutive threads)
+template <class P, int S_, int NT, bool OUT_G, class GOUT>
+__device__ __forceinline__ void xy_y_stage(float2* buf, const float2* __restrict__ tw, const GOUT& gout) {
+    constexpr int R = P::radix(S_), S = P::inner(S_), L = P::L, H = L / 2 + 1;
+    constexpr int NB = L / R, ITEMS = NB * H, TRIPS = (ITEMS + NT - 1) / NT;
+    constexpr int TWS = L / (R * S);
+#pragma unroll 1
+    for (int it = 0; it < TRIPS; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (ITEMS % NT != 0 && i >= ITEMS) break;
+        const int col = i % H, b = i / H;
+        const int hi = b / S, lo = b - hi * S;
+        const int base = hi * R * S + lo;
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = buf[(base + k * S) * H + col];
+        FastDft<-1, R>::run(v);
+        if constexpr (S > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], tw[lo * k * TWS]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (OUT_G) gout.st(col, P::natural(base + k * S), v[k]);
+            else buf[(base + k * S) * H + col] = v[k];
+        }
+    }
+}
+
+template <class P, int NT>
+__global__ void __launch_bounds__(NT, 2) k_xy_fast(const GridDev* __restrict__ grids, const Chunk* __restrict__ chunks,
+                                                   const int64_t* const* __restrict__ gmf,
+                                                   const float2* __restrict__ tw_arena, float2* __restrict__ wsB,
+                                                   int F) {
+    constexpr int L = P::L, H = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_fast[];
+    float2* buf = reinterpret_cast<float2*>(smem_fast);   // L x H
+    float2* tw = buf + L * H;
+    const Chunk ch = chunks[blockIdx.x];
+    const GridDev& g = grids[ch.grid];
+    const int z = ch.tile;
+    const int G0 = g.G[0], G1 = g.G[1];
+    const int nl = (G1 + 1) / 2;
+    for (int t = threadIdx.x; t < L; t += NT) tw[t] = tw_arena[g.fx.tw_off + t];
+    // rows 2 nl .. L-1 are the y transform's zero padding
+    for (int t = threadIdx.x + 2 * nl * H; t < L * H; t += NT) buf[t] = make_float2(0.f, 0.f);
+    XyIn<L> gin;
+    gin.p = gmf[ch.grid] + (long long)z * G1 * G0;
+    gin.G0 = G0;
+    gin.G1 = G1;
+    gin.scale = pow2_neg<float>(F);
+    __syncthreads();   // twiddles
+    xy_x_stage<P, 0, NT, true, 2 * H>(buf, tw, gin, nl);
+    __syncthreads();
+    xy_x_stage<P, 1, NT, false, 2 * H>(buf, tw, gin, nl);
+    if constexpr (P::NST == 3) {
+        __syncthreads();
+        xy_x_stage<P, 2, NT, false, 2 * H>(buf, tw, gin, nl);
+    }
+    __syncthreads();
+    // separation, one warp per line (its storage is touched by no other warp)
+    {
+        constexpr int KR = (H + 31) / 32;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int p = warp; p < nl; p += NT / 32) {
+            float2* lb = buf + p * 2 * H;
+            float2 za[KR], zb[KR];
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int k = lane + 32 * r;
+                if (k < H) {
+                    za[r] = lb[P::position(k)];
+                    zb[r] = lb[P::position(k == 0 ? 0 : L - k)];
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int k = lane + 32 * r;
+                if (k < H) {
+                    const float2 zz = za[r], zm = zb[r];
+                    lb[k] = make_float2(0.5f * (zz.x + zm.x), 0.5f * (zz.y - zm.y));
+                    // row G1 of an odd G1 is zero padding, exactly
+                    lb[H + k] = 2 * p + 1 < G1 ? make_float2(0.5f * (zz.y + zm.y), 0.5f * (zm.x - zz.x))
+                                               : make_float2(0.f, 0.f);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    XyOut<L> gout;
+    gout.p = wsB + (g.wsB + (long long)z * L * g.Hx);
+    gout.Hx = g.Hx;
+    const NoIO none;
+    xy_y_stage<P, 0, NT, false>(buf, tw, none);
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        xy_y_stage<P, 1, NT, false>(buf, tw, none);
+        __syncthreads();
+        xy_y_stage<P, 2, NT, true>(buf, tw, gout);
+    } else {
+        xy_y_stage<P, 1, NT, true>(buf, tw, gout);
+    }
+}
+
+// ---- fused y + x inverse over one window plane ------------------------------------
+// The inverse of k_xy_fast's pair, for grids with M0 = M1 = L: one CTA takes
+// the z pass's output plane A[zw][ky][kx] (L x H), runs the y inverse over its
+// H columns and the C2R x inverse of its window row pairs in the same shared
+// plane, and writes only the window phi_short[zw][yw][xw] to HBM.
+//  - y: decimation-in-frequency inverse stages (conjugate twiddles) over the
+//    columns, the first reading natural ky from HBM; the rows end in
+//    digit-reversed order: natural row y sits at row position(y);
+//  - x lines: window rows 2p, 2p+1 are natural rows ya, yb at plane rows
+//    ra = position(ya), rb = position(yb); line p's element e lives at
+//    (ra, e) for e < H and at (rb, e - H) beyond; one warp per line builds it
+//    in place, Z_k = A_k + i B_k and Z_{L-k} = conj A_k + i conj B_k;
+//  - x: decimation-in-frequency inverse stages on the lines (butterflies on
+//    consecutive threads), the last writing the window cells of rows 2p and
+//    2p + 1 times 1/(M0 M1 M2).
+template <int L> struct YxIn {
+    const float2* __restrict__ p;    // A row ky = 0 of this plane, column 0
+    int Hx;
+    __device__ __forceinline__ float2 ld(int col, int ky) const { return p[ky * Hx + col]; }
+};
+
+// one DIF stage of the y columns with DIR and an optional HBM input
+template <class P, int S_, int NT, bool IN_G, int DIR, class GIN>
+__device__ __forceinline__ void yx_y_stage(float2* buf, const float2* __restrict__ tw, const GIN& gin) {
+    constexpr int R = P::radix(S_), S = P::inner(S_), L = P::L, H = L / 2 + 1;
+    constexpr int NB = L / R, ITEMS = NB * H, TRIPS = (ITEMS + NT - 1) / NT;
+    constexpr int TWS = L / (R * S);
+#pragma unroll 1
+    for (int it = 0; it < TRIPS; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (ITEMS % NT != 0 && i >= ITEMS) break;
+        const int col = i % H, b = i / H;
+        const int hi = b / S, lo = b - hi * S;
+        const int base = hi * R * S + lo;
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if constexpr (IN_G) v[k] = gin.ld(col, base + k * S);
+            else v[k] = buf[(base + k * S) * H + col];
+        }
+        FastDft<DIR, R>::run(v);
+        if constexpr (S > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, DIR>(tw, lo * k * TWS));
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) buf[(base + k * S) * H + col] = v[k];
+    }
+}
+
+// the plane rows of window row pair p (natural rows (s0 + 2p) mod L and the next)
+template <class P>
+__device__ __forceinline__ void yx_rows(int p, int s0, int& ra, int& rb) {
+    constexpr int L = P::L;
+    int ya = s0 + 2 * p;
+    while (ya >= L) ya -= L;
+    int yb = ya + 1;
+    if (yb >= L) yb -= L;
+    ra = P::position(ya);
+    rb = P::position(yb);
+}
+
+// one DIF inverse stage of the x lines (split rows ra | rb, butterflies on
+// consecutive threads); the last stage writes the window
+template <class P, int S_, int NT, bool OUT_G>
+__device__ __forceinline__ void yx_x_stage(float2* buf, const float2* __restrict__ tw, int nl, int s0y, int s0x,
+                                           float* __restrict__ out, int W0, int W1, float norm) {
+    constexpr int R = P::radix(S_), S = P::inner(S_), L = P::L, H = L / 2 + 1;
+    constexpr int NB = L / R;
+    constexpr int TWS = L / (R * S);
+    const int items = NB * nl;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < items; i += NT) {
+        const int line = i / NB, b = i - line * NB;
+        const int hi = b / S, lo = b - hi * S;
+        const int base = hi * R * S + lo;
+        int ra, rb;
+        yx_rows<P>(line, s0y, ra, rb);
+        float2 v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int e = base + k * S;
+            v[k] = e < H ? buf[ra * H + e] : buf[rb * H + e - H];
+        }
+        FastDft<1, R>::run(v);
+        if constexpr (S > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, 1>(tw, lo * k * TWS));
+        }
+        if constexpr (OUT_G) {
+            float* r0 = out + (long long)(2 * line) * W0;
+            const bool has1 = 2 * line + 1 < W1;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                int w = P::natural(base + k * S) - s0x;
+                if (w < 0) w += L;
+                for (; w < W0; w += L) {
+                    r0[w] = v[k].x * norm;
+                    if (has1) r0[W0 + w] = v[k].y * norm;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int e = base + k * S;
+                if (e < H) buf[ra * H + e] = v[k];
+                else buf[rb * H + e - H] = v[k];
+            }
+        }
+    }
+}
+
+template <class P, int NT>
+__global__ void __launch_bounds__(NT, 2) k_yx_fast(const GridDev* __restrict__ grids, const Chunk* __restrict__ chunks,
+                                                   const float2* __restrict__ tw_arena,
+                                                   const float2* __restrict__ wsA, void* const* __restrict__ phis,
+                                                   int comp) {
+    constexpr int L = P::L, H = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_fast[];
+    float2* buf = reinterpret_cast<float2*>(smem_fast);   // L x H
+    float2* tw = buf + L * H;
+    const Chunk ch = chunks[blockIdx.x];
+    const GridDev& g = grids[ch.grid];
+    const int zw = ch.tile;
+    const int W0 = g.W[0], W1 = g.W[1];
+    const int nl = (W1 + 1) / 2;
+    for (int t = threadIdx.x; t < L; t += NT) tw[t] = tw_arena[g.fx.tw_off + t];
+    YxIn<L> gin;
+    gin.p = wsA + (g.wsA + (long long)zw * L * g.Hx);
+    gin.Hx = g.Hx;
+    __syncthreads();   // twiddles
+    yx_y_stage<P, 0, NT, true, 1>(buf, tw, gin);
+    __syncthreads();
+    yx_y_stage<P, 1, NT, false, 1>(buf, tw, gin);
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        yx_y_stage<P, 2, NT, false, 1>(buf, tw, gin);
+        __syncthreads();
+    }
+    // the window's row pairs as complex lines, one warp per line
+    const int s0y = g.s0[1], s0x = g.s0[0];
+    {
+        constexpr int KR = (H + 31) / 32;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int p = warp; p < nl; p += NT / 32) {
+            int ra, rb;
+            yx_rows<P>(p, s0y, ra, rb);
+            const bool has1 = 2 * p + 1 < W1;
+            float2 av[KR], bv[KR];
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int k = lane + 32 * r;
+                if (k < H) {
+                    av[r] = buf[ra * H + k];
+                    bv[r] = has1 ? buf[rb * H + k] : make_float2(0.f, 0.f);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int k = lane + 32 * r;
+                if (k < H) {
+                    const float2 a = av[r], bb = bv[r];
+                    buf[ra * H + k] = make_float2(a.x - bb.y, a.y + bb.x);            // element k
+                    if (k > 0 && L - k >= H)                                         // element L - k
+                        buf[rb * H + (L - k - H)] = make_float2(a.x + bb.y, bb.x - a.y);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    float* out = reinterpret_cast<float*>(phis[ch.grid]) + (long long)comp * g.W[0] * g.W[1] * g.W[2] +
+                 (long long)zw * W1 * W0;
+    const float norm = (float)g.inv_m3;
+    yx_x_stage<P, 0, NT, false>(buf, tw, nl, s0y, s0x, out, W0, W1, norm);
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        yx_x_stage<P, 1, NT, false>(buf, tw, nl, s0y, s0x, out, W0, W1, norm);
+        __syncthreads();
+        yx_x_stage<P, 2, NT, true>(buf, tw, nl, s0y, s0x, out, W0, W1, norm);
+    } else {
+        yx_x_stage<P, 1, NT, true>(buf, tw, nl, s0y, s0x, out, W0, W1, norm);
+    }
+}
+
 }  // namespace
 }  // namespace apm

@@ -37,15 +37,25 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
     const int r0 = c.tile * g.rows_gas;
     const int r1 = min(nrows, r0 + g.rows_gas);
     const GridDev* p = par ? &pgrids[g.parent] : nullptr;
+    if (!own && !par) {
+        // no baryons: the CTA's rows are one flat range of zeros, written as
+        // 16-byte stores when the range starts 16-byte aligned
+        int64_t* __restrict__ z = out + (long long)r0 * G0;
+        const long long n = (long long)(r1 - r0) * G0;
+        long long i0 = 0;
+        if ((reinterpret_cast<size_t>(z) & 15) == 0) {
+            longlong2* __restrict__ z2 = reinterpret_cast<longlong2*>(z);
+            for (long long i = threadIdx.x; i < n / 2; i += blockDim.x) z2[i] = make_longlong2(0, 0);
+            i0 = n & ~1LL;
+        }
+        for (long long i = i0 + threadIdx.x; i < n; i += blockDim.x) z[i] = 0;
+        return;
+    }
     int last = -1, cy = 0, cz = 0;
     bool yz_in = false;
     for (RowWalk it(r0, G0); it.r < r1; it.next()) {
         const int r = it.r, x = it.x;
         int64_t* row = out + (long long)r * G0;
-        if (!own && !par) {
-            row[x] = 0;
-            continue;
-        }
         if (r != last) {
             last = r;
             cy = r % G1 - B;

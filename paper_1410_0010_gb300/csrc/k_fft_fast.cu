@@ -50,14 +50,55 @@ cudaError_t configure_one() {
                                 (int)smem_of<L>());
 }
 
+// the fused x + y forward (x-forward unit only), for the lengths whose plane
+// fits the shared-memory limit
+template <int L, int A, int B, int Cc>
+constexpr bool xy_fits() { return (size_t)(L * (L / 2 + 1) + L) * 8 <= (size_t)kFftSmemLimit; }
+
+template <int L, int A, int B, int Cc>
+cudaError_t configure_xy() {
+    if constexpr (kFastMode == 3 && xy_fits<L, A, B, Cc>())
+        return cudaFuncSetAttribute(k_xy_fast<FastPlan<A, B, Cc>, kFastXyThreads>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_xy_smem(L));
+    if constexpr (kFastMode == 4 && xy_fits<L, A, B, Cc>())
+        return cudaFuncSetAttribute(k_yx_fast<FastPlan<A, B, Cc>, kFastXyThreads>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_xy_smem(L));
+    return cudaSuccess;
+}
+
 cudaError_t configure_fast() {
     cudaError_t e = cudaSuccess;
 #define APM_FAST_CASE(LL, A, B, C) \
-    if (e == cudaSuccess) e = configure_one<LL, A, B, C>();
+    if (e == cudaSuccess) e = configure_one<LL, A, B, C>(); \
+    if (e == cudaSuccess) e = configure_xy<LL, A, B, C>();
     APM_FAST_LENGTHS(APM_FAST_CASE)
 #undef APM_FAST_CASE
     return e;
 }
+
+#if APM_FAST_MODE == 4
+template <int L, int A, int B, int Cc>
+cudaError_t launch_yx_one(const FftArgs& a, void* const* phis, cudaStream_t s) {
+    if constexpr (xy_fits<L, A, B, Cc>()) {
+        k_yx_fast<FastPlan<A, B, Cc>, kFastXyThreads><<<a.n_chunks, kFastXyThreads, fast_xy_smem(L), s>>>(
+            a.g, a.chunks, (const float2*)a.tw, (const float2*)a.wsA, phis, a.comp);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+#endif
+
+#if APM_FAST_MODE == 3
+template <int L, int A, int B, int Cc>
+cudaError_t launch_xy_one(const FftArgs& a, const int64_t* const* gmf, cudaStream_t s) {
+    if constexpr (xy_fits<L, A, B, Cc>()) {
+        k_xy_fast<FastPlan<A, B, Cc>, kFastXyThreads><<<a.n_chunks, kFastXyThreads, fast_xy_smem(L), s>>>(
+            a.g, a.chunks, gmf, (const float2*)a.tw, (float2*)a.wsB, a.F);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+#endif
 
 cudaError_t launch_fast(int L, const FftArgs& a, const int64_t* const* gmf, void* const* phis, cudaStream_t s) {
     if (a.n_chunks <= 0) return cudaSuccess;
@@ -86,11 +127,31 @@ cudaError_t launch_fft_yi_fast(int L, const FftArgs& a, cudaStream_t s) {
 }
 #elif APM_FAST_MODE == 3
 cudaError_t fft_configure_fast_xf() { return configure_fast(); }
+cudaError_t launch_fft_xy_fast(int L, const FftArgs& a, const int64_t* const* gmf, cudaStream_t s) {
+    if (a.n_chunks <= 0) return cudaSuccess;
+    switch (L) {
+#define APM_FAST_CASE(LL, A, B, C) \
+    case LL: return launch_xy_one<LL, A, B, C>(a, gmf, s);
+        APM_FAST_LENGTHS(APM_FAST_CASE)
+#undef APM_FAST_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
 cudaError_t launch_fft_xf_fast(int L, const FftArgs& a, const int64_t* const* gmf, cudaStream_t s) {
     return launch_fast(L, a, gmf, nullptr, s);
 }
 #else
 cudaError_t fft_configure_fast_xi() { return configure_fast(); }
+cudaError_t launch_fft_yx_fast(int L, const FftArgs& a, void* const* phis, cudaStream_t s) {
+    if (a.n_chunks <= 0) return cudaSuccess;
+    switch (L) {
+#define APM_FAST_CASE(LL, A, B, C) \
+    case LL: return launch_yx_one<LL, A, B, C>(a, phis, s);
+        APM_FAST_LENGTHS(APM_FAST_CASE)
+#undef APM_FAST_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
 cudaError_t launch_fft_xi_fast(int L, const FftArgs& a, void* const* phis, cudaStream_t s) {
     return launch_fast(L, a, nullptr, phis, s);
 }

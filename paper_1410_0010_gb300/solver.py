@@ -245,6 +245,19 @@ class Solver:
         sh.packing = int(shapes.get("packing", cur["packing"]))
         check(lib().apm_set_fft_shapes(self._ctx, level, ctypes.byref(sh)), "apm_set_fft_shapes")
 
+    def pass_kernels(self, level):
+        """Per FFT pass (x fwd, y fwd, z, y inv, x inv), the kernel each grid of
+        the level runs (in level_grids[level] order): 0 runtime plan, 1
+        compile-time plan, 2 fused plane kernel (x and y passes together), 3
+        none (done by the fused kernel)."""
+        n = len(self.level_grids[level])
+        out = []
+        for q in range(5):
+            kinds = (ctypes.c_int32 * n)()
+            check(lib().apm_get_pass_kernels(self._ctx, level, q, kinds, n), "apm_get_pass_kernels")
+            out.append(list(kinds))
+        return out
+
     def shape_key(self, level):
         """Autotuner cache key of a level: GPU name, precision and every grid's
         FFT lengths, GMF box and window (what the pass shapes depend on)."""

@@ -94,10 +94,12 @@ def test_algorithmic_bytes_per_operator():
     M = (30, 30, 30)
     E = (N + 2,) * 3
 
-    def solver(h, comps):
+    def solver(h, comps, fused=False):
         W = (N + 2 * h,) * 3
         info = [dict(gmf=G, fft=M, phi_short=W, field=E, comps=comps)]
-        return types.SimpleNamespace(level_grids=[[0]], info=info, n_levels=1), W
+        kinds = [[2], [3], [1], [3], [2]] if fused else [[1]] * 5
+        return types.SimpleNamespace(level_grids=[[0]], info=info, n_levels=1,
+                                     pass_kernels=lambda lev: kinds), W
     w = types.SimpleNamespace(n_particles=0, gas=None, grids=[types.SimpleNamespace(dims=(N, N, N))])
     csz, rsz = 8, 4
     Hx = M[0] // 2 + 1
@@ -116,3 +118,12 @@ def test_algorithmic_bytes_per_operator():
     for k in ("gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd"):
         assert asp[k] == a2[k] == a4[k], k
     assert a2["fft_x_fwd"] == 8 * int(np.prod(G)) + csz * G[1] * G[2] * Hx
+    # the fused plane kernels: the x spectrum between the x and y passes (and
+    # the y inverse's output between the y and x inverse) never reaches HBM
+    sf, Wf = solver(2, 1, fused=True)
+    af = b.algorithmic_bytes(sf, w, [0], csz, rsz, True)
+    assert af["fft_y_fwd"] == af["fft_y_inv"] == 0
+    assert af["fft_x_fwd"] == 8 * int(np.prod(G)) + csz * G[2] * M[1] * Hx
+    assert af["fft_x_inv"] == csz * Wf[2] * M[1] * Hx + rsz * int(np.prod(Wf))
+    assert af["fft_z_green"] == a2["fft_z_green"]
+    assert af["fft_x_fwd"] + af["fft_y_fwd"] < a2["fft_x_fwd"] + a2["fft_y_fwd"]

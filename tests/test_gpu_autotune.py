@@ -112,7 +112,7 @@ def test_runtime_plans_and_radix_stay_within_tolerance():
     pacc = torch.zeros((3, P.n), dtype=s.dtype, device="cuda")
     s.step(P, 1e-3, bufs, pacc)
     ref = _fields(bufs)
-    for plan, radix in (([1] * 5, 16), ([1] * 5, 8), ([0, 1, 0, 1, 0], 8)):
+    for plan, radix in (([1] * 5, 16), ([1] * 5, 8), ([0, 1, 0, 1, 0], 8), ([2, 0, 0, 0, 2], 16)):
         for lev in range(s.n_levels):
             sh = s.fft_shapes(lev)
             sh.update(plan=plan, max_radix=radix)
@@ -127,12 +127,12 @@ def test_shape_validation_and_roundtrip():
     from paper_1410_0010_gb300._lib import ApmError
     s, _ = _setup("fp32")
     sh = {"budget": [512, 1024, 2048, 4096, 8192], "threads": [128, 256, 128, 256, 128],
-          "plan": [0, 1, 0, 1, 1], "max_radix": 8, "packing": 1}
+          "plan": [2, 1, 0, 1, 2], "max_radix": 8, "packing": 1}
     s.set_fft_shapes(1, sh)
     assert s.fft_shapes(1) == sh
     base = {"budget": [2048] * 5, "threads": [256] * 5, "plan": [0] * 5, "max_radix": 16, "packing": 0}
     for bad in ({"budget": [0] * 5}, {"threads": [48] * 5}, {"threads": [512] * 5}, {"threads": [64] * 5},
-                {"plan": [2] * 5}, {"max_radix": 12}, {"packing": 2}):
+                {"plan": [3] * 5}, {"plan": [0, 2, 0, 0, 0]}, {"max_radix": 12}, {"packing": 2}):
         with pytest.raises(ApmError):
             s.set_fft_shapes(1, dict(base, **bad))
     assert s.fft_shapes(1) == sh
