@@ -26,7 +26,11 @@
  *    context's precision is APM_FP32 and double for APM_FP64.
  *  - `stream` is a cudaStream_t (NULL: the legacy default stream).  Calls are
  *    asynchronous on it; calls on one context must be ordered (one stream, or
- *    synchronised by the caller).  A context is not thread-safe.
+ *    synchronised by the caller).  A context is not thread-safe.  Within a
+ *    call, an FFT pass whose grids run different kernels spreads them over the
+ *    context's three auxiliary streams, forked from `stream` and joined back
+ *    to it with events: the work stays ordered on `stream`, and a capture of
+ *    `stream` takes the branches in.
  *  - Errors detectable on the host are returned immediately and nothing is
  *    enqueued.  Errors the kernels detect (fixed-point overflow, a particle
  *    outside an isolated box, a wait that ran out) are latched in a device

@@ -118,6 +118,13 @@ struct apm_ctx {
     void** d_tabs = nullptr;         // [role][level]: each level's device pointer table of the role
     Profiler prof;
     bool batched = true;             // apm_set_grid_batching
+    // auxiliary streams on which the segments of one FFT pass (grids of
+    // different kernels) run side by side, forked from and joined to the
+    // caller's stream with events
+    static constexpr int kAux = 3;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kAux] = {};
     std::vector<cudaGraphExec_t> graphs;   // apm_graph_end (null: destroyed)
     // particle processing order (apm_reserve_order / apm_order_particles)
     struct Order {
@@ -529,11 +536,27 @@ cudaError_t run_pass(apm_ctx* c, const Level& L, int q, const PassPlan& P, void*
         const PassSeg& sg = P.seg[P.seg_of[grid]];
         return run_seg(c, L, q, P, sg, P.first[grid], P.count[grid], d_gmf, d_phis, s, comp);
     }
-    for (const PassSeg& sg : P.seg) {
-        cudaError_t e = run_seg(c, L, q, P, sg, sg.first, sg.count, d_gmf, d_phis, s, comp);
-        if (e != cudaSuccess) return e;
+    const int nseg = (int)P.seg.size();
+    if (nseg <= 1) return nseg ? run_seg(c, L, q, P, P.seg[0], P.seg[0].first, P.seg[0].count, d_gmf, d_phis, s, comp)
+                               : cudaSuccess;
+    // the segments write disjoint grids: segment 0 on the caller's stream, the
+    // others round-robin on the auxiliary streams, so that one segment's last
+    // partial wave overlaps the next one's CTAs
+    const int used = std::min(nseg - 1, apm_ctx::kAux);
+    cudaError_t e = cudaEventRecord(c->ev_fork, s);
+    for (int j = 0; j < used && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->aux[j], c->ev_fork, 0);
+    for (int i = 0; i < nseg && e == cudaSuccess; ++i) {
+        const PassSeg& sg = P.seg[i];
+        e = run_seg(c, L, q, P, sg, sg.first, sg.count, d_gmf, d_phis, i == 0 ? s : c->aux[(i - 1) % used], comp);
     }
-    return cudaSuccess;
+    // joined even after a failed launch, so that no auxiliary stream stays
+    // forked from a capturing stream
+    for (int j = 0; j < used; ++j) {
+        const cudaError_t e1 = cudaEventRecord(c->ev_join[j], c->aux[j]);
+        const cudaError_t e2 = cudaStreamWaitEvent(s, c->ev_join[j], 0);
+        if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    return e;
 }
 
 // Uploads the device pointers of one role if they changed since the last call.
@@ -678,15 +701,23 @@ apm_status apm_create(const apm_config* cfg, apm_ctx** out) {
         delete c;
         return APM_E_CUDA;
     }
+    bool aux_ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; j < apm_ctx::kAux && aux_ok; ++j)
+        aux_ok = cudaStreamCreateWithFlags(&c->aux[j], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_join[j], cudaEventDisableTiming) == cudaSuccess;
+    if (!aux_ok) {
+        cudaGetLastError();
+        apm_destroy(c);
+        return APM_E_CUDA;
+    }
     if (fault_alloc() || cudaMalloc((void**)&c->d_status, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
-        delete c;
+        apm_destroy(c);
         return fault_alloc() ? APM_E_NOMEM : APM_E_CUDA;
     }
     if (cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess || fft_configure() != cudaSuccess) {
-        cudaFree(c->d_status);
         cudaGetLastError();
-        delete c;
+        apm_destroy(c);
         return APM_E_CUDA;
     }
     *out = c;
@@ -697,6 +728,11 @@ void apm_destroy(apm_ctx* c) {
     if (!c) return;
     free_hierarchy(c);
     profile_free(c->prof);
+    for (int j = 0; j < apm_ctx::kAux; ++j) {
+        if (c->aux[j]) cudaStreamDestroy(c->aux[j]);
+        if (c->ev_join[j]) cudaEventDestroy(c->ev_join[j]);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->d_status) cudaFree(c->d_status);
     delete c;
 }
