@@ -209,41 +209,51 @@ def kernel_source_hash():
 
 
 def ncu_label(name):
-    """bench.py's kernel label of an ncu kernel name (the column passes by their
-    template arguments <T, axis, mode, threads>), or None."""
+    """bench.py's kernel label of an ncu kernel name, or None.  The column passes
+    (runtime k_col<T, axis, mode, threads> and compile-time-planned
+    k_col_fast<plan, axis, mode, lines, threads>) by their axis and mode; the
+    fused plane kernels by the x pass they stand in for."""
     import re
-    m = re.search(r"k_([a-z_]+)(<[^>]*>)?\(", name)
+    name = name.replace("<unnamed>", "")   # anonymous-namespace markers
+    m = re.search(r"\bk_([a-z_]+)[<(]", name)
     if not m:
         return None
-    base, targs = m.group(1), m.group(2) or ""
-    if base == "col":
-        a = [t.strip() for t in targs.strip("<>").split(",")]
+    base = m.group(1)
+    if base in ("col", "col_fast"):
+        rest = re.sub(r"FastPlan<[^>]*>", "P", name[m.end():])
+        a = [t.strip() for t in rest.split(">")[0].split(",")]
         return {("1", "0"): "fft_y_fwd", ("2", "1"): "fft_z_green", ("1", "2"): "fft_y_inv",
                 ("2", "3"): "fft_z_green"}.get((a[1], a[2])) if len(a) >= 3 else None
-    return {"gas_init": "gas_init", "deposit_levels": "tsc_deposit", "xf": "fft_x_fwd", "xi": "fft_x_inv",
-            "accel": "accel_carry", "interp_levels": "tsc_interp"}.get(base)
+    return {"gas_init": "gas_init", "deposit_levels": "tsc_deposit", "deposit": "tsc_deposit",
+            "xf": "fft_x_fwd", "xf_fast": "fft_x_fwd", "xy_fast": "fft_x_fwd",
+            "xi": "fft_x_inv", "xi_fast": "fft_x_inv", "yx_fast": "fft_x_inv",
+            "accel": "accel_carry", "accel_var": "accel_carry", "interp_levels": "tsc_interp",
+            "interp": "tsc_interp"}.get(base)
 
 
-def write_traffic(csv_path, small="c5s", full="c5", scale=8):
-    """profiles/traffic.json from an ncu --csv capture of one step of the `small`
-    workload (dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over
-    the step's launches of each kernel), with the per-launch figures scaled by
-    `scale` for the `full` workload and the sha256 of the current sources."""
+def write_traffic(csv_paths, small="c5s", full="c5", scale=8):
+    """profiles/traffic.json from ncu --csv captures (one or more files, comma
+    separated) of the `small` workload: dram__bytes_read.sum +
+    dram__bytes_write.sum per launch, mean over the captured launches of each
+    kernel label, with the per-launch figures scaled by `scale` for the `full`
+    workload and the sha256 of the current sources."""
     import csv
-    rows = list(csv.reader(open(csv_path)))
-    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
-    H = rows[hdr]
-    ki, mi, vi, ui, ii = (H.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
     unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
     per = {}
-    for r in rows[hdr + 1:]:
-        if len(r) <= vi or not r[mi].startswith("dram__bytes_"):
-            continue
-        label = ncu_label(r[ki])
-        if label is None:
-            continue
-        d = per.setdefault(label, {})
-        d[int(r[ii])] = d.get(int(r[ii]), 0.0) + float(r[vi].replace(",", "")) * unit.get(r[ui], 1)
+    for fi, csv_path in enumerate(csv_paths.split(",")):
+        rows = list(csv.reader(open(csv_path)))
+        hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+        H = rows[hdr]
+        ki, mi, vi, ui, ii = (H.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
+        for r in rows[hdr + 1:]:
+            if len(r) <= vi or not r[mi].startswith("dram__bytes_"):
+                continue
+            label = ncu_label(r[ki])
+            if label is None:
+                continue
+            d = per.setdefault(label, {})
+            key = (fi, int(r[ii]))
+            d[key] = d.get(key, 0.0) + float(r[vi].replace(",", "")) * unit.get(r[ui], 1)
     import apm_inputs as W
     ws, wf = W.NAMES[small], W.NAMES[full]
     out = {}
@@ -252,9 +262,9 @@ def write_traffic(csv_path, small="c5s", full="c5", scale=8):
         out[f"{ws}:{label}"] = int(round(mean))
         out[f"{wf}:{label}"] = int(round(mean * scale))
     doc = {"source_sha256": kernel_source_hash(),
-           "note": ("dram__bytes_read.sum + dram__bytes_write.sum per launch (mean over the launches of one "
-                    f"step), captured on {ws} and scaled x{scale} to {wf} ({scale}x the cells, grids and "
-                    f"particles per launch); the {ws} values are kept as measured"),
+           "note": ("dram__bytes_read.sum + dram__bytes_write.sum per launch (mean over the captured launches "
+                    f"of each kernel label), captured on {ws} and scaled x{scale} to {wf} ({scale}x the cells, "
+                    f"grids and particles per launch); the {ws} values are kept as measured"),
            "per_launch_bytes": out}
     path = os.path.join(ROOT, "profiles", "traffic.json")
     with open(path, "w") as f:
@@ -791,8 +801,8 @@ def main():
                     help="skip timing the plain per-grid launch path (FP64 and FP32)")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
-    ap.add_argument("--write-traffic", metavar="CSV",
-                    help="write profiles/traffic.json from an ncu --csv capture of one c5s step, then exit")
+    ap.add_argument("--write-traffic", metavar="CSV[,CSV...]",
+                    help="write profiles/traffic.json from ncu --csv captures of c5s launches, then exit")
     ap.add_argument("--no-evolution", action="store_true", help="skip timing the evolution timestep")
     ap.add_argument("--gradient", choices=["fd2", "fd4", "spectral"], default="fd2",
                     help="the gradient operator of the measured solve (default: the two-point difference)")

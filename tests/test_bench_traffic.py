@@ -28,6 +28,16 @@ def test_kernel_names_map_to_labels():
     assert b.ncu_label("void unnamed>::k_accel<float>(LevelDev, const GridDev *)") == "accel_carry"
     assert b.ncu_label("void unnamed>::k_interp_levels<float>(const LevelDev *, int)") == "tsc_interp"
     assert b.ncu_label("void at::native::vectorized_elementwise_kernel<4>(int)") is None
+    fast = "void apm::<unnamed>::k_col_fast<apm::<unnamed>::FastPlan<15, 10, 1>, {}, {}, 16, 80>(const GridDev *)"
+    assert b.ncu_label(fast.format(1, 0)) == "fft_y_fwd"
+    assert b.ncu_label(fast.format(2, 1)) == "fft_z_green"
+    assert b.ncu_label(fast.format(1, 2)) == "fft_y_inv"
+    plan = "apm::<unnamed>::FastPlan<8, 8, 8>, "
+    assert b.ncu_label(f"void apm::<unnamed>::k_xf_fast<{plan}16, 256>(const GridDev *)") == "fft_x_fwd"
+    assert b.ncu_label(f"void apm::<unnamed>::k_xi_fast<{plan}16, 256>(const GridDev *)") == "fft_x_inv"
+    assert b.ncu_label(f"void apm::<unnamed>::k_xy_fast<{plan}384>(const GridDev *)") == "fft_x_fwd"
+    assert b.ncu_label(f"void apm::<unnamed>::k_yx_fast<{plan}384>(const GridDev *)") == "fft_x_inv"
+    assert b.ncu_label("apm::<unnamed>::k_order_bins(LevelDev, Particles)") is None
 
 
 def test_write_traffic_averages_scales_and_stamps(tmp_path, monkeypatch):
