@@ -214,7 +214,9 @@ def ncu_label(name):
     k_col_fast<plan, axis, mode, lines, threads>) by their axis and mode; the
     fused plane kernels by the x pass they stand in for."""
     import re
-    name = name.replace("<unnamed>", "")   # anonymous-namespace markers
+    # anonymous-namespace markers: "ns::<unnamed>::" (demangled) or
+    # "unnamed>::" (ncu's CSV)
+    name = name.replace("::<unnamed>::", "::").replace("unnamed>::", "")
     m = re.search(r"\bk_([a-z_]+)[<(]", name)
     if not m:
         return None
@@ -437,12 +439,15 @@ def run_apm(args):
     w = workload(args.workload)
     levels = list(range(1 + max(g.level for g in w.grids))) if w.solve_levels is None else w.solve_levels
 
+    # auto: measured below (with and without the order, after tuning); the
+    # other legs follow the choice
     use_order = args.order == "on" or (args.order == "auto" and not w.spatial_order)
+    order_note = args.order
 
-    def make(precision, gradient=args.gradient, order=use_order):
+    def make(precision, gradient=args.gradient, order=None):
         s = Solver(w.grids, periodic=w.periodic, precision=precision,
                    mass_frac_bits=w.mass_frac_bits, device=local, gradient=gradient)
-        if order:    # the particle processing order, recomputed every step (apm_order_particles)
+        if use_order if order is None else order:   # the particle processing order, recomputed every step
             s.reserve_order(w.n_particles)
         return s, s.alloc_all()
 
@@ -482,6 +487,21 @@ def run_apm(args):
     for _ in range(args.warmup):
         step32()
     s32.sync_status()
+    if args.order == "auto" and not w.spatial_order:
+        # the order costs a sort per step and pays in the particle kernels only
+        # where the caller's order is incoherent: five eager steps each way
+        def t_order(on):
+            s32.reserve_order(n if on else 0)
+            for _ in range(2):
+                step32()
+            return timed(step32, 5)
+        t_on, t_off = t_order(True), t_order(False)
+        use_order = t_on < t_off
+        s32.reserve_order(n if use_order else 0)
+        order_note = f"auto: {t_on:.3f} ms per eager step with the order, {t_off:.3f} without"
+        for _ in range(2):
+            step32()
+        s32.sync_status()
     graph = None
     try:   # the step as a library-owned CUDA graph (apm_graph_begin / apm_graph_end)
         graph = s32.capture(step32)
@@ -740,7 +760,7 @@ def run_apm(args):
                    "interior_cells": cells, "particles": n, "periodic": w.periodic,
                    "l2": "inputs larger than L2 (no flush)", "cuda_graph": used_graph,
                    "parallelism": f"replicas x{world}", "gradient": args.gradient,
-                   "particle_order": "on" if use_order else "off",
+                   "particle_order": "on" if use_order else "off", "particle_order_choice": order_note,
                    "fft_shapes": shapes32},
         "particles_per_s": job_rate(ranks, n, ms) * 1e6,
         "roofline": roofline,
@@ -795,8 +815,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--order", choices=["auto", "on", "off"], default="auto",
                     help="sort the particles by root-level bin every step before the particle kernels "
-                         "(apm_order_particles; results are bit-identical either way); auto: unless the "
-                         "workload stores its particles in spatial order (the Zel'dovich lattice)")
+                         "(apm_order_particles; results are bit-identical either way); auto: off when the "
+                         "workload stores its particles in spatial order (the Zel'dovich lattice), otherwise "
+                         "the faster of five eager steps with and without it")
     ap.add_argument("--no-per-grid", action="store_true",
                     help="skip timing the plain per-grid launch path (FP64 and FP32)")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")

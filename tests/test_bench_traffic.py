@@ -38,6 +38,11 @@ def test_kernel_names_map_to_labels():
     assert b.ncu_label(f"void apm::<unnamed>::k_xy_fast<{plan}384>(const GridDev *)") == "fft_x_fwd"
     assert b.ncu_label(f"void apm::<unnamed>::k_yx_fast<{plan}384>(const GridDev *)") == "fft_x_inv"
     assert b.ncu_label("apm::<unnamed>::k_order_bins(LevelDev, Particles)") is None
+    # ncu's CSV writes the anonymous namespace as "unnamed>::"
+    assert b.ncu_label("void unnamed>::k_xf_fast<unnamed>::FastPlan<16, 16, 1>, 16, 256>(const GridDev *)") \
+        == "fft_x_fwd"
+    assert b.ncu_label("void unnamed>::k_col_fast<unnamed>::FastPlan<15, 10, 1>, 2, 1, 16, 80>(int)") \
+        == "fft_z_green"
 
 
 def test_write_traffic_averages_scales_and_stamps(tmp_path, monkeypatch):
