@@ -441,7 +441,8 @@ def run_apm(args):
 
     # auto: measured below (with and without the order, after tuning); the
     # other legs follow the choice
-    use_order = args.order == "on" or (args.order == "auto" and not w.spatial_order)
+    use_order = args.order in ("on", "tiles") or (args.order == "auto" and not w.spatial_order)
+    use_tiles = args.order == "tiles"
     order_note = args.order
 
     def make(precision, gradient=args.gradient, order=None):
@@ -449,6 +450,7 @@ def run_apm(args):
                    mass_frac_bits=w.mass_frac_bits, device=local, gradient=gradient)
         if use_order if order is None else order:   # the particle processing order, recomputed every step
             s.reserve_order(w.n_particles)
+            s.set_deposit_tiles(use_tiles)          # ... and the deposit through shared-memory tiles
         return s, s.alloc_all()
 
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in w.particles.items()}
@@ -490,15 +492,19 @@ def run_apm(args):
     if args.order == "auto" and not w.spatial_order:
         # the order costs a sort per step and pays in the particle kernels only
         # where the caller's order is incoherent: five eager steps each way
-        def t_order(on):
+        def t_order(on, tiles):
             s32.reserve_order(n if on else 0)
+            s32.set_deposit_tiles(tiles)
             for _ in range(2):
                 step32()
             return timed(step32, 5)
-        t_on, t_off = t_order(True), t_order(False)
-        use_order = t_on < t_off
+        t = {"off": t_order(False, False), "on": t_order(True, False), "tiles": t_order(True, True)}
+        pick = min(t, key=t.get)
+        use_order, use_tiles = pick != "off", pick == "tiles"
         s32.reserve_order(n if use_order else 0)
-        order_note = f"auto: {t_on:.3f} ms per eager step with the order, {t_off:.3f} without"
+        s32.set_deposit_tiles(use_tiles)
+        order_note = ("auto: ms per eager step " +
+                      ", ".join(f"{k} {v:.3f}" for k, v in t.items()) + f"; chose {pick}")
         for _ in range(2):
             step32()
         s32.sync_status()
@@ -760,7 +766,8 @@ def run_apm(args):
                    "interior_cells": cells, "particles": n, "periodic": w.periodic,
                    "l2": "inputs larger than L2 (no flush)", "cuda_graph": used_graph,
                    "parallelism": f"replicas x{world}", "gradient": args.gradient,
-                   "particle_order": "on" if use_order else "off", "particle_order_choice": order_note,
+                   "particle_order": ("tiles" if use_tiles else "on") if use_order else "off",
+                   "particle_order_choice": order_note,
                    "fft_shapes": shapes32},
         "particles_per_s": job_rate(ranks, n, ms) * 1e6,
         "roofline": roofline,
@@ -813,11 +820,12 @@ def main():
     ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "c5s"], default="c5")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--order", choices=["auto", "on", "off"], default="auto",
+    ap.add_argument("--order", choices=["auto", "on", "off", "tiles"], default="auto",
                     help="sort the particles by root-level bin every step before the particle kernels "
-                         "(apm_order_particles; results are bit-identical either way); auto: off when the "
-                         "workload stores its particles in spatial order (the Zel'dovich lattice), otherwise "
-                         "the faster of five eager steps with and without it")
+                         "(apm_order_particles; results are bit-identical either way); tiles: also deposit "
+                         "through shared-memory tiles (apm_set_deposit_tiles); auto: off when the workload "
+                         "stores its particles in spatial order (the Zel'dovich lattice), otherwise the fastest "
+                         "of five eager steps each way")
     ap.add_argument("--no-per-grid", action="store_true",
                     help="skip timing the plain per-grid launch path (FP64 and FP32)")
     ap.add_argument("--no-tune", action="store_true", help="default FFT pass shapes, no autotuner")

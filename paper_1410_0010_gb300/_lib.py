@@ -69,6 +69,7 @@ SIGNATURES = {
     "apm_autotune_level": (c_i32, [c_void_p, c_i32, ctypes.POINTER(c_void_p),
                                    ctypes.POINTER(c_void_p), c_void_p]),
     "apm_set_grid_batching": (c_i32, [c_void_p, c_i32]),
+    "apm_set_deposit_tiles": (c_i32, [c_void_p, c_i32]),
     "apm_reserve_order": (c_i32, [c_void_p, c_i64]),
     "apm_graph_begin": (c_i32, [c_void_p, c_void_p]),
     "apm_graph_end": (c_i32, [c_void_p, c_void_p, ctypes.POINTER(c_i32)]),

@@ -118,6 +118,7 @@ struct apm_ctx {
     void** d_tabs = nullptr;         // [role][level]: each level's device pointer table of the role
     Profiler prof;
     bool batched = true;             // apm_set_grid_batching
+    bool dep_tiles = false;          // apm_set_deposit_tiles
     // auxiliary streams on which the segments of one FFT pass (grids of
     // different kernels) run side by side, forked from and joined to the
     // caller's stream with events
@@ -628,12 +629,16 @@ Particles to_dev(const apm_particles* p) {
 }
 
 // the interpolation calls visit the particles in the current order when it
-// was computed for this many particles (any order gives the same results).
-// The deposits keep the caller's order: in bin order, neighbouring threads
-// add into the same cells and their L2 reductions serialise (measured slower
-// on the batched level), while the interpolation's gathers gain from it.
+// was computed for this many particles (any order gives the same results);
+// so do the deposits with apm_set_deposit_tiles(1), which then gather each
+// CTA's charges of its bin in shared memory (k_deposit<true>).  Without the
+// tiles the deposits keep the caller's order: in bin order neighbouring
+// threads reduce into the same cells and their L2 reductions serialise.
 void use_order(const apm_ctx* c, Particles& P) {
-    if (c->order.perm && c->order.n == P.n) P.perm = c->order.perm;
+    if (c->order.perm && c->order.n == P.n) {
+        P.perm = c->order.perm;
+        P.order_shift = c->order.shift;
+    }
 }
 
 bool particles_ok(const apm_particles* p) {
@@ -1108,6 +1113,7 @@ apm_status apm_deposit(apm_ctx* c, int32_t level, const apm_particles* particles
         return APM_E_CUDA;
     }
     Particles P = to_dev(particles);
+    if (c->dep_tiles) use_order(c, P);
     Trace t(c, K_DEPOSIT, s);
     return cuda_status(launch_deposit(L.dev, P, half_dt, c->cfg.box, c->cfg.mass_frac_bits,
                                       (int64_t* const*)d_gmf, c->d_status, s));
@@ -1154,6 +1160,7 @@ apm_status apm_deposit_all(apm_ctx* c, const apm_particles* particles, double ha
             return APM_E_CUDA;
     }
     Particles P = to_dev(particles);
+    if (c->dep_tiles) use_order(c, P);
     Trace t(c, K_DEPOSIT, s);
     return cuda_status(launch_deposit_levels(c->d_levels, nl, P, half_dt, c->cfg.box, c->cfg.mass_frac_bits,
                                              (int64_t* const* const*)(c->d_tabs + (size_t)R_GMF * nl),
@@ -1199,6 +1206,12 @@ apm_status apm_solve_level(apm_ctx* c, int32_t level, const int64_t* const* gmf,
                 if (run_pass(c, L, q, L.pass[q], d_gmf, d_phis, s, comp, gk) != cudaSuccess) return APM_E_CUDA;
             }
     }
+    return APM_OK;
+}
+
+apm_status apm_set_deposit_tiles(apm_ctx* c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return APM_E_INVALID;
+    c->dep_tiles = on == 1;
     return APM_OK;
 }
 

@@ -452,6 +452,7 @@ struct Particles {
     long long n;
     const double *x, *y, *z, *vx, *vy, *vz, *m;
     const int* perm = nullptr;   // processing order (launch_order): slot i visits particle perm[i]
+    int order_shift = 0;         // ... sorted by bins of 2^order_shift root cells (x fastest)
     __device__ __forceinline__ long long at(long long i) const { return perm ? (long long)perm[i] : i; }
 };
 

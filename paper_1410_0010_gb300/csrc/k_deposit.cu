@@ -5,6 +5,8 @@
 // associative, so the field is bit-identical for any particle order and any
 // atomic interleaving.  Every floating-point step uses explicitly rounded
 // intrinsics (no contraction), so the charges equal a plain IEEE evaluation.
+#include <climits>
+
 #include "apm_internal.cuh"
 
 namespace apm {
@@ -114,6 +116,47 @@ __device__ __forceinline__ void add_charge(int64_t* __restrict__ out, unsigned i
         asm volatile("red.global.add.u64 [%0], %1;" ::"l"(out + idx), "l"((unsigned long long)q));
 }
 
+// ---- the deposit of particles in bin order: per-CTA tiles in shared memory ----
+// With the particles sorted by bins of 2^s root cells (apm_order_particles,
+// x fastest), a CTA's particles lie in one bin or in two x-neighbours, and
+// their clouds overlap.  For each level whose tile fits kTileCells, the CTA
+// keeps the charges that fall into one grid's box around its first
+// candidate particle's bin (that bin and the next along x, with one cell of
+// halo) in shared memory: each 64-bit sum is two 32-bit words, added with
+// native 32-bit atomics, the low word's carry going to the high word, so the
+// sum is exact modulo 2^64.  Charges outside the box, or to another grid, go
+// straight to L2.  After a barrier the CTA sends one reduction per nonzero
+// cell.  Integer sums do not depend on the order: the field is bit-identical
+// to the direct deposit's.
+constexpr int kTileCells = 2304;    // 9 KB of low words and 9 KB of high words
+constexpr int kMaxTileLevels = 4;
+struct DepTile {
+    int gi;          // the grid (index on the level), < 0: no tile
+    int o[3];        // box origin in the grid's GMF cells
+    int n[3];        // box extents
+    int base;        // first cell in the words
+};
+struct TileSet {
+    DepTile* t;      // per tile slot
+    unsigned* lo;
+    unsigned* hi;
+};
+
+// v into slot `slot`'s tile when grid gi's cell (cx, cy, cz) lies in it
+__device__ __forceinline__ bool tile_add(const TileSet& ts, int slot, int gi, int cx, int cy, int cz, long long v) {
+    if (slot < 0) return false;
+    const DepTile& t = ts.t[slot];
+    if (t.gi != gi) return false;
+    const unsigned x = (unsigned)(cx - t.o[0]), y = (unsigned)(cy - t.o[1]), z = (unsigned)(cz - t.o[2]);
+    if (x >= (unsigned)t.n[0] || y >= (unsigned)t.n[1] || z >= (unsigned)t.n[2]) return false;
+    const int k = t.base + (int)x + t.n[0] * ((int)y + t.n[1] * (int)z);
+    const unsigned lo = (unsigned)v, hi = (unsigned)((unsigned long long)v >> 32);
+    const unsigned old = atomicAdd(ts.lo + k, lo);
+    const unsigned add_hi = hi + (old + lo < old ? 1u : 0u);   // the carry out of the low word
+    if (add_hi) atomicAdd(ts.hi + k, add_hi);
+    return true;
+}
+
 // CTA size and minimum resident CTAs per SM of the particle deposit
 #ifndef APM_DEP_THREADS
 #define APM_DEP_THREADS 128
@@ -131,11 +174,12 @@ __device__ __forceinline__ unsigned long long mul63(unsigned long long a, unsign
 // The 27 charges of one particle into every candidate grid [e0, e1) of the
 // level: ((|M| wx) wy) wz for the 26 outer cells, every product rounded half up
 // on the scale 2^63, the centre cell M minus the others.  SMALL: |M| < 2^32.
-template <bool SMALL>
+template <bool SMALL, bool TILE>
 __device__ __forceinline__ void scatter_charges(const LevelDev& L, int64_t* const* __restrict__ gmf,
                                                 unsigned* __restrict__ status, long long M,
                                                 unsigned long long aM, const unsigned long long w[3][3],
-                                                const long long ic[3], int e0, int e1, bool outside) {
+                                                const long long ic[3], int e0, int e1, bool outside,
+                                                const TileSet& ts, int slot) {
     unsigned long long mx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) mx[a] = mul63<SMALL>(aM, w[0][a]);
@@ -169,14 +213,17 @@ __device__ __forceinline__ void scatter_charges(const LevelDev& L, int64_t* cons
                     long long v = (long long)mul63<SMALL>(mxy[a], w[2][c]);
                     v = M < 0 ? -v : v;
                     others += v;
-                    if (ok && cx[a] >= 0 && APM_IN_BOUNDS(row + (unsigned)cx[a], g.cells_gmf, status))
-                        add_charge(out, row + (unsigned)cx[a], v);
+                    if (ok && cx[a] >= 0 && APM_IN_BOUNDS(row + (unsigned)cx[a], g.cells_gmf, status)) {
+                        if (!TILE || !tile_add(ts, slot, gi, cx[a], cy[b], cz[c], v))
+                            add_charge(out, row + (unsigned)cx[a], v);
+                    }
                 }
             }
         }
         const unsigned ci = (unsigned)cx[1] + G0 * (unsigned)cy[1] + G01 * (unsigned)cz[1];
-        if (cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0 && APM_IN_BOUNDS(ci, g.cells_gmf, status))
-            add_charge(out, ci, M - others);
+        if (cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0 && APM_IN_BOUNDS(ci, g.cells_gmf, status)) {
+            if (!TILE || !tile_add(ts, slot, gi, cx[1], cy[1], cz[1], M - others)) add_charge(out, ci, M - others);
+        }
     }
 }
 
@@ -184,9 +231,10 @@ __device__ __forceinline__ void scatter_charges(const LevelDev& L, int64_t* cons
 // grids of one level; false when the particle is not a candidate of the level
 // (then it is none of a finer level's either: finer GMF boxes lie inside the
 // interiors of their parents).
+template <bool TILE>
 __device__ __forceinline__ bool deposit_level(const LevelDev& L, const long long X[3], long long M,
                                               bool outside, int64_t* const* __restrict__ gmf,
-                                              unsigned* __restrict__ status) {
+                                              unsigned* __restrict__ status, const TileSet& ts, int slot) {
     const int PB = L.frac_bits;
     long long ic[3];
 #pragma unroll
@@ -213,9 +261,9 @@ __device__ __forceinline__ bool deposit_level(const LevelDev& L, const long long
     for (int j = 0; j < 3; ++j) tsc_fixed(X[j], PB, w[j]);
     const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
     if (aM < (1ULL << 32))   // every product has a 32-bit factor: |M|, then (|M| wx), then (|M| wx) wy
-        scatter_charges<true>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
+        scatter_charges<true, TILE>(L, gmf, status, M, aM, w, ic, e0, e1, outside, ts, slot);
     else
-        scatter_charges<false>(L, gmf, status, M, aM, w, ic, e0, e1, outside);
+        scatter_charges<false, TILE>(L, gmf, status, M, aM, w, ic, e0, e1, outside, ts, slot);
     return true;
 }
 
@@ -240,59 +288,195 @@ __device__ __forceinline__ bool particle_fixed(const LevelDev& L, const Particle
     return true;
 }
 
-__global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(LevelDev L, Particles P, double half_dt,
-                                                 double box, int F,
-                                                 int64_t* const* __restrict__ gmf,
-                                                 unsigned* __restrict__ status) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+// the first candidate grid of level L for the fixed-point position X (the
+// root: grid 0), or -1 when the particle is no candidate of the level
+__device__ __forceinline__ int first_candidate(const LevelDev& L, const long long X[3]) {
+    if (L.is_root) return 0;
+    const TileMap& m = L.map;
+    long long t[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const long long rel = (X[j] >> L.frac_bits) - m.lo[j];
+        if (rel < 0) return -1;
+        t[j] = rel >> m.shift;
+        if (t[j] >= m.nt[j]) return -1;
+    }
+    const long long tile = t[0] + (long long)m.nt[0] * (t[1] + (long long)m.nt[1] * t[2]);
+    const int e0 = m.dep_off[tile];
+    return e0 == m.dep_off[tile + 1] ? -1 : m.dep_list[e0];
+}
+
+// the box of tile slot `slot` on absolute level `lev` for bins of 2^shift root
+// cells: the bin and the next along x, one cell of halo (extents n); false
+// when the slots up to this one exceed kTileCells
+__device__ __forceinline__ bool tile_extent(int lev, int shift, int n[3], int& cells) {
+    if (shift + lev > 10) return false;
+    const int b = 1 << (shift + lev);
+    n[0] = 2 * b + 2;
+    n[1] = n[2] = b + 2;
+    cells = n[0] * n[1] * n[2];
+    return true;
+}
+
+// tile set-up of a CTA over levels lv[0..nl) (the levels in slot order): the
+// layout (every thread), then the anchor of each slot (the CTA's first
+// particle that is a candidate of its level) and, by that thread, the grid
+// and origin; returns the number of slots and the words used
+template <class LV>
+__device__ __forceinline__ int tile_setup(const TileSet& ts, int* anchor, const LV& lv, int nl, int shift, bool ok,
+                                          const long long X[3], int& used) {
+    int nslots = 0;
+    used = 0;
+    for (int l = 0; l < nl && l < kMaxTileLevels; ++l) {
+        int n[3], cells;
+        if (!tile_extent(lv(l).level, shift, n, cells) || used + cells > kTileCells) break;
+        if (threadIdx.x == 0) {
+            DepTile& t = ts.t[l];
+            t.gi = -1;
+            t.n[0] = n[0];
+            t.n[1] = n[1];
+            t.n[2] = n[2];
+            t.base = used;
+            anchor[l] = INT_MAX;
+        }
+        used += cells;
+        ++nslots;
+    }
+    for (int k = threadIdx.x; k < used; k += blockDim.x) {
+        ts.lo[k] = 0u;
+        ts.hi[k] = 0u;
+    }
+    __syncthreads();
+    if (ok)
+        for (int l = 0; l < nslots; ++l) {
+            if (first_candidate(lv(l), X) < 0) break;
+            atomicMin(anchor + l, (int)threadIdx.x);
+        }
+    __syncthreads();
+    if (ok)
+        for (int l = 0; l < nslots; ++l)
+            if (anchor[l] == (int)threadIdx.x) {
+                const LevelDev& L = lv(l);
+                const int gi = first_candidate(L, X);
+                const GridDev& g = L.g[gi];
+                DepTile& t = ts.t[l];
+                t.gi = gi;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    t.o[j] = (int)(((X[j] >> (kPosBits + shift)) << (shift + L.level)) - g.lo[j]) - 1;
+            }
+    __syncthreads();
+    return nslots;
+}
+
+// one reduction per nonzero tile cell (after a barrier that follows every charge)
+template <class LV, class GM>
+__device__ __forceinline__ void tile_flush(const TileSet& ts, int nslots, int used, const LV& lv, const GM& gm) {
+    for (int k = threadIdx.x; k < used; k += blockDim.x) {
+        int l = 0;
+        while (l + 1 < nslots && k >= ts.t[l + 1].base) ++l;
+        const DepTile& t = ts.t[l];
+        const unsigned long long v = ((unsigned long long)ts.hi[k] << 32) | ts.lo[k];
+        if (t.gi < 0 || v == 0ULL) continue;
+        const int r = k - t.base;
+        const int x = r % t.n[0], y = (r / t.n[0]) % t.n[1], z = r / (t.n[0] * t.n[1]);
+        const GridDev& g = lv(l).g[t.gi];
+        const unsigned idx = (unsigned)(t.o[0] + x) + (unsigned)g.G[0] * ((unsigned)(t.o[1] + y) +
+                                                                           (unsigned)g.G[1] * (unsigned)(t.o[2] + z));
+        add_charge(gm(l)[t.gi], idx, (long long)v);
+    }
+}
+
+// the deposit of slot i's particle into one level (the candidate test first
+// on refined levels: most particles leave there)
+template <bool TILE>
+__device__ __forceinline__ void deposit_one(const LevelDev& L, const Particles& P, long long i, double half_dt,
+                                            double box, int F, int64_t* const* __restrict__ gmf,
+                                            unsigned* __restrict__ status, const TileSet& ts, int slot) {
     const long long p = P.at(i);
     long long X[3], M;
     bool outside;
-    // the candidate test comes first on refined levels (most particles leave there)
     if (!L.is_root) {
         const double xd[3] = {drift_raw(P.x[p], P.vx[p], half_dt), drift_raw(P.y[p], P.vy[p], half_dt),
                               drift_raw(P.z[p], P.vz[p], half_dt)};
-        const TileMap& m = L.map;
-        long long t[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            X[j] = fixed_position(xd[j], L);
-            long long rel = (X[j] >> L.frac_bits) - m.lo[j];
-            if (rel < 0) return;
-            t[j] = rel >> m.shift;
-            if (t[j] >= m.nt[j]) return;
-        }
-        long long tile = t[0] + (long long)m.nt[0] * (t[1] + (long long)m.nt[1] * t[2]);
-        if (m.dep_off[tile] == m.dep_off[tile + 1]) return;
+        for (int j = 0; j < 3; ++j) X[j] = fixed_position(xd[j], L);
+        if (first_candidate(L, X) < 0) return;
         bool ok;
         M = scaled_rint(P.m[p], F, ok);
         if (!ok) {
             atomicOr(status, kStOverflow);
             return;
         }
-        deposit_level(L, X, M, false, gmf, status);
+        deposit_level<TILE>(L, X, M, false, gmf, status, ts, slot);
         return;
     }
     if (!particle_fixed(L, P, p, half_dt, box, F, X, &M, &outside, status)) return;
-    deposit_level(L, X, M, outside, gmf, status);
+    deposit_level<TILE>(L, X, M, outside, gmf, status, ts, slot);
+}
+
+// TILE: the particles are in bin order, and each CTA gathers the charges of
+// its bin in shared memory (see tile_add)
+template <bool TILE>
+__global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit(LevelDev L, Particles P, double half_dt,
+                                                 double box, int F,
+                                                 int64_t* const* __restrict__ gmf,
+                                                 unsigned* __restrict__ status) {
+    __shared__ unsigned t_lo[TILE ? kTileCells : 1], t_hi[TILE ? kTileCells : 1];
+    __shared__ DepTile tiles[TILE ? kMaxTileLevels : 1];
+    __shared__ int anchor[TILE ? kMaxTileLevels : 1];
+    const TileSet ts{tiles, t_lo, t_hi};
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if constexpr (!TILE) {
+        if (i < P.n) deposit_one<false>(L, P, i, half_dt, box, F, gmf, status, ts, -1);
+    } else {
+        // the anchor's position: drifted and fixed like the deposit's (the
+        // candidate and mass checks follow in deposit_one)
+        long long X[3] = {0, 0, 0};
+        const bool live = i < P.n;
+        if (live) {
+            const long long p = P.at(i);
+            const double xd[3] = {drift_raw(P.x[p], P.vx[p], half_dt), drift_raw(P.y[p], P.vy[p], half_dt),
+                                  drift_raw(P.z[p], P.vz[p], half_dt)};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) X[j] = fixed_position(xd[j], L);
+        }
+        auto lv = [&](int) -> const LevelDev& { return L; };
+        int used;
+        const int nslots = tile_setup(ts, anchor, lv, 1, P.order_shift, live, X, used);
+        if (live) deposit_one<true>(L, P, i, half_dt, box, F, gmf, status, ts, nslots > 0 ? 0 : -1);
+        __syncthreads();
+        tile_flush(ts, nslots, used, lv, [&](int) { return gmf; });
+    }
 }
 
 // Every level in one pass over the particles: the position and mass are
 // converted once, then deposited level by level from the root down while the
 // particle is a candidate.  levels: the LevelDev of each level; gmfs[l]: the
 // GMF pointer table of level l.
+template <bool TILE>
 __global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit_levels(
     const LevelDev* __restrict__ levels, int nl, Particles P, double half_dt, double box, int F,
     int64_t* const* const* __restrict__ gmfs, unsigned* __restrict__ status) {
+    __shared__ unsigned t_lo[TILE ? kTileCells : 1], t_hi[TILE ? kTileCells : 1];
+    __shared__ DepTile tiles[TILE ? kMaxTileLevels : 1];
+    __shared__ int anchor[TILE ? kMaxTileLevels : 1];
+    const TileSet ts{tiles, t_lo, t_hi};
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    const long long p = P.at(i);
-    long long X[3], M;
-    bool outside;
-    if (!particle_fixed(levels[0], P, p, half_dt, box, F, X, &M, &outside, status)) return;
-    for (int l = 0; l < nl; ++l)
-        if (!deposit_level(levels[l], X, M, l == 0 && outside, gmfs[l], status)) break;
+    long long X[3] = {0, 0, 0}, M = 0;
+    bool outside = false, ok = false;
+    if (i < P.n) ok = particle_fixed(levels[0], P, P.at(i), half_dt, box, F, X, &M, &outside, status);
+    int nslots = 0, used = 0;
+    auto lv = [&](int l) -> const LevelDev& { return levels[l]; };
+    if constexpr (TILE) nslots = tile_setup(ts, anchor, lv, nl, P.order_shift, ok, X, used);
+    if (ok)
+        for (int l = 0; l < nl; ++l)
+            if (!deposit_level<TILE>(levels[l], X, M, l == 0 && outside, gmfs[l], status, ts, l < nslots ? l : -1))
+                break;
+    if constexpr (TILE) {
+        __syncthreads();
+        tile_flush(ts, nslots, used, lv, [&](int l) { return gmfs[l]; });
+    }
 }
 
 }  // namespace
@@ -310,7 +494,10 @@ cudaError_t launch_deposit(const LevelDev& L, const Particles& P, double half_dt
                            int F, int64_t* const* gmf, unsigned* status, cudaStream_t s) {
     if (P.n <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n + kDepThreads - 1) / kDepThreads);
-    k_deposit<<<blocks, kDepThreads, 0, s>>>(L, P, half_dt, box, F, gmf, status);
+    if (P.perm)
+        k_deposit<true><<<blocks, kDepThreads, 0, s>>>(L, P, half_dt, box, F, gmf, status);
+    else
+        k_deposit<false><<<blocks, kDepThreads, 0, s>>>(L, P, half_dt, box, F, gmf, status);
     return cudaGetLastError();
 }
 
@@ -319,7 +506,10 @@ cudaError_t launch_deposit_levels(const LevelDev* levels, int nl, const Particle
                                   cudaStream_t s) {
     if (P.n <= 0 || nl <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n + kDepThreads - 1) / kDepThreads);
-    k_deposit_levels<<<blocks, kDepThreads, 0, s>>>(levels, nl, P, half_dt, box, F, gmfs, status);
+    if (P.perm)
+        k_deposit_levels<true><<<blocks, kDepThreads, 0, s>>>(levels, nl, P, half_dt, box, F, gmfs, status);
+    else
+        k_deposit_levels<false><<<blocks, kDepThreads, 0, s>>>(levels, nl, P, half_dt, box, F, gmfs, status);
     return cudaGetLastError();
 }
 

@@ -226,6 +226,12 @@ class Solver:
         plain per-grid baseline.  Results are bit-identical."""
         check(lib().apm_set_grid_batching(self._ctx, 1 if batched else 0), "apm_set_grid_batching")
 
+    def set_deposit_tiles(self, on):
+        """True: while a particle order is current, the deposits visit the
+        particles in it and gather each CTA's charges in shared-memory tiles
+        (bit-identical; pays where many particles share cells).  Default off."""
+        check(lib().apm_set_deposit_tiles(self._ctx, 1 if on else 0), "apm_set_deposit_tiles")
+
     def fft_shapes(self, level):
         sh = ApmFftShapes()
         check(lib().apm_get_fft_shapes(self._ctx, level, ctypes.byref(sh)), "apm_get_fft_shapes")
