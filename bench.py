@@ -107,7 +107,50 @@ class Clocks:
 # ----------------------------------------------------------------------------
 # algorithmic bytes of each kernel (compulsory HBM traffic of its inputs/outputs)
 # ----------------------------------------------------------------------------
-def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
+def interp_field_bytes(w, levels, parts, half_dt, rsz, chunk=1 << 22):
+    """Acceleration-field bytes the interpolation reads at least once: each
+    particle reads the 27 cells around its drifted position on its owner grid
+    (the finest solved grid whose interior holds it), three components of rsz
+    bytes; a cell read by several particles counts once.  Computed on the
+    device from the particle arrays (FP64 drift; a particle on a cell edge may
+    land one cell over, which changes the count negligibly)."""
+    import torch
+    N0 = w.grids[0].dims[0]
+    x = [parts[k] + parts["v" + k] * half_dt for k in ("x", "y", "z")]
+    if w.periodic:
+        x = [torch.remainder(v, 1.0) for v in x]
+    n = x[0].numel()
+    dev = x[0].device
+    owner = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    order = sorted((g.level, gi) for gi, g in enumerate(w.grids) if g.level in levels)
+    for lev, gi in order:                      # coarse to fine: a finer grid overrides
+        g = w.grids[gi]
+        scale = N0 * 2 ** lev
+        inside = torch.ones(n, dtype=torch.bool, device=dev)
+        for j in range(3):
+            c = torch.floor(x[j] * scale).to(torch.int64)
+            inside &= (c >= g.start[j]) & (c < g.start[j] + g.dims[j])
+        owner[inside] = gi
+    offs = torch.stack(torch.meshgrid(*(torch.arange(-1, 2, device=dev),) * 3, indexing="ij"), -1).reshape(27, 3)
+    total = 0
+    for lev, gi in order:
+        g = w.grids[gi]
+        E = [d + 2 for d in g.dims]
+        mark = torch.zeros(E[0] * E[1] * E[2], dtype=torch.bool, device=dev)
+        ids = torch.nonzero(owner == gi).flatten()
+        scale = N0 * 2 ** lev
+        for a in range(0, ids.numel(), chunk):
+            sel = ids[a:a + chunk]
+            c = torch.stack([torch.floor(x[j][sel] * scale).to(torch.int64) - g.start[j] + 1 for j in range(3)], -1)
+            cl = (c[:, None, :] + offs[None, :, :]).reshape(-1, 3)
+            ok = ((cl >= 0) & (cl < torch.tensor(E, device=dev))).all(-1)
+            cl = cl[ok]
+            mark[cl[:, 0] + E[0] * (cl[:, 1] + E[1] * cl[:, 2])] = True
+        total += int(mark.sum()) * 3 * rsz
+    return total
+
+
+def algorithmic_bytes(solver, w, levels, csz, rsz, batched, interp_fields=None):
     """Bytes per step per kernel, summed over the solved levels.
 
     csz / rsz: bytes of one complex / real value of the precision; batched:
@@ -115,7 +158,9 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
     The spectral gradient runs the z, y-inverse and x-inverse passes once per
     component (phi, A_x, A_y, A_z), each reading its input again; its
     acceleration kernel reads phi and the three components on the output
-    cells instead of differencing."""
+    cells instead of differencing.  interp_fields: the acceleration-field
+    bytes the interpolation reads (interp_field_bytes); None counts every
+    grid's whole field."""
     out = {k: 0 for k in ("gas_init", "tsc_deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green",
                           "fft_y_inv", "fft_x_inv", "accel_carry", "tsc_interp", "particle_order")}
     n = w.n_particles
@@ -150,7 +195,8 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
                 out["accel_carry"] += 4 * rsz * ec + 4 * rsz * ec
             else:
                 out["accel_carry"] += rsz * Wd[0] * Wd[1] * Wd[2] + 4 * rsz * ec
-            out["tsc_interp"] += 3 * rsz * ec
+            if interp_fields is None:
+                out["tsc_interp"] += 3 * rsz * ec
         if not batched:
             out["tsc_deposit"] += 56 * n      # x, y, z, vx, vy, vz, m per level
             out["tsc_interp"] += 48 * n       # positions and velocities per level
@@ -158,6 +204,8 @@ def algorithmic_bytes(solver, w, levels, csz, rsz, batched):
         out["tsc_deposit"] += 56 * n
         out["tsc_interp"] += 48 * n
     out["tsc_interp"] += 3 * rsz * n      # accelerations written once
+    if interp_fields is not None:
+        out["tsc_interp"] += interp_fields
     return out
 
 
@@ -715,7 +763,8 @@ def run_apm(args):
     # ---------------- roofline of the dominant kernel
     hbm, peak_src = peaks()
     batched = levels == list(range(s32.n_levels))
-    ab = algorithmic_bytes(s32, w, levels, 8, 4, batched)
+    ab = algorithmic_bytes(s32, w, levels, 8, 4, batched,
+                           interp_fields=interp_field_bytes(w, levels, dparts, w.half_dt, 4))
     kernels = {}
     for name, (cnt, tot) in prof.items():
         if cnt == 0:

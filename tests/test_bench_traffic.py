@@ -142,3 +142,36 @@ def test_algorithmic_bytes_per_operator():
     assert af["fft_x_inv"] == csz * Wf[2] * M[1] * Hx + rsz * int(np.prod(Wf))
     assert af["fft_z_green"] == a2["fft_z_green"]
     assert af["fft_x_fwd"] + af["fft_y_fwd"] < a2["fft_x_fwd"] + a2["fft_y_fwd"]
+
+
+def test_interp_field_bytes_counts_each_read_cell_once():
+    """The interpolation's field bytes: 27 cells per particle on its owner grid
+    (the finest solved grid holding it), each cell once, three components."""
+    import types
+
+    import numpy as np
+    import torch
+    b = _bench()
+    from apm_inputs import GridDesc
+    grids = [GridDesc(0, -1, (0, 0, 0), (8, 8, 8)), GridDesc(1, 0, (4, 4, 4), (6, 6, 6))]
+    w = types.SimpleNamespace(grids=grids, periodic=False)
+
+    def parts(pos):
+        pos = np.asarray(pos, dtype=np.float64).T
+        d = {k: torch.tensor(pos[j]) for j, k in enumerate("xyz")}
+        d.update({"v" + k: torch.zeros(pos.shape[1], dtype=torch.float64) for k in "xyz"})
+        return d
+    one = (0.1, 0.1, 0.1)                        # root cell 0: its cloud reaches cell -1 of the window
+    same = (0.11, 0.12, 0.1)                     # the same root cell: no new cells
+    near = (0.26, 0.1, 0.1)                      # root cell 2: its cloud shares x = 1 with the first
+    child = (0.45, 0.45, 0.45)                   # level-1 cell 7, inside the child: owned by it
+    assert b.interp_field_bytes(w, [0, 1], parts([one]), 0.0, 4) == 27 * 12
+    assert b.interp_field_bytes(w, [0, 1], parts([one, same]), 0.0, 4) == 27 * 12
+    assert b.interp_field_bytes(w, [0, 1], parts([one, near]), 0.0, 4) == (27 + 18) * 12
+    assert b.interp_field_bytes(w, [0, 1], parts([one, child]), 0.0, 4) == 2 * 27 * 12
+    # a drift of one root cell moves the cloud
+    d = parts([one])
+    d["vx"][:] = 1.0
+    assert b.interp_field_bytes(w, [0, 1], d, 0.125, 4) == 27 * 12
+    # only the solved levels own particles
+    assert b.interp_field_bytes(w, [1], parts([one, child]), 0.0, 4) == 27 * 12
