@@ -68,6 +68,10 @@ template <int A, int B, int Cc> struct FastPlan {
         const int d2 = rest / Cc, d3 = rest - d2 * Cc;
         return d1 + A * d2 + A * B * d3;
     }
+    // the natural-index weight of the last digit: in the last stage (inner
+    // stride 1) a butterfly's element k sits at position base + k, and its
+    // natural index is natural(base) + k last_weight()
+    static constexpr int last_weight() { return L / radix(NST - 1); }
     // the position of natural index k (the inverse of natural())
     __device__ __forceinline__ static int position(int k) {
         const int d1 = k % A, q = k / A;
@@ -109,9 +113,11 @@ __device__ __forceinline__ void fast_dif_stage(float2* buf, const float2* __rest
 #pragma unroll
             for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, DIR>(tw, lo * k * TWS));
         }
+        static_assert(!OUT_G || S == 1, "global output only from the last stage");
+        const int nat0 = OUT_G ? P::natural(base) : 0;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            if constexpr (OUT_G) gout.st(P::natural(base + k * S), v[k]);
+            if constexpr (OUT_G) gout.st(nat0 + k * P::last_weight(), v[k]);
             else buf[(base + k * S) * PITCH + line] = v[k];
         }
     }
@@ -138,9 +144,11 @@ __device__ __forceinline__ void fast_dit_stage(float2* buf, const float2* __rest
         const int hi = b / S, lo = b - hi * S;
         const int base = hi * R * S + lo;
         float2 v[R];
+        static_assert(!IN_G || S == 1, "global input only to the first inverse stage");
+        const int nat0 = IN_G ? P::natural(base) : 0;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            if constexpr (IN_G) v[k] = gin.ld(P::natural(base + k * S));
+            if constexpr (IN_G) v[k] = gin.ld(nat0 + k * P::last_weight());
             else v[k] = buf[(base + k * S) * PITCH + line];
         }
         if constexpr (S > 1) {
@@ -210,6 +218,16 @@ template <int L> struct FastOut {
     }
 };
 
+// Output element i of a pass with no window (the y forward: all L outputs)
+struct FastOutAll {
+    float2* __restrict__ p;
+    int stride;
+    bool live;
+    __device__ __forceinline__ void st(int i, float2 v) const {
+        if (live) p[i * stride] = v;
+    }
+};
+
 // Column pass (AX 1: y, 2: z) with compile-time plan P, TX kx columns per CTA
 // (the level's lines for this pass) and NT threads; the same work list and
 // layout as k_col (MODE 0 yf, 1 z with the table, 2 yi).
@@ -257,16 +275,18 @@ __global__ void __launch_bounds__(NT) k_col_fast(const GridDev* __restrict__ gri
     __syncthreads();   // twiddles
 
     if constexpr (MODE == 0) {
+        // the y forward writes all M1 outputs: no window test
+        const FastOutAll gall{gout.p, gout.stride, live};
         if constexpr (P::NST == 2) {
-            fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gout);
+            fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gall);
             __syncthreads();
-            fast_dif_stage<P, 1, TX, NT, false, true>(buf, tw, gin, gout);
+            fast_dif_stage<P, 1, TX, NT, false, true>(buf, tw, gin, gall);
         } else {
-            fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gout);
+            fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gall);
             __syncthreads();
-            fast_dif_stage<P, 1, TX, NT, false, false>(buf, tw, gin, gout);
+            fast_dif_stage<P, 1, TX, NT, false, false>(buf, tw, gin, gall);
             __syncthreads();
-            fast_dif_stage<P, 2, TX, NT, false, true>(buf, tw, gin, gout);
+            fast_dif_stage<P, 2, TX, NT, false, true>(buf, tw, gin, gall);
         }
     } else if constexpr (MODE == 2) {
         if constexpr (P::NST == 2) {
@@ -396,9 +416,11 @@ __device__ __forceinline__ void fast_dif_stage_rows(float2* buf, const float2* _
 #pragma unroll
             for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, DIR>(tw, lo * k * TWS));
         }
+        static_assert(!OUT_G || S == 1, "global output only from the last stage");
+        const int nat0 = OUT_G ? P::natural(base) : 0;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            if constexpr (OUT_G) gout.st(line, P::natural(base + k * S), v[k]);
+            if constexpr (OUT_G) gout.st(line, nat0 + k * P::last_weight(), v[k]);
             else buf[(base + k * S) * PITCH + line] = v[k];
         }
     }
@@ -569,9 +591,11 @@ __device__ __forceinline__ void xy_y_stage(float2* buf, const float2* __restrict
 #pragma unroll
             for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], tw[lo * k * TWS]);
         }
+        static_assert(!OUT_G || S == 1, "global output only from the last stage");
+        const int nat0 = OUT_G ? P::natural(base) : 0;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            if constexpr (OUT_G) gout.st(col, P::natural(base + k * S), v[k]);
+            if constexpr (OUT_G) gout.st(col, nat0 + k * P::last_weight(), v[k]);
             else buf[(base + k * S) * H + col] = v[k];
         }
     }
@@ -743,11 +767,12 @@ __device__ __forceinline__ void yx_x_stage(float2* buf, const float2* __restrict
             for (int k = 1; k < R; ++k) v[k] = mul<float>(v[k], twid<float, 1>(tw, lo * k * TWS));
         }
         if constexpr (OUT_G) {
+            static_assert(S == 1, "window output only from the last stage");
             float* r0 = out + (long long)(2 * line) * W0;
             const bool has1 = 2 * line + 1 < W1;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                int w = P::natural(base + k * S) - s0x;
+                int w = P::natural(base) + k * P::last_weight() - s0x;
                 if (w < 0) w += L;
                 for (; w < W0; w += L) {
                     r0[w] = v[k].x * norm;
