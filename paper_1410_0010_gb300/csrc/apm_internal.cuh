@@ -174,7 +174,9 @@ inline bool fast_length(int L) {
 // dynamic shared memory of a fast column-pass CTA: the buffer and the twiddles
 inline size_t fast_col_smem(int L) { return (size_t)(L * kFastTx + L) * sizeof(float2); }
 // ... and of a fast x-pass CTA (rows padded to kFastNp + 1 lines)
-inline size_t fast_row_smem(int L) { return (size_t)(L * (kFastNp + 1) + L) * sizeof(float2); }
+// (the x-inverse pads its lines by one element every R_last positions: at
+// most L / 2 more)
+inline size_t fast_row_smem(int L) { return (size_t)(L * (kFastNp + 1) + L / 2 + L) * sizeof(float2); }
 
 // Column-pass chunks carry (kx tile, line index of the other axis) as
 // (kt << 20) | other: other < 2^20, kt < 2^11.

@@ -390,8 +390,17 @@ __global__ void __launch_bounds__(NT) k_xf_fast(const GridDev* __restrict__ grid
 // ---- x-inverse pass ---------------------------------------------------------------
 // One DIF stage s with the butterflies of a line on consecutive threads (item
 // i: butterfly i % NB, line i / NB), so the HBM accesses of the first and last
-// stages run along rows; buffer element (position, line) at pos PITCH + line.
+// stages run along rows; buffer element (position e, line) at
+// rows_index(e) + line = e PITCH + e / R_last + line.  The last stage's lanes
+// step through positions R_last apart: with PITCH odd, one extra element
+// every R_last positions makes that stride odd too (R_last PITCH + 1), so a
+// half-warp's 64-bit accesses fall in distinct bank pairs (with R_last = 16
+// and no padding, all sixteen hit one pair).
 // The global accessors take the line: gin.ld(line, n), gout.st(line, n, v).
+template <class P, int PITCH>
+__device__ __forceinline__ int rows_index(int e) {
+    return e * PITCH + e / P::radix(P::NST - 1);
+}
 template <class P, int S_, int NL, int NT, bool IN_G, bool OUT_G, int DIR, int PITCH, class GIN, class GOUT>
 __device__ __forceinline__ void fast_dif_stage_rows(float2* buf, const float2* __restrict__ tw, const GIN& gin,
                                                     const GOUT& gout) {
@@ -409,7 +418,7 @@ __device__ __forceinline__ void fast_dif_stage_rows(float2* buf, const float2* _
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             if constexpr (IN_G) v[k] = gin.ld(line, base + k * S);
-            else v[k] = buf[(base + k * S) * PITCH + line];
+            else v[k] = buf[rows_index<P, PITCH>(base + k * S) + line];
         }
         FastDft<DIR, R>::run(v);
         if constexpr (S > 1) {
@@ -421,7 +430,7 @@ __device__ __forceinline__ void fast_dif_stage_rows(float2* buf, const float2* _
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             if constexpr (OUT_G) gout.st(line, nat0 + k * P::last_weight(), v[k]);
-            else buf[(base + k * S) * PITCH + line] = v[k];
+            else buf[rows_index<P, PITCH>(base + k * S) + line] = v[k];
         }
     }
 }
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(NT) k_xi_fast(const GridDev* __restrict__ grid
     constexpr int L = P::L, H = L / 2 + 1, PITCH = NP + 1;
     extern __shared__ __align__(16) unsigned char smem_fast[];
     float2* buf = reinterpret_cast<float2*>(smem_fast);
-    float2* tw = buf + L * PITCH;
+    float2* tw = buf + rows_index<P, PITCH>(L);   // past the padded line buffer (<= L PITCH + L / 2)
     const Chunk ch = chunks[blockIdx.x];
     const GridDev& g = grids[ch.grid];
     const int W0 = g.W[0];
