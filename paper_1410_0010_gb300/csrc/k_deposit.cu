@@ -13,6 +13,18 @@ namespace apm {
 namespace {
 
 
+// no baryons: the CTA's rows are one flat range of n zeros, written as
+// 16-byte stores when the range starts 16-byte aligned
+__device__ __noinline__ void zero_range(int64_t* __restrict__ z, long long n) {
+    long long i0 = 0;
+    if ((reinterpret_cast<size_t>(z) & 15) == 0) {
+        longlong2* __restrict__ z2 = reinterpret_cast<longlong2*>(z);
+        for (long long i = threadIdx.x; i < n / 2; i += blockDim.x) z2[i] = make_longlong2(0, 0);
+        i0 = n & ~1LL;
+    }
+    for (long long i = i0 + threadIdx.x; i < n; i += blockDim.x) z[i] = 0;
+}
+
 // One CTA per batch of `rows` GMF rows (a row: G0 cells along x at fixed y, z).
 __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __restrict__ pgrids,
                            const double* const* __restrict__ gas,
@@ -40,60 +52,39 @@ __global__ void __launch_bounds__(256) k_gas_init(LevelDev L, const GridDev* __r
     const int r1 = min(nrows, r0 + g.rows_gas);
     const GridDev* p = par ? &pgrids[g.parent] : nullptr;
     if (!own && !par) {
-        // no baryons: the CTA's rows are one flat range of zeros, written as
-        // 16-byte stores when the range starts 16-byte aligned
-        int64_t* __restrict__ z = out + (long long)r0 * G0;
-        const long long n = (long long)(r1 - r0) * G0;
-        long long i0 = 0;
-        if ((reinterpret_cast<size_t>(z) & 15) == 0) {
-            longlong2* __restrict__ z2 = reinterpret_cast<longlong2*>(z);
-            for (long long i = threadIdx.x; i < n / 2; i += blockDim.x) z2[i] = make_longlong2(0, 0);
-            i0 = n & ~1LL;
-        }
-        for (long long i = i0 + threadIdx.x; i < n; i += blockDim.x) z[i] = 0;
+        zero_range(out + (long long)r0 * G0, (long long)(r1 - r0) * G0);
         return;
     }
-    // the density of GMF cell (r, x): interior gas, the parent's gas on the
-    // border, or none
-    auto density = [&](int r, int x) -> double {
-        const int cy = r % G1 - B, cz = r / G1 - B;
-        const int cx = x - B;
-        if (cy >= 0 && cy < g.N[1] && cz >= 0 && cz < g.N[2] && cx >= 0 && cx < g.N[0])
-            return own ? own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)] : 0.0;
-        if (!par) return 0.0;
-        // parent cell floor(c / 2): the refinement factor is 2 (checked on the host);
-        // past an isolated root's faces (the only border cells with no parent
-        // cell, checked on the host) there are no baryons
-        const long long px = ((g.start[0] + cx) >> 1) - p->start[0];
-        const long long py = ((g.start[1] + cy) >> 1) - p->start[1];
-        const long long pz = ((g.start[2] + cz) >> 1) - p->start[2];
-        if (px >= 0 && px < p->N[0] && py >= 0 && py < p->N[1] && pz >= 0 && pz < p->N[2])
-            return par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
-        return 0.0;
-    };
-    // kGasUnroll cells per thread at a time: their density loads are all in
-    // flight before the first conversion
-    constexpr int kGasUnroll = 4;
-    for (RowWalk it(r0, G0); it.r < r1;) {
-        int rr[kGasUnroll], xx[kGasUnroll];
-        double rho[kGasUnroll];
-#pragma unroll
-        for (int u = 0; u < kGasUnroll; ++u) {
-            rr[u] = it.r;
-            xx[u] = it.x;
-            if (it.r < r1) it.next();
+    int last = -1, cy = 0, cz = 0;
+    bool yz_in = false;
+    for (RowWalk it(r0, G0); it.r < r1; it.next()) {
+        const int r = it.r, x = it.x;
+        int64_t* row = out + (long long)r * G0;
+        if (r != last) {
+            last = r;
+            cy = r % G1 - B;
+            cz = r / G1 - B;
+            yz_in = cy >= 0 && cy < g.N[1] && cz >= 0 && cz < g.N[2];
         }
-#pragma unroll
-        for (int u = 0; u < kGasUnroll; ++u) rho[u] = rr[u] < r1 ? density(rr[u], xx[u]) : 0.0;
-#pragma unroll
-        for (int u = 0; u < kGasUnroll; ++u) {
-            const long long cell = (long long)rr[u] * G0 + xx[u];
-            if (rr[u] < r1 && APM_IN_BOUNDS(cell, g.cells_gmf, L.status)) {
-                bool ok = false;
-                long long v = pow2 ? scaled_rint(rho[u], K, ok) : 0;
-                if (!ok) v = __double2ll_rn(__dmul_rn(__dmul_rn(rho[u], vol), scale));
-                out[cell] = v;
-            }
+        const int cx = x - B;
+        double rho = 0.0;
+        if (yz_in && cx >= 0 && cx < g.N[0]) {
+            if (own) rho = own[cx + (long long)g.N[0] * (cy + (long long)g.N[1] * cz)];
+        } else if (par) {
+            // parent cell floor(c / 2): the refinement factor is 2 (checked on the host);
+            // past an isolated root's faces (the only border cells with no parent
+            // cell, checked on the host) there are no baryons
+            long long px = ((g.start[0] + cx) >> 1) - p->start[0];
+            long long py = ((g.start[1] + cy) >> 1) - p->start[1];
+            long long pz = ((g.start[2] + cz) >> 1) - p->start[2];
+            if (px >= 0 && px < p->N[0] && py >= 0 && py < p->N[1] && pz >= 0 && pz < p->N[2])
+                rho = par[px + (long long)p->N[0] * (py + (long long)p->N[1] * pz)];
+        }
+        if (APM_IN_BOUNDS((long long)r * G0 + x, g.cells_gmf, L.status)) {
+            bool ok = false;
+            long long v = pow2 ? scaled_rint(rho, K, ok) : 0;
+            if (!ok) v = __double2ll_rn(__dmul_rn(__dmul_rn(rho, vol), scale));
+            row[x] = v;
         }
     }
 }
