@@ -336,9 +336,8 @@ apm_status apm_set_deposit_tiles(apm_ctx* ctx, int32_t on);
  *  threads[p] the runtime-planned pass's CTA size, 128 or 256;
  *  plan[p]    0: FP32 grids whose length has a compile-time plan (every
  *             {2,3,5,7}-smooth length from 36 to 84, and 128, 150, 256, 512)
- *             run the kernel specialised for it (16 lines per CTA; not the
- *             spectral gradient's z pass); 1: every grid runs the
- *             runtime-planned kernel; 2 (x forward and x inverse only): as 0,
+ *             run the kernel specialised for it (16 lines per CTA); 1: every
+ *             grid runs the runtime-planned kernel; 2 (x forward and x inverse only): as 0,
  *             and grids with M0 = M1 whose M x (M/2 + 1) plane fits 200 KB run
  *             the x and y transforms of a whole z plane in one kernel (the y
  *             pass then has no work for them; the inverse needs the window no

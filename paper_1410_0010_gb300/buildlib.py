@@ -26,7 +26,7 @@ SOURCES = [("apm_api.cu", "apm_api.o", []), ("k_green.cu", "k_green.o", []),
            ("apm_noalloc.cu", "apm_noalloc.o", []), ("k_order.cu", "k_order.o", [])] + [
     ("k_fft_col.cu", f"k_fft_col_{p}_{m}.o", [f"-DAPM_COL_FP64={1 if p == 'f64' else 0}", f"-DAPM_COL_MODE={m}"])
     for p in ("f32", "f64") for m in (0, 1, 2, 3)] + [
-    ("k_fft_fast.cu", f"k_fft_fast_{m}.o", [f"-DAPM_FAST_MODE={m}"]) for m in (0, 1, 2, 3, 4)]
+    ("k_fft_fast.cu", f"k_fft_fast_{m}.o", [f"-DAPM_FAST_MODE={m}"]) for m in (0, 1, 2, 3, 4, 5)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
           "--expt-relaxed-constexpr"]

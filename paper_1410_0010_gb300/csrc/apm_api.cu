@@ -355,9 +355,9 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
     P.seg_of.assign(ng, 0);
     P.seg.clear();
     // the kernel of each grid: a compile-time plan for the FP32 passes of its
-    // length, if there is one (not for the spectral gradient's z pass, whose
-    // components share this work list with the runtime-planned kernel, nor for
-    // the x-forward pass while its bulk-copy wait is made to run out)
+    // length, if there is one (not for the x-forward pass while its bulk-copy
+    // wait is made to run out); a spectral gradient's components run the z pass
+    // on the same work list (k_col_fast MODE 3, or k_col MODE 3)
     std::vector<int> fast(ng, 0), lens(ng, 0);
     const bool row = q == kPassXf || q == kPassXi;
     // with plan 2 on the x-forward pass, a grid with M0 = M1 whose plane fits
@@ -381,7 +381,7 @@ apm_status build_pass(apm_ctx* c, const Level& L, int q, int budget, int threads
         const GridDev& g = L.hg[k];
         lens[k] = row ? g.M[0] : (q == kPassZ ? g.M[2] : g.M[1]);
         if (!f64 && L.plan[q] != 1 && fft_fast_enabled() && fast_length(lens[k]) &&
-            !(q == kPassZ && c->cfg.gradient == APM_GRAD_SPECTRAL) && !(q == kPassXf && fault_wait()))
+            !(q == kPassXf && fault_wait()))
             fast[k] = lens[k];
         if ((q == kPassXf || q == kPassYf) && fused_xy(g)) fast[k] = q == kPassXf ? -lens[k] : kSkip;
         if ((q == kPassXi || q == kPassYi) && fused_yx(g)) fast[k] = q == kPassXi ? -lens[k] : kSkip;
@@ -509,7 +509,8 @@ cudaError_t run_seg(apm_ctx* c, const Level& L, int q, const PassPlan& P, const 
     if (sg.fast_L) {
         switch (q) {
             case kPassYf: return launch_fft_yf_fast(sg.fast_L, a, s);
-            case kPassZ: return launch_fft_z_fast(sg.fast_L, a, s);
+            case kPassZ:   // component comp > 0 of a spectral gradient: the table times -i D_comp
+                return comp > 0 ? launch_fft_zgrad_fast(sg.fast_L, a, s) : launch_fft_z_fast(sg.fast_L, a, s);
             case kPassYi: return launch_fft_yi_fast(sg.fast_L, a, s);
             case kPassXf: return launch_fft_xf_fast(sg.fast_L, a, (const int64_t* const*)d_gmf, s);
             default: return launch_fft_xi_fast(sg.fast_L, a, d_phis, s);

@@ -525,6 +525,7 @@ cudaError_t launch_fft_xi(const FftArgs& a, void* const* phis, cudaStream_t s);
 // yf, z (with the table) and yi; a.chunks hold kFastTx columns per CTA
 cudaError_t launch_fft_yf_fast(int L, const FftArgs& a, cudaStream_t s);
 cudaError_t launch_fft_z_fast(int L, const FftArgs& a, cudaStream_t s);
+cudaError_t launch_fft_zgrad_fast(int L, const FftArgs& a, cudaStream_t s);   // spectral component a.comp
 cudaError_t launch_fft_yi_fast(int L, const FftArgs& a, cudaStream_t s);
 // the fused x + y forward over one z plane (k_xy_fast) of a grid with
 // M0 = M1 = L: the plane (L rows x L/2 + 1 columns) and the twiddles

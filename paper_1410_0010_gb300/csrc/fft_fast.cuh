@@ -230,11 +230,12 @@ struct FastOutAll {
 
 // Column pass (AX 1: y, 2: z) with compile-time plan P, TX kx columns per CTA
 // (the level's lines for this pass) and NT threads; the same work list and
-// layout as k_col (MODE 0 yf, 1 z with the table, 2 yi).
+// layout as k_col (MODE 0 yf, 1 z with the table, 2 yi, 3 z with the table
+// times -i D_comp of spectral-gradient component comp).
 template <class P, int AX, int MODE, int TX, int NT>
 __global__ void __launch_bounds__(NT) k_col_fast(const GridDev* __restrict__ grids, const Chunk* __restrict__ chunks,
                                                  const float2* __restrict__ tw_arena, const float* __restrict__ tab,
-                                                 float2* __restrict__ wsA, float2* __restrict__ wsB) {
+                                                 float2* __restrict__ wsA, float2* __restrict__ wsB, int comp) {
     constexpr int L = P::L;
     extern __shared__ __align__(16) unsigned char smem_fast[];
     float2* buf = reinterpret_cast<float2*>(smem_fast);
@@ -302,12 +303,28 @@ __global__ void __launch_bounds__(NT) k_col_fast(const GridDev* __restrict__ gri
         }
     } else {
         // phi-hat = T(kappa) rho-hat between the forward and the inverse
+        // (MODE 1); MODE 3, a spectral-gradient component comp (1-3):
+        // -i D_comp T(kappa) rho-hat
         const int ky = other;
         const int fy = ky <= M1 / 2 ? ky : M1 - ky;
-        TabCol<float> tabf;   // a dead line reads column 0 (its results are never stored)
-        tabf.p = tab + (g.tab_off + (long long)fy * Hx + (live ? kx0 + line : 0));
-        tabf.zst = g.Hy2 * Hx;
-        tabf.L = L;
+        TabCol<float> tabc;   // a dead line reads column 0 (its results are never stored)
+        tabc.p = tab + (g.tab_off + (long long)fy * Hx + (live ? kx0 + line : 0));
+        tabc.zst = g.Hy2 * Hx;
+        tabc.L = L;
+        using Tab = typename std::conditional<MODE == 3, TabGrad<float>, TabCol<float>>::type;
+        Tab tabf;
+        if constexpr (MODE == 3) {
+            const int kx = kx0 + line;
+            tabf.tab = tabc;
+            tabf.comp = comp;
+            tabf.dz = (float)g.dk[2];
+            const int M0 = g.M[0];
+            const int kyc = ky <= M1 / 2 ? ky : ky - M1;
+            tabf.dline = comp == 1 ? (2 * kx == M0 ? 0.f : (float)(g.dk[0] * kx))
+                                   : (comp == 2 ? (2 * ky == M1 ? 0.f : (float)(g.dk[1] * kyc)) : 0.f);
+        } else {
+            tabf = tabc;
+        }
         fast_dif_stage<P, 0, TX, NT, true, false>(buf, tw, gin, gout);
         __syncthreads();
         if constexpr (P::NST == 3) {

@@ -1,19 +1,20 @@
 // k_fft_fast.cu -- launchers of the FP32 FFT passes with compile-time plans
 // (fft_fast.cuh), one per length of APM_FAST_LENGTHS; compiled once per pass
-// with -DAPM_FAST_MODE=0|1|2|3|4 (yf, z, yi, xf, xi) so the instantiations
-// build in parallel.
+// with -DAPM_FAST_MODE=0|1|2|3|4|5 (yf, z, yi, xf, xi, z of a spectral-gradient
+// component) so the instantiations build in parallel.
 #include "fft_fast.cuh"
 
 #if !defined(APM_FAST_MODE)
-#error "k_fft_fast.cu is compiled with -DAPM_FAST_MODE=0|1|2|3|4"
+#error "k_fft_fast.cu is compiled with -DAPM_FAST_MODE=0|1|2|3|4|5"
 #endif
 
 namespace apm {
 
 namespace {
 constexpr int kFastMode = APM_FAST_MODE;
-constexpr bool kFastRow = kFastMode >= 3;
-constexpr int kFastAx = kFastMode == 1 ? 2 : 1;
+constexpr bool kFastRow = kFastMode == 3 || kFastMode == 4;
+constexpr int kFastAx = (kFastMode == 1 || kFastMode == 5) ? 2 : 1;
+constexpr int kColMode = kFastMode == 5 ? 3 : kFastMode;   // k_col_fast's MODE
 constexpr int kLines = kFastRow ? kFastNp : kFastTx;
 
 template <int A, int B, int Cc>
@@ -22,7 +23,7 @@ constexpr auto kernel_of() {
     constexpr int NT = fast_threads(A, B, Cc, kLines);
     if constexpr (kFastMode == 3) return k_xf_fast<P, kFastNp, NT>;
     else if constexpr (kFastMode == 4) return k_xi_fast<P, kFastNp, NT>;
-    else return k_col_fast<P, kFastAx, kFastMode, kFastTx, NT>;
+    else return k_col_fast<P, kFastAx, kColMode, kFastTx, NT>;
 }
 
 template <int L>
@@ -40,7 +41,7 @@ cudaError_t launch_one(const FftArgs& a, const int64_t* const* gmf, void* const*
                                                   a.comp);
     else
         kern<<<a.n_chunks, NT, smem_of<L>(), s>>>(a.g, a.chunks, (const float2*)a.tw, (const float*)a.tab,
-                                                  (float2*)a.wsA, (float2*)a.wsB);
+                                                  (float2*)a.wsA, (float2*)a.wsB, a.comp);
     return cudaGetLastError();
 }
 
@@ -139,6 +140,11 @@ cudaError_t launch_fft_xy_fast(int L, const FftArgs& a, const int64_t* const* gm
 }
 cudaError_t launch_fft_xf_fast(int L, const FftArgs& a, const int64_t* const* gmf, cudaStream_t s) {
     return launch_fast(L, a, gmf, nullptr, s);
+}
+#elif APM_FAST_MODE == 5
+cudaError_t fft_configure_fast_zg() { return configure_fast(); }
+cudaError_t launch_fft_zgrad_fast(int L, const FftArgs& a, cudaStream_t s) {
+    return launch_fast(L, a, nullptr, nullptr, s);
 }
 #else
 cudaError_t fft_configure_fast_xi() { return configure_fast(); }

@@ -19,6 +19,7 @@ cudaError_t fft_configure_fast_z();
 cudaError_t fft_configure_fast_yi();
 cudaError_t fft_configure_fast_xf();
 cudaError_t fft_configure_fast_xi();
+cudaError_t fft_configure_fast_zg();
 
 // Allows every pass kernel up to kFftSmemLimit of dynamic shared memory
 // (above the 48 KB default).
@@ -35,7 +36,7 @@ cudaError_t fft_configure() {
                                fft_configure_zg_f32, fft_configure_yf_f64, fft_configure_z_f64,
                                fft_configure_yi_f64, fft_configure_zg_f64, fft_configure_fast_yf,
                                fft_configure_fast_z, fft_configure_fast_yi, fft_configure_fast_xf,
-                               fft_configure_fast_xi};
+                               fft_configure_fast_xi, fft_configure_fast_zg};
     for (auto f : cols) {
         cudaError_t e = f();
         if (e != cudaSuccess) return e;
