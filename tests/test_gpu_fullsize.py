@@ -17,7 +17,8 @@
   parent's 64^3 footprint on the root, with the particle accelerations they
   own; FD, parent carry and particle interpolation on samples;
 * the periodic 128^3 + three levels hierarchy in FP64 against the oracle at
-  the FP64 tolerance.
+  the FP64 tolerance, and its deposit through shared-memory tiles (particles
+  in bin order) bit-exact against the direct deposit.
 """
 import numpy as np
 import pytest
@@ -47,6 +48,38 @@ def test_plummer_periodic_three_levels_full(plummer, gradient):
     ref = _plummer_ref(plummer, gradient)
     gpu = run_gpu(w.grids, w.particles, w.half_dt, periodic=True, precision="fp32", gradient=gradient)
     compare(gpu, ref, "fp32")
+
+
+def test_plummer_deposit_tiles_bit_exact(plummer):
+    """The deposit through shared-memory tiles (particles in bin order,
+    apm_set_deposit_tiles: the mode bench.py picks for this workload) at full
+    size: every grid's mass field equals the direct deposit's bit for bit,
+    all levels at once and level by level."""
+    import torch
+
+    from paper_1410_0010_gb300.solver import Particles, Solver
+    w, _ = plummer
+    P = Particles({k: torch.as_tensor(np.ascontiguousarray(v), device="cuda") for k, v in w.particles.items()})
+    s = Solver(w.grids, periodic=True, precision="fp32", mass_frac_bits=w.mass_frac_bits, device=0)
+    bufs = s.alloc_all()
+    gmf = s._per_grid(bufs, "gmf")
+    s.deposit_all(P, w.half_dt, gmf, None)
+    direct = [t.clone() for t in gmf]
+    s.reserve_order(w.n_particles)
+    s.set_deposit_tiles(True)
+    s.order_particles(P, w.half_dt)
+    for t in gmf:
+        t.fill_(-1)
+    s.deposit_all(P, w.half_dt, gmf, None)
+    s.sync_status()
+    assert all(torch.equal(a, b) for a, b in zip(gmf, direct))
+    for lev in range(s.n_levels):
+        for t in bufs[lev]["gmf"]:
+            t.fill_(-1)
+        s.deposit(lev, P, w.half_dt, bufs[lev]["gmf"])
+    s.sync_status()
+    assert all(torch.equal(a, b) for a, b in zip(gmf, direct))
+    s.close()
 
 
 def test_plummer_periodic_three_levels_full_fp64(plummer):
