@@ -545,20 +545,55 @@ __global__ void __launch_bounds__(NT) k_xi_fast(const GridDev* __restrict__ grid
 //    and B_k to row 2p + 1 (column k);
 //  - y: DIF stages over the H columns (element-major, consecutive threads on
 //    consecutive columns), the last writing natural ky to HBM.
-template <int L> struct XyIn {
-    const int64_t* __restrict__ p;   // row 0 of the z plane
-    int G0, G1;
-    float scale;
-    __device__ __forceinline__ float2 ld(int line, int x) const {
-        float a = 0.f, b = 0.f;
-        if (x < G0) {
-            const int64_t* row = p + (long long)(2 * line) * G0;
-            if (2 * line < G1) a = fixed_to_real<float>(row[x], scale);
-            if (2 * line + 1 < G1) b = fixed_to_real<float>(row[G0 + x], scale);
+// The plane's x lines from the mass field (rows 2p, 2p + 1 packed as one
+// complex line p, line storage LS): one thread per pair of x positions of a
+// row pair, with 16-byte loads of both rows (consecutive threads on
+// consecutive positions) and one 16-byte shared store of the two complex
+// values; converted exactly (hardware int64 -> float rounding, power-of-two
+// scale).  Positions G0 .. L-1 and the row G1 of an odd G1 are zero.  LS is
+// even (2 (L/2 + 1)), so the stores are 16-byte aligned; with an odd G0 the
+// last pair writes position G0 (a zero), which lies inside the line storage
+// (LS >= L + 1) and is read by no x stage when G0 = L.
+template <int L, int NT, int LS>
+__device__ __forceinline__ void xy_load_plane(float2* buf, const int64_t* __restrict__ in, int G0, int G1, int nl,
+                                              float scale) {
+    const int half = (G0 + 1) / 2;   // position pairs per row
+    const bool vec = !(G0 & 1) && !(reinterpret_cast<size_t>(in) & 15);
+    const int items = nl * half;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < items; i += NT) {
+        const int p = i / half, x = 2 * (i - p * half);
+        const bool odd_row = 2 * p + 1 < G1;
+        const int64_t* r0 = in + (long long)(2 * p) * G0 + x;
+        long long a0, a1, b0 = 0, b1 = 0;
+        if (vec) {
+            const longlong2 u = *reinterpret_cast<const longlong2*>(r0);
+            a0 = u.x;
+            a1 = u.y;
+            if (odd_row) {
+                const longlong2 w = *reinterpret_cast<const longlong2*>(r0 + G0);
+                b0 = w.x;
+                b1 = w.y;
+            }
+        } else {
+            const bool x1 = x + 1 < G0;
+            a0 = r0[0];
+            a1 = x1 ? r0[1] : 0;
+            if (odd_row) {
+                b0 = r0[G0];
+                b1 = x1 ? r0[G0 + 1] : 0;
+            }
         }
-        return make_float2(a, b);
+        *reinterpret_cast<float4*>(buf + p * LS + x) =
+            make_float4(fixed_to_real<float>(a0, scale), fixed_to_real<float>(b0, scale),
+                        fixed_to_real<float>(a1, scale), fixed_to_real<float>(b1, scale));
     }
-};
+    const int pad = L - 2 * half;
+    for (int t = threadIdx.x; t < nl * pad; t += NT) {
+        const int p = t / pad;
+        buf[p * LS + 2 * half + (t - p * pad)] = make_float2(0.f, 0.f);
+    }
+}
 template <int L> struct XyOut {
     float2* __restrict__ p;          // B row ky = 0 of this plane, column 0
     int Hx;
@@ -644,18 +679,15 @@ __global__ void __launch_bounds__(NT, 2) k_xy_fast(const GridDev* __restrict__ g
     for (int t = threadIdx.x; t < L; t += NT) tw[t] = tw_arena[g.fx.tw_off + t];
     // rows 2 nl .. L-1 are the y transform's zero padding
     for (int t = threadIdx.x + 2 * nl * H; t < L * H; t += NT) buf[t] = make_float2(0.f, 0.f);
-    XyIn<L> gin;
-    gin.p = gmf[ch.grid] + (long long)z * G1 * G0;
-    gin.G0 = G0;
-    gin.G1 = G1;
-    gin.scale = pow2_neg<float>(F);
-    __syncthreads();   // twiddles
-    xy_x_stage<P, 0, NT, true, 2 * H>(buf, tw, gin, nl);
+    xy_load_plane<L, NT, 2 * H>(buf, gmf[ch.grid] + (long long)z * G1 * G0, G0, G1, nl, pow2_neg<float>(F));
+    __syncthreads();   // twiddles and the x lines
+    const NoIO none;
+    xy_x_stage<P, 0, NT, false, 2 * H>(buf, tw, none, nl);
     __syncthreads();
-    xy_x_stage<P, 1, NT, false, 2 * H>(buf, tw, gin, nl);
+    xy_x_stage<P, 1, NT, false, 2 * H>(buf, tw, none, nl);
     if constexpr (P::NST == 3) {
         __syncthreads();
-        xy_x_stage<P, 2, NT, false, 2 * H>(buf, tw, gin, nl);
+        xy_x_stage<P, 2, NT, false, 2 * H>(buf, tw, none, nl);
     }
     __syncthreads();
     // separation, one warp per line (its storage is touched by no other warp)
@@ -691,7 +723,6 @@ __global__ void __launch_bounds__(NT, 2) k_xy_fast(const GridDev* __restrict__ g
     XyOut<L> gout;
     gout.p = wsB + (g.wsB + (long long)z * L * g.Hx);
     gout.Hx = g.Hx;
-    const NoIO none;
     xy_y_stage<P, 0, NT, false>(buf, tw, none);
     __syncthreads();
     if constexpr (P::NST == 3) {
