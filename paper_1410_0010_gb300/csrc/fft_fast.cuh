@@ -352,9 +352,9 @@ struct NoIO {
 
 // xf: GMF rows -> half spectra along x, A[z][y][kx] (the layout of k_xf).
 // Load pass: the CTA's rows are one contiguous int64 range, read with
-// consecutive threads on consecutive cells and converted (hardware int64 ->
-// float rounding, exact power-of-two scale); positions past G0 and missing
-// rows are zero.  Then the forward stages in place, and the separation of the
+// consecutive threads on consecutive pairs of cells of a row pair and
+// converted (hardware int64 -> float rounding, exact power-of-two scale);
+// positions past G0 and missing rows are zero.  Then the forward stages in place, and the separation of the
 // two real rows, A_k = (Z_k + conj Z_{L-k}) / 2, B_k = (Z_k - conj Z_{L-k}) / 2i,
 // written with consecutive threads on consecutive kx.
 template <class P, int NP, int NT>
@@ -374,13 +374,44 @@ __global__ void __launch_bounds__(NT) k_xf_fast(const GridDev* __restrict__ grid
     const int64_t* __restrict__ in = gmf[ch.grid] + r_first * G0;
     for (int t = threadIdx.x; t < L; t += NT) tw[t] = tw_arena[g.fx.tw_off + t];
     const float scale = pow2_neg<float>(F);
-    float* fb = reinterpret_cast<float*>(buf);
-    // element (x, row q): buffer float (x PITCH + q / 2) * 2 + (q & 1)
-    for (int f = threadIdx.x; f < 2 * NP * L; f += NT) {
-        const int q = f / L, x = f - q * L;
-        float v = 0.f;
-        if (q < nr && x < G0) v = fixed_to_real<float>(in[q * G0 + x], scale);
-        fb[(x * PITCH + (q >> 1)) * 2 + (q & 1)] = v;
+    // element (x, line p) = (row 2p, row 2p + 1) at x; one thread per pair of
+    // positions of a line, with 16-byte loads of both rows when G0 is even
+    {
+        constexpr int HALF = (L + 1) / 2;
+        const bool vec = !(G0 & 1) && !(reinterpret_cast<size_t>(in) & 15);
+#pragma unroll 4
+        for (int i = threadIdx.x; i < NP * HALF; i += NT) {
+            const int p = i / HALF, x = 2 * (i - p * HALF);
+            const int q = 2 * p;
+            const int64_t* r0 = in + (long long)q * G0 + x;
+            long long a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+            if (vec && x < G0) {   // G0 even: x + 1 < G0 too
+                if (q < nr) {
+                    const longlong2 u = *reinterpret_cast<const longlong2*>(r0);
+                    a0 = u.x;
+                    a1 = u.y;
+                }
+                if (q + 1 < nr) {
+                    const longlong2 w = *reinterpret_cast<const longlong2*>(r0 + G0);
+                    b0 = w.x;
+                    b1 = w.y;
+                }
+            } else {
+                const bool x0 = x < G0, x1 = x + 1 < G0;
+                if (q < nr) {
+                    if (x0) a0 = r0[0];
+                    if (x1) a1 = r0[1];
+                }
+                if (q + 1 < nr) {
+                    if (x0) b0 = r0[G0];
+                    if (x1) b1 = r0[G0 + 1];
+                }
+            }
+            buf[x * PITCH + p] = make_float2(fixed_to_real<float>(a0, scale), fixed_to_real<float>(b0, scale));
+            if (L % 2 == 0 || x + 1 < L)
+                buf[(x + 1) * PITCH + p] =
+                    make_float2(fixed_to_real<float>(a1, scale), fixed_to_real<float>(b1, scale));
+        }
     }
     __syncthreads();
     const NoIO none;
