@@ -156,6 +156,7 @@ __device__ __forceinline__ bool tile_add(const TileSet& ts, int slot, int gi, in
 #define APM_DEP_MIN_CTAS 6
 #endif
 constexpr int kDepThreads = APM_DEP_THREADS;
+static_assert(kDepThreads % 32 == 0, "the root deposit exchanges charges across whole warps");
 
 template <bool SMALL>
 __device__ __forceinline__ unsigned long long mul63(unsigned long long a, unsigned long long b) {
@@ -216,6 +217,124 @@ __device__ __forceinline__ void scatter_charges(const LevelDev& L, int64_t* cons
             if (!TILE || !tile_add(ts, slot, gi, cx[1], cy[1], cz[1], M - others)) add_charge(out, ci, M - others);
         }
     }
+}
+
+// ---- the root level with x neighbours merged across the warp ----
+// Particles stored in x order (a lattice such as the Zel'dovich workloads',
+// row by row) put lane j's cloud next to lane j-1's along x: at a spacing of
+// two cells, lane j-1's column cx+1 is lane j's column cx-1, in the same nine
+// (y, z) rows.  Lane j then adds lane j-1's nine column +1 charges to its own
+// column (0 or 1) on the same cells, and lane j-1 leaves them out: one 64-bit
+// reduction per such cell instead of two.  Integer addition is exact and
+// associative, so the field is the same bit for bit.  The partners are tested
+// on the cells themselves (all of cy and cz, and lane j-1's cx[2] against
+// lane j's cx[0] or cx[1]), so the edge rules (fold, wrap, drop) need no
+// special case.  A lane never merges into its column 2, the one it may pass
+// on, so no charge is ever forwarded twice.
+template <bool SMALL>
+__device__ __forceinline__ void scatter_root_merged(const GridDev& g, int64_t* __restrict__ out,
+                                                    unsigned* __restrict__ status, long long M,
+                                                    unsigned long long aM, const unsigned long long w[3][3],
+                                                    const int cx[3], const int cy[3], const int cz[3], bool ok,
+                                                    int ma, bool give) {
+    constexpr unsigned kFull = 0xffffffffu;
+    unsigned long long mx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mx[a] = mul63<SMALL>(aM, w[0][a]);
+    const unsigned G0 = g.G[0], G01 = (unsigned)g.G[0] * g.G[1];
+    long long others = 0, centre_in = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        unsigned long long mxy[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mxy[a] = mul63<SMALL>(mx[a], w[1][b]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            long long v[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a == 1 && b == 1 && c == 1) {
+                    v[a] = 0;
+                    continue;
+                }
+                long long q = (long long)mul63<SMALL>(mxy[a], w[2][c]);
+                q = M < 0 ? -q : q;
+                others += q;
+                v[a] = q;
+            }
+            // lane j-1's column 2 of this row (every lane exchanges)
+            const long long in = __shfl_up_sync(kFull, v[2], 1);
+            if (ma == 0) {
+                v[0] += in;
+            } else if (ma == 1) {
+                if (b == 1 && c == 1) centre_in = in;
+                else v[1] += in;
+            }
+            const bool rok = ok && cy[b] >= 0 && cz[c] >= 0;
+            const unsigned row = G0 * (unsigned)cy[b] + G01 * (unsigned)cz[c];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a == 1 && b == 1 && c == 1) continue;
+                if (a == 2 && give) continue;
+                if (rok && cx[a] >= 0 && APM_IN_BOUNDS(row + (unsigned)cx[a], g.cells_gmf, status))
+                    add_charge(out, row + (unsigned)cx[a], v[a]);
+            }
+        }
+    }
+    const unsigned ci = (unsigned)cx[1] + G0 * (unsigned)cy[1] + G01 * (unsigned)cz[1];
+    if (ok && cx[1] >= 0 && cy[1] >= 0 && cz[1] >= 0 && APM_IN_BOUNDS(ci, g.cells_gmf, status))
+        add_charge(out, ci, M - others + centre_in);
+}
+
+// The root level's deposit of this lane's particle (fixed-point position X,
+// integer mass M; ok false: no particle, the lane only takes part in the
+// exchanges).  Every lane of the warp must call it, with none exited.
+__device__ __forceinline__ void deposit_root_merged(const LevelDev& L, const long long X[3], long long M,
+                                                    bool ok, bool outside, int64_t* const* __restrict__ gmf,
+                                                    unsigned* __restrict__ status) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const GridDev& g = L.g[0];
+    const int PB = L.frac_bits;
+    long long ic[3];
+    unsigned long long w[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        ic[j] = X[j] >> PB;
+        tsc_fixed(X[j], PB, w[j]);
+    }
+    if (ok && g.mode == 1 && outside) atomicOr(status, kStOutOfBox);
+    int cx[3], cy[3], cz[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        cx[k] = edge_rule(ic[0] + k - 1 - g.lo[0], g.G[0], g.mode);
+        cy[k] = edge_rule(ic[1] + k - 1 - g.lo[1], g.G[1], g.mode);
+        cz[k] = edge_rule(ic[2] + k - 1 - g.lo[2], g.G[2], g.mode);
+    }
+    // lane j-1's cells, exchanged unconditionally (every lane reaches every shuffle)
+    const int lane = threadIdx.x & 31;
+    const int pok = __shfl_up_sync(kFull, ok ? 1 : 0, 1);
+    const int pcx2 = __shfl_up_sync(kFull, cx[2], 1);
+    int pcy[3], pcz[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        pcy[k] = __shfl_up_sync(kFull, cy[k], 1);
+        pcz[k] = __shfl_up_sync(kFull, cz[k], 1);
+    }
+    bool same = ok && pok != 0 && lane > 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) same = same && pcy[k] == cy[k] && pcz[k] == cz[k];
+    // this lane's column that takes lane j-1's column 2 (-1: none)
+    const int ma = !same ? -1 : (cx[0] == pcx2 ? 0 : (cx[1] == pcx2 ? 1 : -1));
+    // lane j+1 takes this lane's column 2
+    const int next_takes = __shfl_down_sync(kFull, ma >= 0 ? 1 : 0, 1);
+    const bool give = ok && lane < 31 && next_takes != 0;
+    const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
+    // one product width for the whole warp (the general products round the
+    // same way), so that every lane reaches the same shuffles
+    if (__all_sync(kFull, !ok || aM < (1ULL << 32)))
+        scatter_root_merged<true>(g, gmf[0], status, M, aM, w, cx, cy, cz, ok, ma, give);
+    else
+        scatter_root_merged<false>(g, gmf[0], status, M, aM, w, cx, cy, cz, ok, ma, give);
 }
 
 // Deposit of one particle (fixed-point position X, integer mass M) into the
@@ -460,8 +579,17 @@ __global__ void __launch_bounds__(kDepThreads, APM_DEP_MIN_CTAS) k_deposit_level
     int nslots = 0, used = 0;
     auto lv = [&](int l) -> const LevelDev& { return levels[l]; };
     if constexpr (TILE) nslots = tile_setup(ts, anchor, lv, nl, P.order_shift, ok, X, used);
+    int l0 = 0;
+    if constexpr (!TILE) {
+        // the root with the warp's x neighbours merged: every lane, with or
+        // without a particle (blocks are whole warps)
+        if (levels[0].is_root) {
+            deposit_root_merged(levels[0], X, M, ok, outside, gmfs[0], status);
+            l0 = 1;
+        }
+    }
     if (ok)
-        for (int l = 0; l < nl; ++l)
+        for (int l = l0; l < nl; ++l)
             if (!deposit_level<TILE>(levels[l], X, M, l == 0 && outside, gmfs[l], status, ts, l < nslots ? l : -1))
                 break;
     if constexpr (TILE) {

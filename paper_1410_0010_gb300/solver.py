@@ -443,9 +443,11 @@ class Graph:
 class StepPipeline:
     """End-to-end solves from pinned host particles to host accelerations, with
     the copies overlapped: two device particle/acceleration buffer sets, each
-    with its own captured solve (a library-owned CUDA graph), and a copy stream that uploads
-    step k+1's particles and downloads step k-1's accelerations while step k
-    solves.  Every step still copies all of its inputs in and its result out.
+    with its own captured solve (a library-owned CUDA graph), an upload stream
+    that copies step k+1's particles in while step k solves, and a download
+    stream that copies step k's accelerations out once it has solved (one
+    stream per direction, so that a full-duplex host link runs both at once).
+    Every step still copies all of its inputs in and its result out.
 
     solver, bufs: a Solver and its alloc_all() buffers (shared by both sets);
     host: dict of pinned float64 host arrays (PARTICLE_KEYS); the rest as for
@@ -466,6 +468,7 @@ class StepPipeline:
             self.sets.append((P, pacc))
         self.hout = [torch.empty((3, self.n), dtype=solver.dtype).pin_memory() for _ in range(2)]
         self.copy = torch.cuda.Stream(device=dev)
+        self.copy_out = torch.cuda.Stream(device=dev)
         self.graphs = []
         for P, pacc in self.sets:
             for k in PARTICLE_KEYS:
@@ -495,7 +498,9 @@ class StepPipeline:
                     P.t[key].copy_(src[key], non_blocking=True)
                 ev_in[k % 2].record(cp)
 
+        dn = self.copy_out
         cp.wait_stream(comp)
+        dn.wait_stream(comp)
         if steps > 0:
             upload(0)
         for k in range(steps):
@@ -509,9 +514,10 @@ class StepPipeline:
                 if k >= 1:
                     cp.wait_event(ev_done[1 - b])      # set 1-b is free once step k-1 has solved
                 upload(k + 1)
-            with torch.cuda.stream(cp):
-                cp.wait_event(ev_done[b])
+            with torch.cuda.stream(dn):
+                dn.wait_event(ev_done[b])
                 dst = self.hout[b] if outputs is None else outputs(k)
                 dst.copy_(self.sets[b][1], non_blocking=True)
-                ev_out[b].record(cp)
+                ev_out[b].record(dn)
         comp.wait_stream(cp)
+        comp.wait_stream(dn)

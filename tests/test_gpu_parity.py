@@ -206,6 +206,58 @@ def test_deposit_is_order_independent_bitwise():
     assert rel_l2(a["pacc"][:, perm], b["pacc"]) < 1e-6
 
 
+def _x_rows(rng, n_rows, per_row, n_cells, spacing=2.0, jitter=0.3, lo=0.0, hi=1.0, wrap=True):
+    """Rows of particles stored x-fastest, `spacing` cells apart along x with a
+    small jitter (some neighbours 1 or 3 cells apart), each row at a random
+    (y, z) inside [lo, hi) and a random x start (wrapping past 1 when `wrap`)."""
+    d = 1.0 / n_cells
+    xs, ys, zs = [], [], []
+    for _ in range(n_rows):
+        x0 = rng.random() if wrap else lo + 0.1 * (hi - lo) * rng.random()
+        y0, z0 = lo + (hi - lo) * rng.random(), lo + (hi - lo) * rng.random()
+        x = x0 + d * (spacing * np.arange(per_row) + jitter * rng.standard_normal(per_row))
+        xs.append(np.mod(x, 1.0) if wrap else np.clip(x, lo, hi - 1e-9))
+        ys.append(np.full(per_row, y0))
+        zs.append(np.full(per_row, z0))
+    x, y, z = (np.concatenate(a) for a in (xs, ys, zs))
+    n = len(x)
+    return dict(x=x, y=y, z=z, vx=np.zeros(n), vy=np.zeros(n), vz=np.zeros(n))
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_root_deposit_of_x_ordered_particles_bit_exact(periodic):
+    """The root deposit merges the charges that x-neighbouring lanes give the
+    same cells (one reduction instead of two).  Rows of particles two cells
+    apart (some one or three) exercise it: rows that wrap the periodic root,
+    rows whose clouds fold at an isolated root's faces, warps mixing the
+    32-bit and 64-bit product widths, a ragged last warp, and a refined level
+    below the root.  The mass field stays bit-exact against the oracle."""
+    rng = np.random.default_rng(21 if periodic else 22)
+    n_cells = 24
+    grids = [GridDesc(0, -1, (0, 0, 0), (n_cells,) * 3), GridDesc(1, 0, (12, 10, 14), (16, 16, 12))]
+    if periodic:
+        parts = _x_rows(rng, 37, 29, n_cells)
+    else:
+        # rows hugging the low and high faces: their clouds fold onto the edge cells
+        edge = 0.5 / n_cells
+        parts = W.concat_particles(_x_rows(rng, 20, 11, n_cells, lo=edge, hi=1.0 - edge, wrap=False),
+                                   _x_rows(rng, 17, 9, n_cells, spacing=1.0, lo=0.0, hi=1.0, wrap=False))
+        for k in ("y", "z"):
+            sel = rng.random(len(parts[k])) < 0.3
+            parts[k][sel] = np.where(rng.random(sel.sum()) < 0.5, 0.2 / n_cells, 1.0 - 0.2 / n_cells)
+    n = len(parts["x"])
+    # most masses below 2^-20 (32-bit products at 52 fraction bits), some not
+    m = np.full(n, 2.0 ** -24) * (1.0 + rng.random(n))
+    m[rng.random(n) < 0.05] = 0.25
+    parts["m"] = m
+    ref = run_oracle(grids, parts, 0.0, periodic=periodic)
+    gpu = run_gpu(grids, parts, 0.0, periodic=periodic, precision="fp64")
+    compare(gpu, ref, "fp64")
+    per_level = run_gpu(grids, parts, 0.0, periodic=periodic, precision="fp64", batched=False)
+    for gi in gpu["gmf"]:
+        assert np.array_equal(gpu["gmf"][gi], per_level["gmf"][gi]), gi
+
+
 def test_sine_wave_periodic_mode_matches_closed_form_on_gpu():
     """Sec. 3.4 on the GPU: the FP64 path reproduces the single-mode solution."""
     import oracle
